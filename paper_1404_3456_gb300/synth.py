@@ -1,0 +1,207 @@
+"""Seeded synthetic genomes and shotgun fragment sets.
+
+This module is shared by the tests, the benchmark and the oracle's checks.  It
+holds none of the method's arithmetic: it only draws genomes and fragments and
+joins fragments into a '$'-separated ASCII text (the input format the library
+and the oracle both accept).  All randomness comes from numpy's PCG64 seeded
+per instance, so every input is reproducible from (workload, seed).
+
+The paper's dataset (Bacillus megaterium MSP20.1 from NCBI, Sec. V) is not
+available; these workloads stand in for it, with the paper's shotgun model
+(Sec. III, Fig. 2): a genome over {A, C, G, T} is cut into error-free fragments
+whose break positions are all different (Sec. III, Fig. 4).
+
+Workloads
+---------
+``tiny``     10,000 bp i.i.d. genome, 200 reads of 400 bp at distinct uniform
+             starts plus reads pinned at both ends, consecutive starts at most
+             400 - 31 apart and every 31-mer of the genome unique (so the only
+             overlaps >= 31 are the true ones); reads in shuffled order.
+``sa64m``    64,000,000 bp genome: 90 % i.i.d., 5 % tandem arrays (period
+             U{2..50}, U{10..200} exact copies), 5 % copies of one 300 bp
+             element, each copy with 1 % point substitutions.  One '$'.
+``batched``  independent instances: genome log-uniform [2 kbp, 200 kbp] i.i.d.;
+             reads of length U{100..1000} at uniform starts until 8x coverage.
+``served``   jobs: genome log-uniform [5 kbp, 5 Mbp] with 2 % tandem arrays
+             (period U{2..50}, copies U{10..200}); 150 bp reads at 10x.
+``large``    1.5 Gbp genome: 85 % i.i.d., 10 % tandem (period U{2..100},
+             copies U{10..200}), 5 % copies of a 6 kbp element with 0.5 %
+             substitutions; plus 10 M reads of 150 bp at 1x.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+BASES = np.frombuffer(b"ACGT", dtype=np.uint8)
+SEP = ord("$")
+
+
+def rng_for(seed: int, stream: int = 0) -> np.random.Generator:
+    return np.random.Generator(np.random.PCG64([int(seed), int(stream)]))
+
+
+def iid(rng: np.random.Generator, n: int) -> np.ndarray:
+    """n i.i.d. uniform bases as ASCII bytes."""
+    return BASES[rng.integers(0, 4, size=int(n), dtype=np.uint8)]
+
+
+def substitute(rng: np.random.Generator, seq: np.ndarray, p: float) -> np.ndarray:
+    """Each position replaced with probability p by one of the 3 other bases, uniformly."""
+    codes = np.searchsorted(BASES, seq).astype(np.uint8)  # A,C,G,T -> 0..3 (BASES is sorted)
+    hit = rng.random(seq.shape) < p
+    shift = rng.integers(1, 4, size=seq.shape, dtype=np.uint8)
+    codes = np.where(hit, (codes + shift) % 4, codes).astype(np.uint8)
+    return BASES[codes]
+
+
+def genome_with_repeats(rng, G: int, frac_tandem: float, period: tuple, copies: tuple,
+                        frac_elem: float = 0.0, elem_len: int = 0, elem_subst: float = 0.0):
+    """A genome of exactly G bases: i.i.d. segments with tandem arrays and
+    element copies inserted at uniformly shuffled points between them."""
+    blocks = []
+    budget = int(round(frac_tandem * G))
+    used = 0
+    while used < budget:
+        P = int(rng.integers(period[0], period[1] + 1))
+        C = int(rng.integers(copies[0], copies[1] + 1))
+        arr = np.tile(iid(rng, P), C)[: budget - used]
+        blocks.append(arr)
+        used += arr.size
+    if frac_elem > 0 and elem_len > 0:
+        elem = iid(rng, elem_len)
+        n_copies = int(round(frac_elem * G)) // elem_len
+        if n_copies:
+            mat = np.broadcast_to(elem, (n_copies, elem_len))
+            mat = substitute(rng, mat, elem_subst)
+            blocks.extend(list(mat))
+    order = rng.permutation(len(blocks)) if blocks else np.zeros(0, dtype=np.int64)
+    blocks = [blocks[i] for i in order]
+    n_iid = G - sum(b.size for b in blocks)
+    if n_iid < 0:
+        raise ValueError("repeat fractions exceed the genome")
+    body = iid(rng, n_iid)
+    cuts = np.sort(rng.integers(0, n_iid + 1, size=len(blocks)))
+    parts = []
+    prev = 0
+    for c, b in zip(cuts, blocks):
+        parts.append(body[prev:c])
+        parts.append(b)
+        prev = c
+    parts.append(body[prev:])
+    g = np.concatenate(parts) if parts else body
+    assert g.size == G
+    return g
+
+
+def join_reads(reads) -> np.ndarray:
+    """Fragments joined into one text, each followed by '$'."""
+    total = sum(int(r.size) + 1 for r in reads)
+    out = np.empty(total, dtype=np.uint8)
+    pos = 0
+    for r in reads:
+        out[pos: pos + r.size] = r
+        out[pos + r.size] = SEP
+        pos += r.size + 1
+    return out
+
+
+def genome_text(genome: np.ndarray) -> np.ndarray:
+    """A single genome as a one-fragment text (genome + '$')."""
+    return join_reads([genome])
+
+
+def _kmers_unique(g: np.ndarray, k: int) -> bool:
+    if g.size < k:
+        return True
+    view = np.lib.stride_tricks.sliding_window_view(g, k)
+    packed = np.ascontiguousarray(view).view(np.dtype((np.void, k))).ravel()
+    return np.unique(packed).size == packed.size
+
+
+def tiny(seed: int, G: int = 10_000, read_len: int = 400, n_random: int = 200,
+         min_overlap: int = 31):
+    """The tiny workload.  Returns dict(genome, reads, starts, text, min_overlap)."""
+    rng = rng_for(seed, 1)
+    while True:
+        genome = iid(rng, G)
+        if _kmers_unique(genome, min_overlap):
+            break
+    max_gap = read_len - min_overlap
+    while True:
+        pick = rng.choice(np.arange(1, G - read_len), size=n_random, replace=False)
+        starts = np.sort(np.concatenate([[0, G - read_len], pick]))
+        if np.all(np.diff(starts) <= max_gap):
+            break
+    order = rng.permutation(starts.size)
+    starts = starts[order]
+    reads = [genome[s: s + read_len] for s in starts]
+    return dict(genome=genome, reads=reads, starts=starts, text=join_reads(reads),
+                min_overlap=min_overlap)
+
+
+def shotgun(rng, genome: np.ndarray, coverage: float, len_lo: int, len_hi: int):
+    """Error-free reads of length U{len_lo..len_hi} at uniform starts until the
+    read bases reach coverage x |genome|."""
+    G = genome.size
+    target = coverage * G
+    reads, starts = [], []
+    total = 0
+    while total < target:
+        n = int(rng.integers(len_lo, len_hi + 1))
+        n = min(n, G)
+        s = int(rng.integers(0, G - n + 1))
+        reads.append(genome[s: s + n])
+        starts.append(s)
+        total += n
+    return reads, np.array(starts, dtype=np.int64)
+
+
+def log_uniform(rng, lo: float, hi: float) -> int:
+    return int(round(float(np.exp(rng.uniform(np.log(lo), np.log(hi))))))
+
+
+def batched_instance(seed: int, index: int, g_lo: int = 2_000, g_hi: int = 200_000,
+                     coverage: float = 8.0, len_lo: int = 100, len_hi: int = 1000,
+                     min_overlap: int = 31):
+    rng = rng_for(seed * 1_000_003 + index, 3)
+    G = log_uniform(rng, g_lo, g_hi)
+    genome = iid(rng, G)
+    reads, starts = shotgun(rng, genome, coverage, len_lo, len_hi)
+    return dict(genome=genome, reads=reads, starts=starts, text=join_reads(reads),
+                min_overlap=min_overlap)
+
+
+def batched(seed: int, n_instances: int = 4096, **kw):
+    return [batched_instance(seed, i, **kw) for i in range(n_instances)]
+
+
+def served_job(seed: int, index: int, g_lo: int = 5_000, g_hi: int = 5_000_000,
+               coverage: float = 10.0, read_len: int = 150, min_overlap: int = 41):
+    rng = rng_for(seed * 1_000_003 + index, 4)
+    G = log_uniform(rng, g_lo, g_hi)
+    genome = genome_with_repeats(rng, G, 0.02, (2, 50), (10, 200))
+    reads, starts = shotgun(rng, genome, coverage, read_len, read_len)
+    return dict(genome=genome, reads=reads, starts=starts, text=join_reads(reads),
+                min_overlap=min_overlap)
+
+
+def sa64m_genome(seed: int, G: int = 64_000_000) -> np.ndarray:
+    rng = rng_for(seed, 2)
+    return genome_with_repeats(rng, G, 0.05, (2, 50), (10, 200), 0.05, 300, 0.01)
+
+
+def large_genome(seed: int, G: int = 1_500_000_000) -> np.ndarray:
+    rng = rng_for(seed, 5)
+    return genome_with_repeats(rng, G, 0.10, (2, 100), (10, 200), 0.05, 6000, 0.005)
+
+
+def large_reads(seed: int, genome: np.ndarray, n_reads: int = 10_000_000, read_len: int = 150):
+    """n_reads fragments of read_len at uniform starts, as one '$'-joined text."""
+    rng = rng_for(seed, 6)
+    starts = rng.integers(0, genome.size - read_len + 1, size=n_reads)
+    idx = starts[:, None] + np.arange(read_len)[None, :]
+    body = genome[idx]
+    text = np.empty((n_reads, read_len + 1), dtype=np.uint8)
+    text[:, :read_len] = body
+    text[:, read_len] = SEP
+    return text.ravel(), starts
