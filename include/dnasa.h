@@ -1,0 +1,177 @@
+/*
+ * dnasa.h -- C ABI of the GB300 suffix-array DNA reconstruction library
+ * (libdnasa.so).  Method: arxiv 1404.3456, "A Way For Accelerating The DNA
+ * Sequence Reconstruction Problem By CUDA".
+ *
+ * The library reconstructs a DNA sequence from shotgun fragments (Sec. III)
+ * through a suffix array over the fragments (Sec. IV), built on the GPU by
+ * radix sorting (Sec. IV, Algorithm 1 in Sec. V), then answers the
+ * prefix/suffix relations between fragments by searching that suffix array
+ * (Sec. IV, "binary search ... whether one fragment is the prefix of X").
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Text.  Fragments over {A,C,G,T} are joined into one byte text T[0..N); each
+ *   fragment is followed by one '$'.  A single genome is one fragment.
+ *   Fragment r occupies T[toff[r] .. toff[r+1]-1); toff[n_reads] == N.
+ * Order.  Every '$' is its own sentinel, smaller than A < C < G < T; two
+ *   suffixes that reach a '$' at the same offset order by start position.  No
+ *   comparison and no LCP ever crosses a '$'.
+ * Packed form.  Bases only ('$' not stored), 2 bits each (A=0 C=1 G=2 T=3),
+ *   32 per uint64 word, first base in bits 63..62 of word 0, so an unsigned
+ *   word compare is a lexicographic compare.  The bases of fragment r occupy
+ *   base coordinates [toff[r] - r, toff[r+1] - 1 - r).  A packed buffer holds
+ *   dnasa_packed_words(N) words (two zero padding words at the end).
+ * Memory.  Every buffer argument is a DEVICE pointer (for example from
+ *   torch.empty(..., device="cuda")) unless its comment says "host".  The
+ *   caller owns all inputs and outputs; the library owns only the workspace
+ *   inside its context.  A host pointer where a device pointer is required is
+ *   rejected with DNASA_INVALID_ARG: there is no CPU fallback.
+ * Streams.  Work is enqueued on the caller's stream (a cudaStream_t passed as
+ *   void*; NULL = the legacy default stream).  Entry points that return a
+ *   size through a host pointer synchronize that stream before returning.
+ * Errors.  Every function returns a dnasa_status; the text of the last error
+ *   is available from dnasa_last_error().  Device-side waits are bounded: a
+ *   wait that gives up yields DNASA_DEVICE_TIMEOUT and leaves the context
+ *   usable.
+ * Index width.  idx_width is DNASA_I32 (int32 SA) or DNASA_I64 (int64 SA).
+ */
+#ifndef DNASA_H
+#define DNASA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DNASA_OK = 0,
+    DNASA_INVALID_ARG = -1,    /* bad size, null or non-device pointer, bad option */
+    DNASA_BAD_ALPHABET = -2,   /* a byte other than A, C, G, T, '$'; or text not '$'-terminated;
+                                  or an empty fragment */
+    DNASA_OOM = -3,            /* workspace could not be allocated (or exceeds the cap) */
+    DNASA_CAPACITY = -4,       /* an output buffer is too small; the size needed is returned */
+    DNASA_DEVICE_TIMEOUT = -5, /* a bounded device-side wait gave up */
+    DNASA_CUDA_ERROR = -6      /* a CUDA runtime call failed */
+} dnasa_status;
+
+enum { DNASA_I32 = 4, DNASA_I64 = 8 };
+
+typedef struct dnasa_ctx dnasa_ctx;
+
+/* Options of the suffix-array build.  Zero in any field selects the default. */
+typedef struct {
+    int32_t digit_bits;        /* radix digit width of the LSD passes: 8 (default) */
+    int32_t tile_items;        /* items per onesweep tile: 3840 (default); other: 1920, 7680 */
+    int64_t finish_threshold;  /* when the suffixes still unsorted after a doubling round
+                                  number at most this many, and every unsorted group has at
+                                  most 1024 members, the rest is sorted by direct comparison
+                                  of packed words; -1 = never; 0 = default */
+    int32_t max_rounds;        /* safety bound on doubling rounds (default 64) */
+    int32_t reserved;
+} dnasa_opts;
+
+/* One suffix-prefix overlap: the last L bases of fragment j equal the first L
+ * bases of fragment k (Sec. III "fir" relation, generalised). */
+typedef struct {
+    int32_t j, k, L;
+} dnasa_edge;
+
+/* Per-round trace of the last sa_build on a context (host-readable). */
+typedef struct {
+    int32_t rounds;            /* doubling rounds run after the initial sort */
+    int32_t finished_direct;   /* 1 if the direct-comparison finisher ran */
+    int32_t h0;                /* symbols in the initial packed key */
+    int32_t reserved;
+    int64_t active[64];        /* unsorted suffixes after the initial sort and each round */
+} dnasa_trace;
+
+/* ---- context --------------------------------------------------------------- */
+
+/* Creates a context on CUDA device `device`.  workspace_cap bounds the device
+ * workspace in bytes (0 = no bound).  *out receives the context (host). */
+int dnasa_create(int device, size_t workspace_cap, dnasa_ctx **out);
+void dnasa_destroy(dnasa_ctx *ctx);
+/* Text of the last error on this context (never NULL; "" when none). */
+const char *dnasa_last_error(dnasa_ctx *ctx);
+/* Synchronizes `stream` and returns the status recorded by device code since
+ * the last call (DNASA_OK or DNASA_DEVICE_TIMEOUT); clears it. */
+int dnasa_sync_status(dnasa_ctx *ctx, void *stream);
+/* Trace of the last sa_build (host struct, copied out). */
+int dnasa_get_trace(dnasa_ctx *ctx, dnasa_trace *out);
+/* Words a packed buffer for an N-symbol text needs (bases / 32 rounded up, + 2). */
+int64_t dnasa_packed_words(int64_t N);
+
+/* ---- S1: pack (Sec. III alphabet; the SA of Sec. IV is over this text) ------- */
+
+/* Validates text[0..N) and writes its packed form and fragment offsets.
+ *   text      device, N bytes of A/C/G/T/'$', last byte '$', no empty fragment
+ *   packed    device, dnasa_packed_words(N) uint64 words (written entirely)
+ *   toff      device, toff_cap int64 entries; receives n_reads + 1 offsets
+ *   n_reads   host out: number of fragments (= number of '$')
+ * Synchronizes the stream.  DNASA_BAD_ALPHABET on a bad byte or empty
+ * fragment; DNASA_CAPACITY when toff_cap < n_reads + 1 (*n_reads still set). */
+int dnasa_pack(dnasa_ctx *ctx, const uint8_t *text, int64_t N, uint64_t *packed,
+               int64_t *toff, int64_t toff_cap, int64_t *n_reads, void *stream);
+
+/* ---- S2-S6: suffix array (Sec. IV "sorted array Pos of all the suffixes") ---- */
+
+/* Builds the suffix array of the packed text by prefix doubling: packed 29-mer
+ * initial keys, then rounds that radix sort (rank[i], rank[i+h]) pairs of the
+ * still-unsorted suffixes, with an optional direct-comparison finisher.
+ *   packed, toff   as written by dnasa_pack (toff: n_reads + 1 entries)
+ *   N              text length including every '$' (N >= 1, N < 2^31)
+ *   sa             device, N entries of int32 or int64 (idx_width): sa[j] is
+ *                  the text position of the j-th smallest suffix
+ *   opts           host, may be NULL (defaults)
+ * Enqueues on the stream and synchronizes it once per doubling round. */
+int sa_build(dnasa_ctx *ctx, const uint64_t *packed, const int64_t *toff, int64_t n_reads,
+             int64_t N, void *sa, int idx_width, const dnasa_opts *opts, void *stream);
+
+/* ---- S7: LCP ----------------------------------------------------------------- */
+
+/* lcp[0] = 0; lcp[j] = number of equal bases at the start of suffixes sa[j-1]
+ * and sa[j], stopping at the first '$' of either (a '$' never matches).
+ *   lcp  device, N int32.  Enqueues only (no synchronization). */
+int lcp_build(dnasa_ctx *ctx, const uint64_t *packed, const int64_t *toff, int64_t n_reads,
+              int64_t N, const void *sa, int idx_width, int32_t *lcp, void *stream);
+
+/* ---- S8-S9: overlap search + containment (Sec. III "fir", Sec. IV search) ----- */
+
+/* For every fragment j and every suffix X of it with min_overlap <= |X| < |r_j|,
+ * finds the fragments k != j whose first |X| bases equal X and |X| < |r_k|,
+ * keeping for each ordered pair (j, k) the largest such L = |X|.  Edges are
+ * written in (j, k) order.  contained[k] = 1 when fragment k occurs inside
+ * another fragment (of two identical fragments, the larger index is marked).
+ *   sa, lcp     as written by sa_build / lcp_build for the same text
+ *   edges       device, cap entries
+ *   n_edges     host out: number of edges (also when > cap)
+ *   contained   device, n_reads bytes
+ * Synchronizes the stream.  DNASA_CAPACITY when the edges exceed cap. */
+int overlap_search(dnasa_ctx *ctx, const uint64_t *packed, const int64_t *toff, int64_t n_reads,
+                   int64_t N, const void *sa, const int32_t *lcp, int idx_width,
+                   int32_t min_overlap, dnasa_edge *edges, int64_t cap, int64_t *n_edges,
+                   uint8_t *contained, void *stream);
+
+/* ---- S10: whole method on one fragment set (Sec. III, Fig. 3 -> superstring) -- */
+
+/* text -> pack -> SA -> LCP -> overlaps -> greedy layout -> contigs.  Greedy:
+ * edges between non-contained fragments in order of (L desc, j asc, k asc);
+ * (j, k) is accepted when j has no successor, k no predecessor and they lie on
+ * different chains.  Each chain head (no predecessor, ascending index) starts
+ * a contig: the head, then each successor without its first L bases.
+ *   text        device, N bytes (as for dnasa_pack)
+ *   contigs     device, cap bytes: the contigs one after another (ASCII ACGT)
+ *   contig_off  device, off_cap int64: contig c = contigs[off[c] .. off[c+1])
+ *   n_contigs   host out;  needed  host out: bytes the contigs need
+ * Synchronizes the stream.  DNASA_CAPACITY when cap or off_cap is too small. */
+int assemble(dnasa_ctx *ctx, const uint8_t *text, int64_t N, int32_t min_overlap,
+             uint8_t *contigs, int64_t cap, int64_t *contig_off, int64_t off_cap,
+             int64_t *n_contigs, int64_t *needed, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DNASA_H */

@@ -1,0 +1,225 @@
+"""Thin Python binding of libdnasa.so (the C ABI in include/dnasa.h).
+
+Argument marshalling only: every function here passes torch tensors'
+``data_ptr()`` and the current CUDA stream to the C entry point of the same
+name and raises :class:`DnasaError` on a non-zero status.  Every step of the
+path runs in the library's CUDA kernels; there is no CPU fallback, and a
+missing library is an ImportError-like failure on first use, not a silent
+substitute.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdnasa.so")
+
+OK, INVALID_ARG, BAD_ALPHABET, OOM, CAPACITY, DEVICE_TIMEOUT, CUDA_ERROR = 0, -1, -2, -3, -4, -5, -6
+I32, I64 = 4, 8
+_NAMES = {0: "OK", -1: "INVALID_ARG", -2: "BAD_ALPHABET", -3: "OOM", -4: "CAPACITY",
+          -5: "DEVICE_TIMEOUT", -6: "CUDA_ERROR"}
+
+
+class DnasaError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("digit_bits", ctypes.c_int32), ("tile_items", ctypes.c_int32),
+                ("finish_threshold", ctypes.c_int64), ("max_rounds", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class Trace(ctypes.Structure):
+    _fields_ = [("rounds", ctypes.c_int32), ("finished_direct", ctypes.c_int32),
+                ("h0", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("active", ctypes.c_int64 * 64)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+# name -> (restype, argtypes)
+_P, _I64, _I32, _INT = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_int
+_SIGS = {
+    "dnasa_create": (_INT, [_INT, ctypes.c_size_t, ctypes.POINTER(_P)]),
+    "dnasa_destroy": (None, [_P]),
+    "dnasa_last_error": (ctypes.c_char_p, [_P]),
+    "dnasa_sync_status": (_INT, [_P, _P]),
+    "dnasa_get_trace": (_INT, [_P, ctypes.POINTER(Trace)]),
+    "dnasa_packed_words": (_I64, [_I64]),
+    "dnasa_pack": (_INT, [_P, _P, _I64, _P, _P, _I64, ctypes.POINTER(_I64), _P]),
+    "sa_build": (_INT, [_P, _P, _P, _I64, _I64, _P, _INT, ctypes.POINTER(Opts), _P]),
+    "lcp_build": (_INT, [_P, _P, _P, _I64, _I64, _P, _INT, _P, _P]),
+    "overlap_search": (_INT, [_P, _P, _P, _I64, _I64, _P, _P, _INT, _I32, _P, _I64,
+                              ctypes.POINTER(_I64), _P, _P]),
+    "assemble": (_INT, [_P, _P, _I64, _I32, _P, _I64, _P, _I64, ctypes.POINTER(_I64),
+                        ctypes.POINTER(_I64), _P]),
+}
+
+
+def lib():
+    """The loaded library; raises if libdnasa.so has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                                   "`python -c 'import __graft_entry__ as g; g.build()'`")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in _SIGS.items():
+                f = getattr(L, name, None)
+                if f is None:
+                    continue
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("expected a torch tensor")
+    if not t.is_cuda:
+        raise ValueError("tensor must live on a CUDA device (no CPU fallback)")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Context:
+    """Owns a dnasa_ctx (its device workspace) on one CUDA device."""
+
+    def __init__(self, device: int = 0, workspace_cap: int = 0):
+        self.device = device
+        h = ctypes.c_void_p()
+        torch.cuda.init()
+        rc = lib().dnasa_create(device, workspace_cap, ctypes.byref(h))
+        if rc != 0:
+            raise DnasaError(rc, "dnasa_create failed")
+        self.handle = h
+
+    def check(self, rc: int):
+        if rc != 0:
+            raise DnasaError(rc, lib().dnasa_last_error(self.handle).decode())
+
+    def trace(self) -> dict:
+        tr = Trace()
+        self.check(lib().dnasa_get_trace(self.handle, ctypes.byref(tr)))
+        return dict(rounds=tr.rounds, finished_direct=tr.finished_direct, h0=tr.h0,
+                    active=list(tr.active[: tr.rounds + 1]))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().dnasa_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def make_opts(digit_bits=0, tile_items=0, finish_threshold=0, max_rounds=0):
+    return Opts(digit_bits, tile_items, finish_threshold, max_rounds, 0)
+
+
+# ---------------------------------------------------------------- entry points
+
+
+def packed_words(N: int) -> int:
+    return int(lib().dnasa_packed_words(N))
+
+
+def dnasa_pack(ctx: Context, text, packed, toff, stream=None) -> int:
+    n = ctypes.c_int64(0)
+    ctx.check(lib().dnasa_pack(ctx.handle, _ptr(text), text.numel(), _ptr(packed), _ptr(toff),
+                               toff.numel(), ctypes.byref(n), _stream(stream)))
+    return n.value
+
+
+def sa_build(ctx: Context, packed, toff, n_reads: int, N: int, sa, opts: Opts | None = None,
+             stream=None):
+    width = I64 if sa.dtype == torch.int64 else I32
+    ctx.check(lib().sa_build(ctx.handle, _ptr(packed), _ptr(toff), n_reads, N, _ptr(sa), width,
+                             ctypes.byref(opts) if opts is not None else None, _stream(stream)))
+
+
+def lcp_build(ctx: Context, packed, toff, n_reads: int, N: int, sa, lcp, stream=None):
+    width = I64 if sa.dtype == torch.int64 else I32
+    ctx.check(lib().lcp_build(ctx.handle, _ptr(packed), _ptr(toff), n_reads, N, _ptr(sa), width,
+                              _ptr(lcp), _stream(stream)))
+
+
+def overlap_search(ctx: Context, packed, toff, n_reads: int, N: int, sa, lcp, min_overlap: int,
+                   edges, contained, stream=None) -> int:
+    """edges: int32 tensor (cap, 3) of (j, k, L).  Returns the edge count."""
+    width = I64 if sa.dtype == torch.int64 else I32
+    n = ctypes.c_int64(0)
+    cap = edges.shape[0] if edges is not None else 0
+    ctx.check(lib().overlap_search(ctx.handle, _ptr(packed), _ptr(toff), n_reads, N, _ptr(sa),
+                                   _ptr(lcp), width, min_overlap,
+                                   _ptr(edges) if cap else None, cap, ctypes.byref(n),
+                                   _ptr(contained), _stream(stream)))
+    return n.value
+
+
+def assemble(ctx: Context, text, min_overlap: int, contigs, contig_off, stream=None):
+    """Returns (n_contigs, bytes)."""
+    nc = ctypes.c_int64(0)
+    need = ctypes.c_int64(0)
+    ctx.check(lib().assemble(ctx.handle, _ptr(text), text.numel(), min_overlap, _ptr(contigs),
+                             contigs.numel(), _ptr(contig_off), contig_off.numel(),
+                             ctypes.byref(nc), ctypes.byref(need), _stream(stream)))
+    return nc.value, need.value
+
+
+# ---------------------------------------------------------------- conveniences
+# (allocate outputs with torch, then call the entry points above)
+
+
+def pack_text(ctx: Context, text: torch.Tensor, stream=None):
+    """text (cuda uint8) -> (packed uint64-as-int64, toff int64, n_reads)."""
+    N = text.numel()
+    dev = text.device
+    packed = torch.empty(packed_words(N), dtype=torch.int64, device=dev)
+    toff = torch.empty(N // 2 + 2, dtype=torch.int64, device=dev)
+    nr = dnasa_pack(ctx, text, packed, toff, stream)
+    return packed, toff[: nr + 1], nr
+
+
+def suffix_array(ctx: Context, text: torch.Tensor, dtype=torch.int32, opts=None, stream=None):
+    packed, toff, nr = pack_text(ctx, text, stream)
+    sa = torch.empty(text.numel(), dtype=dtype, device=text.device)
+    sa_build(ctx, packed, toff, nr, text.numel(), sa, opts, stream)
+    return sa, packed, toff, nr
+
+
+def assemble_text(ctx: Context, text: torch.Tensor, min_overlap: int, stream=None):
+    """Contigs of one fragment text as a list of bytes."""
+    N = text.numel()
+    cap = N
+    contigs = torch.empty(max(cap, 1), dtype=torch.uint8, device=text.device)
+    off = torch.empty(N // 2 + 2, dtype=torch.int64, device=text.device)
+    nc, nb = assemble(ctx, text, min_overlap, contigs, off, stream)
+    buf = contigs[:nb].cpu().numpy().tobytes()
+    o = off[: nc + 1].cpu().tolist()
+    return [buf[o[i]: o[i + 1]] for i in range(nc)]

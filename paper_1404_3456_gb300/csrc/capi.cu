@@ -1,0 +1,235 @@
+// capi.cu -- the extern "C" entry points of the suffix-array path
+// (sa_build, lcp_build, overlap_search, assemble): argument checks, then the
+// stream-ordered pipeline.  Intermediate buffers of assemble() come from the
+// stream-ordered allocator; each step's scratch comes from the context
+// workspace.
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace dnasa {
+
+int layout_impl(dnasa_ctx *ctx, const TextDesc &t, int64_t max_reads_per_inst,
+                const dnasa_edge *edges, int64_t ne, const uint8_t *contained, uint8_t *contigs,
+                int64_t cap, int64_t *contig_off, int64_t off_cap, int64_t *inst_contig_off,
+                int64_t *n_contigs, int64_t *needed, cudaStream_t s);
+
+namespace {
+
+int check_text_args(dnasa_ctx *ctx, const uint64_t *packed, const int64_t *toff, int64_t n_reads,
+                    int64_t N, const char *who) {
+    if (N <= 0 || N >= (int64_t(1) << 31) || n_reads < 1 || n_reads > N)
+        return fail(ctx, DNASA_INVALID_ARG, std::string(who) + ": need 1 <= n_reads <= N < 2^31");
+    if (!is_device_ptr(ctx, packed) || !is_device_ptr(ctx, toff))
+        return fail(ctx, DNASA_INVALID_ARG, std::string(who) + ": packed and toff must be device pointers");
+    return DNASA_OK;
+}
+
+TextDesc one_instance(const uint64_t *packed, const int64_t *toff, int64_t n_reads, int64_t N) {
+    TextDesc t;
+    t.packed = packed;
+    t.toff = toff;
+    t.n_reads = n_reads;
+    t.N = N;
+    t.inst_toff = nullptr;
+    t.inst_roff = nullptr;
+    t.n_inst = 1;
+    return t;
+}
+
+// SA in the caller's width: int32 writes straight into the caller's buffer,
+// int64 goes through a uint32 stage then widens.
+struct SaView {
+    const uint32_t *sa32 = nullptr;
+    uint32_t *owned = nullptr;
+};
+
+// stream-ordered device buffer
+struct DevBuf {
+    void *p = nullptr;
+    cudaStream_t s = nullptr;
+    ~DevBuf() {
+        if (p) cudaFreeAsync(p, s);
+    }
+};
+
+int dev_alloc(dnasa_ctx *ctx, DevBuf &b, size_t bytes, cudaStream_t s) {
+    b.s = s;
+    cudaError_t e = cudaMallocAsync(&b.p, std::max<size_t>(bytes, 256), s);
+    if (e != cudaSuccess) {
+        b.p = nullptr;
+        return cuda_fail(ctx, e, "cudaMallocAsync");
+    }
+    return DNASA_OK;
+}
+
+__global__ void k_narrow(const int64_t *__restrict__ a, int64_t n, uint32_t *__restrict__ b) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = (uint32_t)a[i];
+}
+
+// A uint32 view of a caller SA (narrowing an int64 SA into a temporary).
+int sa_view(dnasa_ctx *ctx, const void *sa, int idx_width, int64_t N, DevBuf &tmp, cudaStream_t s,
+            const uint32_t **out) {
+    if (idx_width == DNASA_I32) {
+        *out = (const uint32_t *)sa;
+        return DNASA_OK;
+    }
+    DNASA_TRY(dev_alloc(ctx, tmp, (size_t)N * 4, s));
+    int grid = (int)std::min<int64_t>(ceil_div(N, 256), (int64_t)ctx->num_sms * 16);
+    k_narrow<<<std::max(grid, 1), 256, 0, s>>>((const int64_t *)sa, N, (uint32_t *)tmp.p);
+    DNASA_CUDA(ctx, cudaGetLastError());
+    *out = (const uint32_t *)tmp.p;
+    return DNASA_OK;
+}
+
+}  // namespace
+
+// Whole pipeline on a text already on the device, possibly several instances.
+int assemble_impl(dnasa_ctx *ctx, const uint8_t *text, int64_t N, const int64_t *inst_toff_host,
+                  int32_t n_inst, int32_t min_overlap, uint8_t *contigs, int64_t cap,
+                  int64_t *contig_off, int64_t off_cap, int64_t *inst_contig_off, int64_t *n_contigs,
+                  int64_t *needed, const dnasa_opts *opts, cudaStream_t s) {
+    DevBuf packed, toff, sa, lcp, contained, edges, inst_toff, inst_roff;
+    const int64_t toff_cap = N / 2 + 2;
+    DNASA_TRY(dev_alloc(ctx, packed, (size_t)dnasa_packed_words(N) * 8, s));
+    DNASA_TRY(dev_alloc(ctx, toff, (size_t)toff_cap * 8, s));
+    int64_t n_reads = 0;
+    DNASA_TRY(pack_impl(ctx, text, N, (uint64_t *)packed.p, (int64_t *)toff.p, toff_cap, &n_reads, s));
+    TextDesc t = one_instance((const uint64_t *)packed.p, (const int64_t *)toff.p, n_reads, N);
+    int64_t max_reads = n_reads;
+    if (n_inst > 1) {
+        // fragment offsets of the instances: the fragment index at each instance start
+        std::vector<int64_t> roff(n_inst + 1);
+        DNASA_TRY(dev_alloc(ctx, inst_toff, (size_t)(n_inst + 1) * 8, s));
+        DNASA_TRY(dev_alloc(ctx, inst_roff, (size_t)(n_inst + 1) * 8, s));
+        DNASA_CUDA(ctx, cudaMemcpyAsync(inst_toff.p, inst_toff_host, (size_t)(n_inst + 1) * 8,
+                                        cudaMemcpyHostToDevice, s));
+        std::vector<int64_t> toff_h((size_t)n_reads + 1);
+        DNASA_CUDA(ctx, cudaMemcpyAsync(toff_h.data(), toff.p, (size_t)(n_reads + 1) * 8,
+                                        cudaMemcpyDeviceToHost, s));
+        DNASA_CUDA(ctx, cudaStreamSynchronize(s));
+        max_reads = 0;
+        for (int i = 0; i <= n_inst; ++i) {
+            auto it = std::lower_bound(toff_h.begin(), toff_h.end(), inst_toff_host[i]);
+            if (it == toff_h.end() || *it != inst_toff_host[i])
+                return fail(ctx, DNASA_INVALID_ARG, "assemble_batched: an instance does not start at a fragment");
+            roff[i] = it - toff_h.begin();
+            if (i > 0) max_reads = std::max(max_reads, roff[i] - roff[i - 1]);
+            if (i > 0 && roff[i] <= roff[i - 1])
+                return fail(ctx, DNASA_INVALID_ARG, "assemble_batched: empty instance");
+        }
+        DNASA_CUDA(ctx, cudaMemcpyAsync(inst_roff.p, roff.data(), (size_t)(n_inst + 1) * 8,
+                                        cudaMemcpyHostToDevice, s));
+        DNASA_CUDA(ctx, cudaStreamSynchronize(s));
+        t.inst_toff = (const int64_t *)inst_toff.p;
+        t.inst_roff = (const int64_t *)inst_roff.p;
+        t.n_inst = n_inst;
+    }
+    DNASA_TRY(dev_alloc(ctx, sa, (size_t)N * 4, s));
+    DNASA_TRY(dev_alloc(ctx, lcp, (size_t)N * 4, s));
+    DNASA_TRY(dev_alloc(ctx, contained, (size_t)n_reads, s));
+    DNASA_TRY(sa_build_u32(ctx, t, (uint32_t *)sa.p, opts, s));
+    DNASA_TRY(lcp_build_impl(ctx, t, (const uint32_t *)sa.p, (int32_t *)lcp.p, s));
+    int64_t ecap = std::max<int64_t>(8 * n_reads, 1024), ne = 0;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+        if (edges.p) { cudaFreeAsync(edges.p, s); edges.p = nullptr; }
+        DNASA_TRY(dev_alloc(ctx, edges, (size_t)ecap * sizeof(dnasa_edge), s));
+        int rc = overlap_impl(ctx, t, (const uint32_t *)sa.p, (const int32_t *)lcp.p, min_overlap,
+                              (dnasa_edge *)edges.p, ecap, &ne, (uint8_t *)contained.p, s);
+        if (rc == DNASA_CAPACITY && attempt == 0) { ecap = ne + 16; continue; }
+        DNASA_TRY(rc);
+        break;
+    }
+    return layout_impl(ctx, t, max_reads, (const dnasa_edge *)edges.p, ne,
+                       (const uint8_t *)contained.p, contigs, cap, contig_off, off_cap,
+                       inst_contig_off, n_contigs, needed, s);
+}
+
+}  // namespace dnasa
+
+using namespace dnasa;
+
+extern "C" {
+
+int sa_build(dnasa_ctx *ctx, const uint64_t *packed, const int64_t *toff, int64_t n_reads,
+             int64_t N, void *sa, int idx_width, const dnasa_opts *opts, void *stream) {
+    if (!ctx) return DNASA_INVALID_ARG;
+    ctx->last_error.clear();
+    DNASA_TRY(check_text_args(ctx, packed, toff, n_reads, N, "sa_build"));
+    if (idx_width != DNASA_I32 && idx_width != DNASA_I64)
+        return fail(ctx, DNASA_INVALID_ARG, "sa_build: idx_width must be DNASA_I32 or DNASA_I64");
+    if (!is_device_ptr(ctx, sa)) return fail(ctx, DNASA_INVALID_ARG, "sa_build: sa must be a device pointer");
+    if (opts && (opts->tile_items != 0 && opts->tile_items != 2048 && opts->tile_items != 3840 &&
+                 opts->tile_items != 5120))
+        return fail(ctx, DNASA_INVALID_ARG, "sa_build: tile_items must be 0, 2048, 3840 or 5120");
+    if (opts && opts->digit_bits != 0 && opts->digit_bits != 8)
+        return fail(ctx, DNASA_INVALID_ARG, "sa_build: digit_bits must be 0 or 8");
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    TextDesc t = one_instance(packed, toff, n_reads, N);
+    if (idx_width == DNASA_I32) return sa_build_u32(ctx, t, (uint32_t *)sa, opts, s);
+    DevBuf tmp;
+    DNASA_TRY(dev_alloc(ctx, tmp, (size_t)N * 4, s));
+    DNASA_TRY(sa_build_u32(ctx, t, (uint32_t *)tmp.p, opts, s));
+    return widen_u32_to_i64(ctx, (const uint32_t *)tmp.p, N, (int64_t *)sa, s);
+}
+
+int lcp_build(dnasa_ctx *ctx, const uint64_t *packed, const int64_t *toff, int64_t n_reads,
+              int64_t N, const void *sa, int idx_width, int32_t *lcp, void *stream) {
+    if (!ctx) return DNASA_INVALID_ARG;
+    ctx->last_error.clear();
+    DNASA_TRY(check_text_args(ctx, packed, toff, n_reads, N, "lcp_build"));
+    if (idx_width != DNASA_I32 && idx_width != DNASA_I64)
+        return fail(ctx, DNASA_INVALID_ARG, "lcp_build: bad idx_width");
+    if (!is_device_ptr(ctx, sa) || !is_device_ptr(ctx, lcp))
+        return fail(ctx, DNASA_INVALID_ARG, "lcp_build: sa and lcp must be device pointers");
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    DevBuf tmp;
+    const uint32_t *sa32;
+    DNASA_TRY(sa_view(ctx, sa, idx_width, N, tmp, s, &sa32));
+    return lcp_build_impl(ctx, one_instance(packed, toff, n_reads, N), sa32, lcp, s);
+}
+
+int overlap_search(dnasa_ctx *ctx, const uint64_t *packed, const int64_t *toff, int64_t n_reads,
+                   int64_t N, const void *sa, const int32_t *lcp, int idx_width,
+                   int32_t min_overlap, dnasa_edge *edges, int64_t cap, int64_t *n_edges,
+                   uint8_t *contained, void *stream) {
+    if (!ctx) return DNASA_INVALID_ARG;
+    ctx->last_error.clear();
+    DNASA_TRY(check_text_args(ctx, packed, toff, n_reads, N, "overlap_search"));
+    if (idx_width != DNASA_I32 && idx_width != DNASA_I64)
+        return fail(ctx, DNASA_INVALID_ARG, "overlap_search: bad idx_width");
+    if (min_overlap < 1 || !n_edges || cap < 0)
+        return fail(ctx, DNASA_INVALID_ARG, "overlap_search: min_overlap >= 1, n_edges and cap >= 0 required");
+    if (!is_device_ptr(ctx, sa) || !is_device_ptr(ctx, lcp) || !is_device_ptr(ctx, contained) ||
+        (cap > 0 && !is_device_ptr(ctx, edges)))
+        return fail(ctx, DNASA_INVALID_ARG, "overlap_search: sa, lcp, edges, contained must be device pointers");
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    DevBuf tmp;
+    const uint32_t *sa32;
+    DNASA_TRY(sa_view(ctx, sa, idx_width, N, tmp, s, &sa32));
+    return overlap_impl(ctx, one_instance(packed, toff, n_reads, N), sa32, lcp, min_overlap, edges,
+                        cap, n_edges, contained, s);
+}
+
+int assemble(dnasa_ctx *ctx, const uint8_t *text, int64_t N, int32_t min_overlap,
+             uint8_t *contigs, int64_t cap, int64_t *contig_off, int64_t off_cap,
+             int64_t *n_contigs, int64_t *needed, void *stream) {
+    if (!ctx) return DNASA_INVALID_ARG;
+    ctx->last_error.clear();
+    if (N <= 0 || N >= (int64_t(1) << 31) || min_overlap < 1 || !n_contigs || !needed ||
+        cap < 0 || off_cap < 1)
+        return fail(ctx, DNASA_INVALID_ARG, "assemble: bad size, min_overlap or null output");
+    if (!is_device_ptr(ctx, text) || !is_device_ptr(ctx, contig_off) ||
+        (cap > 0 && !is_device_ptr(ctx, contigs)))
+        return fail(ctx, DNASA_INVALID_ARG, "assemble: text, contigs and contig_off must be device pointers");
+    cudaSetDevice(ctx->device);
+    return assemble_impl(ctx, text, N, nullptr, 1, min_overlap, contigs, cap, contig_off, off_cap,
+                         nullptr, n_contigs, needed, nullptr, (cudaStream_t)stream);
+}
+
+}  // extern "C"

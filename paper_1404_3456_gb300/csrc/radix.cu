@@ -1,0 +1,411 @@
+// radix.cu -- stable LSD radix sort of (key, value) pairs, onesweep style.
+//
+// Sec. IV of the paper sorts suffix keys with an LSD radix sort whose passes
+// rank each element as "elements in lower buckets + elements already in the
+// same bucket" (after Satish et al.), built from split/scan/scatter kernels on
+// shared-memory chunks (Algorithm 1).  This is the same sort, re-planned for
+// sm_103a:
+//   * one histogram kernel reads the keys once and counts every digit of every
+//     pass (8-bit digits; warp __match_any_sync aggregation before the shared
+//     atomics, so runs of equal digits cost one atomic per warp);
+//   * then one kernel per digit.  Each CTA takes the next tile id from an
+//     atomic counter, ranks its tile's digits in shared memory (per-warp
+//     match_any ranking), publishes its per-digit counts, and looks back over
+//     its predecessors' published counts (decoupled look-back) to find its
+//     global output offsets; the scatter goes through shared memory so that
+//     each digit's run leaves as a contiguous burst.  Every spin on a
+//     predecessor is bounded: on time-out the CTA sets DERR_TIMEOUT, publishes
+//     an (invalid) inclusive prefix so that no successor waits on it, and the
+//     host reports DNASA_DEVICE_TIMEOUT.
+// Look-back words live in a status buffer owned by the context; each pass
+// stamps its words with an 8-bit epoch so that the buffer is zeroed only when
+// the epoch wraps.
+#include "common.cuh"
+
+namespace dnasa {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kRadixBits = 8;
+constexpr int kRadix = 1 << kRadixBits;
+constexpr int kWarps = kThreads / 32;
+
+// look-back word: [63:62] flag, [61:54] epoch, [53:0] count
+constexpr unsigned long long FLAG_AGG = 1ull << 62;
+constexpr unsigned long long FLAG_INC = 2ull << 62;
+constexpr unsigned long long VAL_MASK = (1ull << 54) - 1;
+
+__device__ __forceinline__ unsigned long long lb_word(unsigned long long flag, uint32_t epoch,
+                                                      unsigned long long v) {
+    return flag | ((unsigned long long)(epoch & 0xFF) << 54) | (v & VAL_MASK);
+}
+
+template <typename K>
+__device__ __forceinline__ uint32_t digit_of(K k, int shift) {
+    return (uint32_t)(k >> shift) & (kRadix - 1);
+}
+
+// ------------------------------------------------------------------ histogram
+template <typename K>
+__global__ void __launch_bounds__(kThreads) k_hist(const K *__restrict__ keys, int64_t n_host,
+                                                   const unsigned long long *__restrict__ d_n,
+                                                   int passes, uint32_t *__restrict__ ghist) {
+    __shared__ uint32_t sh[8 * kRadix];
+    for (int i = threadIdx.x; i < passes * kRadix; i += kThreads) sh[i] = 0;
+    __syncthreads();
+    const int64_t n = d_n ? (int64_t)*d_n : n_host;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp_global = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * kThreads) >> 5;
+    for (int64_t base = warp_global * 32; base < n; base += nwarps * 32) {
+        int64_t i = base + lane;
+        bool valid = i < n;
+        uint32_t vmask = __ballot_sync(0xffffffffu, valid);
+        if (valid) {
+            K k = keys[i];
+            for (int p = 0; p < passes; ++p) {
+                uint32_t d = digit_of(k, p * kRadixBits);
+                uint32_t peers = __match_any_sync(vmask, d);
+                if (lane == __ffs(peers) - 1) atomicAdd(&sh[p * kRadix + d], __popc(peers));
+            }
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < passes * kRadix; i += kThreads) {
+        uint32_t c = sh[i];
+        if (c) atomicAdd(&ghist[i], c);
+    }
+}
+
+// exclusive scan of one 256-bin histogram per block (block = pass)
+__global__ void __launch_bounds__(kRadix) k_hist_scan(uint32_t *__restrict__ ghist) {
+    __shared__ uint32_t wsum[kRadix / 32];
+    uint32_t *h = ghist + blockIdx.x * kRadix;
+    uint32_t v = h[threadIdx.x];
+    uint32_t x = v;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    uint32_t off = 0;
+    for (int i = 0; i < w; ++i) off += wsum[i];
+    h[threadIdx.x] = off + x - v;
+}
+
+// ------------------------------------------------------------------ one digit pass
+template <typename K, int ITEMS, bool HAS_VALS>
+__global__ void __launch_bounds__(kThreads) k_onesweep(
+    const K *__restrict__ kin, const uint32_t *__restrict__ vin, K *__restrict__ kout,
+    uint32_t *__restrict__ vout, const uint32_t *__restrict__ bucket, unsigned long long *status,
+    uint32_t *tile_ctr, int64_t n_host, const unsigned long long *__restrict__ d_n, int shift,
+    uint32_t epoch, uint32_t *err) {
+    constexpr int TILE = kThreads * ITEMS;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    K *s_keys = reinterpret_cast<K *>(smem_raw);
+    uint32_t *s_vals = reinterpret_cast<uint32_t *>(s_keys + TILE);
+    uint32_t *s_whist = s_vals + (HAS_VALS ? TILE : 0);          // [kWarps][kRadix]
+    uint32_t *s_count = s_whist + kWarps * kRadix;                // [kRadix]
+    uint32_t *s_start = s_count + kRadix;                         // [kRadix] tile-local start
+    uint32_t *s_gbase = s_start + kRadix;                         // [kRadix] global base - start
+    uint32_t *s_misc = s_gbase + kRadix;                          // [kWarps + 2]
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) {
+        s_misc[kWarps] = atomicAdd(tile_ctr, 1u);
+        s_misc[kWarps + 1] = 0;   // set when a look-back gave up: skip the scatter
+    }
+    for (int i = tid; i < kWarps * kRadix; i += kThreads) s_whist[i] = 0;
+    __syncthreads();
+    const uint32_t tile = s_misc[kWarps];
+    const int64_t n = d_n ? (int64_t)*d_n : n_host;
+    const int64_t base = (int64_t)tile * TILE;
+    if (base >= n) return;   // uniform over the CTA; later tiles are empty too
+    const int tile_n = (int)min((int64_t)TILE, n - base);
+
+    // ---- load (warp-striped: warp w owns [w*32*ITEMS, (w+1)*32*ITEMS) of the tile)
+    K key[ITEMS];
+    uint16_t lrank[ITEMS];
+    const int wbase = warp * 32 * ITEMS;
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        int idx = wbase + i * 32 + lane;
+        key[i] = idx < tile_n ? kin[base + idx] : K(0);
+    }
+    // ---- rank within the warp, item by item (keeps tile order: stable)
+    uint32_t *wh = s_whist + warp * kRadix;
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        int idx = wbase + i * 32 + lane;
+        bool valid = idx < tile_n;
+        uint32_t vmask = __ballot_sync(0xffffffffu, valid);
+        lrank[i] = 0;
+        if (valid) {
+            uint32_t d = digit_of(key[i], shift);
+            uint32_t peers = __match_any_sync(vmask, d);
+            int leader = __ffs(peers) - 1;
+            uint32_t old = 0;
+            if (lane == leader) {
+                old = wh[d];
+                wh[d] = old + __popc(peers);
+            }
+            old = __shfl_sync(peers, old, leader);
+            lrank[i] = (uint16_t)(old + __popc(peers & lanemask_lt()));
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+    // ---- per digit: exclusive scan over warps, tile count
+    for (int d = tid; d < kRadix; d += kThreads) {
+        uint32_t run = 0;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) {
+            uint32_t c = s_whist[w * kRadix + d];
+            s_whist[w * kRadix + d] = run;
+            run += c;
+        }
+        s_count[d] = run;
+    }
+    __syncthreads();
+    // ---- publish, look back, and form the global base of each digit
+    for (int d = tid; d < kRadix; d += kThreads) {
+        uint32_t c = s_count[d];
+        unsigned long long *my = status + (size_t)tile * kRadix + d;
+        unsigned long long excl = 0;
+        if (tile == 0) {
+            st_relaxed_u64(my, lb_word(FLAG_INC, epoch, c));
+        } else {
+            st_relaxed_u64(my, lb_word(FLAG_AGG, epoch, c));
+            int64_t t = (int64_t)tile - 1;
+            uint32_t spins = 0;
+            bool gave_up = false;
+            while (t >= 0) {
+                unsigned long long w = ld_relaxed_u64(status + (size_t)t * kRadix + d);
+                uint32_t we = (uint32_t)(w >> 54) & 0xFF;
+                unsigned long long flag = w & (3ull << 62);
+                if (flag == 0 || we != (epoch & 0xFF)) {
+                    if (++spins > kSpinLimit || ((spins & 1023) == 0 && ld_relaxed_u32(err) != 0)) {
+                        gave_up = true;
+                        break;
+                    }
+                    __nanosleep(32);
+                    continue;
+                }
+                excl += w & VAL_MASK;
+                if (flag == FLAG_INC) break;
+                --t;
+            }
+            if (gave_up) {
+                atomicOr(err, DERR_TIMEOUT);
+                s_misc[kWarps + 1] = 1;
+            }
+            st_relaxed_u64(my, lb_word(FLAG_INC, epoch, excl + c));
+        }
+        s_gbase[d] = bucket[d] + (uint32_t)excl;
+    }
+    // ---- tile-local exclusive scan of the digit counts (kThreads == kRadix)
+    {
+        uint32_t v = s_count[tid];
+        uint32_t x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        if (lane == 31) s_misc[warp] = x;
+        __syncthreads();
+        uint32_t off = 0;
+        for (int w = 0; w < warp; ++w) off += s_misc[w];
+        s_start[tid] = off + x - v;
+    }
+    __syncthreads();
+    if (s_misc[kWarps + 1]) return;   // offsets unknown: write nothing
+    // ---- scatter keys into shared memory in digit order
+    uint16_t lpos[ITEMS];
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        int idx = wbase + i * 32 + lane;
+        lpos[i] = 0;
+        if (idx < tile_n) {
+            uint32_t d = digit_of(key[i], shift);
+            uint32_t p = s_start[d] + s_whist[warp * kRadix + d] + lrank[i];
+            lpos[i] = (uint16_t)p;
+            s_keys[p] = key[i];
+        }
+    }
+    __syncthreads();
+    if (tid < kRadix) s_gbase[tid] -= s_start[tid];
+    __syncthreads();
+    for (int idx = tid; idx < tile_n; idx += kThreads) {
+        K k = s_keys[idx];
+        uint32_t o = s_gbase[digit_of(k, shift)] + (uint32_t)idx;
+        if (o < (uint64_t)n) kout[o] = k;
+        else atomicOr(err, DERR_BOUNDS);
+    }
+    if (HAS_VALS) {
+#pragma unroll
+        for (int i = 0; i < ITEMS; ++i) {
+            int idx = wbase + i * 32 + lane;
+            if (idx < tile_n) s_vals[lpos[i]] = vin[base + idx];
+        }
+        __syncthreads();
+        for (int idx = tid; idx < tile_n; idx += kThreads) {
+            K k = s_keys[idx];
+            uint32_t o = s_gbase[digit_of(k, shift)] + (uint32_t)idx;
+            if (o < (uint64_t)n) vout[o] = s_vals[idx];
+        }
+    }
+}
+
+template <typename K, int ITEMS, bool HAS_VALS>
+size_t onesweep_smem() {
+    constexpr int TILE = kThreads * ITEMS;
+    return (size_t)TILE * sizeof(K) + (HAS_VALS ? (size_t)TILE * 4 : 0) +
+           (size_t)(kWarps * kRadix + 3 * kRadix + kWarps + 2) * 4;
+}
+
+template <typename K, int ITEMS, bool HAS_VALS>
+cudaError_t launch_pass(int tiles, cudaStream_t s, const K *kin, const uint32_t *vin, K *kout,
+                        uint32_t *vout, const uint32_t *bucket, unsigned long long *status,
+                        uint32_t *tile_ctr, int64_t n_host, const unsigned long long *d_n,
+                        int shift, uint32_t epoch, uint32_t *err) {
+    size_t smem = onesweep_smem<K, ITEMS, HAS_VALS>();
+    auto kern = k_onesweep<K, ITEMS, HAS_VALS>;
+    static bool configured = false;  // per instantiation; same value on every device
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    kern<<<tiles, kThreads, smem, s>>>(kin, vin, kout, vout, bucket, status, tile_ctr, n_host,
+                                       d_n, shift, epoch, err);
+    return cudaGetLastError();
+}
+
+int items_for_tile(int tile_items) {
+    switch (tile_items) {
+        case 2048: return 8;
+        case 5120: return 20;
+        default: return 15;
+    }
+}
+
+}  // namespace
+
+int radix_tile_default() { return 3840; }
+
+size_t radix_scratch_bytes(int64_t n_max, int key_bits, int tile_items) {
+    int passes = (key_bits + kRadixBits - 1) / kRadixBits;
+    (void)n_max; (void)tile_items;
+    return ((size_t)passes * kRadix * 4 + 255) & ~size_t(255);
+}
+
+RadixScratch radix_scratch_take(Arena &a, int64_t n_max, int key_bits, int tile_items) {
+    (void)n_max; (void)tile_items;
+    RadixScratch rs;
+    int passes = (key_bits + kRadixBits - 1) / kRadixBits;
+    rs.hist = a.take<uint32_t>((size_t)passes * kRadix);
+    return rs;
+}
+
+// Look-back status buffer of the context: grown on demand, zeroed on growth and
+// when the 8-bit epoch wraps.
+static int lb_prepare(dnasa_ctx *ctx, size_t words, cudaStream_t s, unsigned long long **buf,
+                      uint32_t *epoch) {
+    if (ctx->lb_words < words) {
+        if (ctx->lb_buf) {
+            cudaStreamSynchronize(s);
+            cudaFree(ctx->lb_buf);
+            ctx->lb_buf = nullptr;
+        }
+        size_t w = words + words / 4 + 4096;
+        cudaError_t e = cudaMalloc(&ctx->lb_buf, w * 8);
+        if (e != cudaSuccess) {
+            ctx->lb_words = 0;
+            ctx->lb_buf = nullptr;
+            return cuda_fail(ctx, e, "look-back status alloc");
+        }
+        ctx->lb_words = w;
+        DNASA_CUDA(ctx, cudaMemsetAsync(ctx->lb_buf, 0, w * 8, s));
+        ctx->lb_epoch = 0;
+    }
+    if (++ctx->lb_epoch > 255) {
+        DNASA_CUDA(ctx, cudaMemsetAsync(ctx->lb_buf, 0, ctx->lb_words * 8, s));
+        ctx->lb_epoch = 1;
+    }
+    *buf = ctx->lb_buf;
+    *epoch = ctx->lb_epoch;
+    return DNASA_OK;
+}
+
+template <typename K>
+int radix_sort_pairs(dnasa_ctx *ctx, const RadixScratch &rs, K *keys[2], uint32_t *vals[2],
+                     int64_t n_host, const unsigned long long *d_n, int key_bits, bool hist_ready,
+                     int tile_items, int *which, cudaStream_t s) {
+    *which = 0;
+    if (n_host <= 0) return DNASA_OK;
+    if (key_bits > (int)(8 * sizeof(K))) return fail(ctx, DNASA_INVALID_ARG, "radix: key_bits");
+    const int passes = (key_bits + kRadixBits - 1) / kRadixBits;
+    if (passes > 8) return fail(ctx, DNASA_INVALID_ARG, "radix: too many passes");
+    const int items = items_for_tile(tile_items);
+    const int tile = kThreads * items;
+    const int tiles = ceil_div(n_host, tile);
+    const bool has_vals = vals && vals[0] && vals[1];
+    if (!hist_ready) {
+        DNASA_CUDA(ctx, cudaMemsetAsync(rs.hist, 0, (size_t)passes * kRadix * 4, s));
+        int grid = (int)std::min<int64_t>((int64_t)ctx->num_sms * 8, ceil_div(n_host, kThreads * 8));
+        if (grid < 1) grid = 1;
+        k_hist<K><<<grid, kThreads, 0, s>>>(keys[0], n_host, d_n, passes, rs.hist);
+        DNASA_CUDA(ctx, cudaGetLastError());
+    }
+    k_hist_scan<<<passes, kRadix, 0, s>>>(rs.hist);
+    DNASA_CUDA(ctx, cudaGetLastError());
+    DNASA_CUDA(ctx, cudaMemsetAsync(ctx->ctrl->tile_ctr, 0, sizeof(uint32_t) * 8, s));
+    int cur = 0;
+    for (int p = 0; p < passes; ++p) {
+        unsigned long long *status;
+        uint32_t epoch;
+        DNASA_TRY(lb_prepare(ctx, (size_t)tiles * kRadix, s, &status, &epoch));
+        const K *kin = keys[cur];
+        K *kout = keys[cur ^ 1];
+        const uint32_t *vin = has_vals ? vals[cur] : nullptr;
+        uint32_t *vout = has_vals ? vals[cur ^ 1] : nullptr;
+        cudaError_t e;
+#define DNASA_PASS(IT, HV)                                                                    \
+    e = launch_pass<K, IT, HV>(tiles, s, kin, vin, kout, vout, rs.hist + p * kRadix, status, \
+                               ctx->ctrl->tile_ctr + p, n_host, d_n, p * kRadixBits, epoch,  \
+                               &ctx->ctrl->err)
+        if (has_vals) {
+            if (items == 8) DNASA_PASS(8, true);
+            else if (items == 20) DNASA_PASS(20, true);
+            else DNASA_PASS(15, true);
+        } else {
+            if (items == 8) DNASA_PASS(8, false);
+            else if (items == 20) DNASA_PASS(20, false);
+            else DNASA_PASS(15, false);
+        }
+#undef DNASA_PASS
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "onesweep pass");
+        cur ^= 1;
+    }
+    *which = cur;
+    return DNASA_OK;
+}
+
+template int radix_sort_pairs<uint32_t>(dnasa_ctx *, const RadixScratch &, uint32_t *[2],
+                                        uint32_t *[2], int64_t, const unsigned long long *, int,
+                                        bool, int, int *, cudaStream_t);
+template int radix_sort_pairs<unsigned long long>(dnasa_ctx *, const RadixScratch &,
+                                                  unsigned long long *[2], uint32_t *[2], int64_t,
+                                                  const unsigned long long *, int, bool, int,
+                                                  int *, cudaStream_t);
+
+// Histogram accumulation entry used by fused producers: nothing here; the
+// producer kernels call radix_digit_count() below.
+
+}  // namespace dnasa

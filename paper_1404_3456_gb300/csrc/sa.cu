@@ -1,0 +1,462 @@
+// sa.cu -- suffix array by prefix doubling over the 2-bit packed text (S2-S6).
+//
+// Sec. IV of the paper builds the suffix array "Pos" by radix sorting suffix
+// keys on the GPU.  Here the keys are:
+//   round 0   (kmer, lc): the first h0 bases of the suffix packed 2 bits each
+//             (zero past the fragment end) and lc = min(bases left, h0).  With
+//             '$' smaller than A this integer order is the suffix order on the
+//             first h0 symbols; suffixes with lc < h0 contain their own '$'
+//             and are final at once (distinct sentinels ordered by position).
+//   round r   (rank[i], rank[i+h]) for the suffixes still in groups of equal
+//             rank, h = h0 * 2^(r-1): the doubling step of Manber & Myers.
+// Each round is a stable LSD radix sort (radix.cu) followed by one rerank
+// kernel that, in a single pass with decoupled look-back, marks group heads,
+// writes SA entries and new ranks (rank = SA index of the group head, i.e. the
+// number of smaller suffixes, Sec. IV's "rank"), drops groups that became
+// singletons and compacts the rest.  When few suffixes remain, a finisher
+// sorts each remaining group by comparing packed words directly.
+#include <algorithm>
+#include <cstring>
+
+#include "block.cuh"
+#include "common.cuh"
+
+namespace dnasa {
+
+namespace {
+
+// ------------------------------------------------------------------ S2: initial keys
+constexpr int kInitThreads = 256;
+constexpr int kInitItems = 8;
+
+__global__ void __launch_bounds__(kInitThreads) k_init_keys(TextDesc t, int h0, int inst_shift,
+                                                            unsigned long long *__restrict__ keys,
+                                                            uint32_t *__restrict__ vals) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * kInitThreads + threadIdx.x) >> 5;
+    const int64_t chunk = warp * 32 * kInitItems;
+    if (chunk >= t.N) return;
+    int64_t p0 = chunk + lane;
+    int64_t r = read_of(t.toff, t.n_reads, min(p0, t.N - 1));
+    int64_t inst = 0;
+    if (t.n_inst > 1) inst = upper_index(t.inst_toff, 0, t.n_inst, min(p0, t.N - 1));
+#pragma unroll
+    for (int i = 0; i < kInitItems; ++i) {
+        int64_t p = p0 + (int64_t)i * 32;
+        if (p >= t.N) break;
+        while (__ldg(t.toff + r + 1) <= p) ++r;
+        if (t.n_inst > 1)
+            while (__ldg(t.inst_toff + inst + 1) <= p) ++inst;
+        int64_t left = __ldg(t.toff + r + 1) - 1 - p;   // bases before this fragment's '$'
+        uint64_t x = bases32(t.packed, (uint64_t)(p - r));
+        uint64_t kmer = x >> (64 - 2 * h0);
+        int lc = (int)min(left, (int64_t)h0);
+        if (lc < h0) kmer &= ~((1ull << (2 * (h0 - lc))) - 1ull);
+        unsigned long long key = ((unsigned long long)kmer << 5) | (unsigned long long)lc;
+        if (t.n_inst > 1) key |= (unsigned long long)inst << inst_shift;
+        keys[p] = key;
+        vals[p] = (uint32_t)p;
+    }
+}
+
+// ------------------------------------------------------------------ S4: rerank + compact
+constexpr int kRrThreads = 256;
+constexpr int kRrItems = 8;
+constexpr int kRrTile = kRrThreads * kRrItems;
+
+// look-back word: [63:62] flag, [61:31] max head index + 1 (0: none), [30:0] kept count
+constexpr unsigned long long RR_AGG = 1ull << 62;
+constexpr unsigned long long RR_INC = 2ull << 62;
+
+__device__ __forceinline__ unsigned long long rr_pack(unsigned long long flag, int64_t head,
+                                                      int64_t keep) {
+    return flag | ((unsigned long long)(head + 1) << 31) | (unsigned long long)keep;
+}
+
+struct RerankOut {
+    int64_t N;          // text length: bound of every SA slot and text position
+    uint32_t *sa, *rank;
+    uint32_t *nslots, *npos, *nhead;
+    uint2 *groups;
+    unsigned long long *kept, *ngroups, *maxgroup;
+};
+
+template <bool ROUND0>
+__global__ void __launch_bounds__(kRrThreads) k_rerank(
+    const unsigned long long *__restrict__ keys, const uint32_t *__restrict__ vals,
+    const uint32_t *__restrict__ slots, int64_t n_host, const unsigned long long *__restrict__ d_n,
+    int h0, RerankOut o, unsigned long long *status, uint32_t *tile_ctr, uint32_t *err) {
+    __shared__ unsigned long long s_k[kRrTile + 2];
+    __shared__ int64_t s_tmp[kRrThreads / 32 + 1];
+    __shared__ int64_t s_incmax[kRrThreads];
+    __shared__ int64_t s_prefix[2];
+    __shared__ uint32_t s_tile;
+    __shared__ int s_abort;
+
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        s_tile = atomicAdd(tile_ctr, 1u);
+        s_abort = 0;
+    }
+    __syncthreads();
+    const uint32_t tile = s_tile;
+    const int64_t n = d_n ? (int64_t)*d_n : n_host;
+    const int64_t base = (int64_t)tile * kRrTile;
+    if (base >= n) return;
+    const int tile_n = (int)min((int64_t)kRrTile, n - base);
+
+    for (int i = tid; i < tile_n + 2; i += kRrThreads) {
+        int64_t j = base - 1 + i;
+        s_k[i] = (j >= 0 && j < n) ? keys[j] : 0ull;
+    }
+    __syncthreads();
+
+    auto is_head = [&](int64_t j) -> bool {   // j in [base, base + tile_n]
+        if (j == 0) return true;
+        unsigned long long k = s_k[j - base + 1];
+        if (ROUND0 && (int)(k & 31ull) < h0) return true;
+        return k != s_k[j - base];
+    };
+
+    int64_t my_max = -1;
+    int64_t my_keep = 0;
+    uint32_t headbits = 0, keepbits = 0, lastbits = 0;
+#pragma unroll
+    for (int i = 0; i < kRrItems; ++i) {
+        int li = tid * kRrItems + i;
+        if (li >= tile_n) break;
+        int64_t j = base + li;
+        bool h = is_head(j);
+        bool nh = (j == n - 1) || is_head(j + 1);
+        bool keep = !(h && nh);
+        if (h) { my_max = j; headbits |= 1u << i; }
+        if (keep) { ++my_keep; keepbits |= 1u << i; }
+        if (nh) lastbits |= 1u << i;
+    }
+    int64_t tile_max, tile_keep;
+    int64_t inc_max = block_inclusive_max<kRrThreads>(my_max, s_tmp, &tile_max, (int64_t)-1);
+    s_incmax[tid] = inc_max;
+    int64_t ex_keep = block_exclusive_sum<kRrThreads>(my_keep, s_tmp, &tile_keep);
+
+    if (tid == 0) {
+        int64_t pmax = -1, psum = 0;
+        unsigned long long *my = status + tile;
+        if (tile == 0) {
+            st_relaxed_u64(my, rr_pack(RR_INC, tile_max, tile_keep));
+        } else {
+            st_relaxed_u64(my, rr_pack(RR_AGG, tile_max, tile_keep));
+            int64_t tt = (int64_t)tile - 1;
+            uint32_t spins = 0;
+            bool gave_up = false;
+            while (tt >= 0) {
+                unsigned long long w = ld_relaxed_u64(status + tt);
+                unsigned long long flag = w & (3ull << 62);
+                if (flag == 0) {
+                    if (++spins > kSpinLimit || ((spins & 1023) == 0 && ld_relaxed_u32(err) != 0)) {
+                        gave_up = true;
+                        break;
+                    }
+                    __nanosleep(32);
+                    continue;
+                }
+                int64_t hv = (int64_t)((w >> 31) & 0x7FFFFFFFull) - 1;
+                int64_t kv = (int64_t)(w & 0x7FFFFFFFull);
+                pmax = max(pmax, hv);
+                psum += kv;
+                if (flag == RR_INC) break;
+                --tt;
+            }
+            if (gave_up) {
+                atomicOr(err, DERR_TIMEOUT);
+                s_abort = 1;
+            }
+            st_relaxed_u64(my, rr_pack(RR_INC, max(pmax, tile_max), psum + tile_keep));
+        }
+        s_prefix[0] = pmax;
+        s_prefix[1] = psum;
+        if (base + tile_n == n) *o.kept = (unsigned long long)(psum + tile_keep);
+    }
+    __syncthreads();
+    if (s_abort) return;   // prefix unknown: write nothing
+    int64_t cur = max(s_prefix[0], tid > 0 ? s_incmax[tid - 1] : (int64_t)-1);
+    int64_t kp = s_prefix[1] + ex_keep;
+#pragma unroll
+    for (int i = 0; i < kRrItems; ++i) {
+        int li = tid * kRrItems + i;
+        if (li >= tile_n) break;
+        int64_t j = base + li;
+        if (headbits >> i & 1u) cur = j;
+        uint32_t slot = ROUND0 ? (uint32_t)j : slots[j];
+        uint32_t pos = vals[j];
+        uint32_t headslot = ROUND0 ? (uint32_t)cur : slot - (uint32_t)(j - cur);
+        if ((int64_t)slot >= o.N || (int64_t)pos >= o.N || kp >= n) {
+            atomicOr(err, DERR_BOUNDS);
+            break;
+        }
+        o.sa[slot] = pos;
+        o.rank[pos] = headslot;
+        if (keepbits >> i & 1u) {
+            o.nslots[kp] = slot;
+            o.npos[kp] = pos;
+            o.nhead[kp] = headslot;
+            if (lastbits >> i & 1u) {
+                uint32_t size = (uint32_t)(j - cur + 1);
+                unsigned long long g = atomicAdd(o.ngroups, 1ull);
+                o.groups[g] = make_uint2((uint32_t)(kp - size + 1), size);
+                atomicMax(o.maxgroup, (unsigned long long)size);
+            }
+            ++kp;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ S5: doubling gather
+__global__ void __launch_bounds__(256) k_gather(const uint32_t *__restrict__ npos,
+                                                const uint32_t *__restrict__ nhead, int64_t n,
+                                                const uint32_t *__restrict__ rank, uint32_t h,
+                                                int b, unsigned long long *__restrict__ keys,
+                                                uint32_t *__restrict__ vals, int64_t N,
+                                                uint32_t *err) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t pos = npos[t];
+        uint32_t r2 = 0;
+        if ((int64_t)pos + h < N) r2 = __ldg(rank + pos + h);
+        else atomicOr(err, DERR_BOUNDS);
+        keys[t] = ((unsigned long long)nhead[t] << b) | r2;
+        vals[t] = pos;
+    }
+}
+
+// ------------------------------------------------------------------ S6: direct finisher
+constexpr int kFinMax = 1024;
+constexpr int kFinThreads = 512;
+
+struct FinMember {
+    int64_t b;      // base coordinate of the first base after the shared h
+    int32_t rem;    // bases left after the shared h (>= 0)
+    uint32_t pos;
+};
+
+__device__ __forceinline__ bool fin_less(const uint64_t *__restrict__ packed, const FinMember &a,
+                                         const FinMember &c) {
+    int64_t off = 0;
+    for (;;) {
+        int64_t la = a.rem - off, lc = c.rem - off;
+        int64_t m = min(min(la, lc), (int64_t)32);
+        if (m <= 0) return la == lc ? a.pos < c.pos : la < lc;
+        uint64_t x = bases32(packed, (uint64_t)(a.b + off));
+        uint64_t y = bases32(packed, (uint64_t)(c.b + off));
+        if (m < 32) {
+            x >>= 64 - 2 * m;
+            y >>= 64 - 2 * m;
+        }
+        if (x != y) return x < y;
+        if (m < 32) return la == lc ? a.pos < c.pos : la < lc;
+        off += 32;
+    }
+}
+
+__global__ void __launch_bounds__(kFinThreads) k_finish(TextDesc t, const uint2 *__restrict__ groups,
+                                                        const unsigned long long *__restrict__ ngroups,
+                                                        const uint32_t *__restrict__ npos,
+                                                        const uint32_t *__restrict__ nslots,
+                                                        uint32_t h, uint32_t *__restrict__ sa) {
+    __shared__ FinMember s_m[kFinMax];
+    __shared__ uint16_t s_idx[kFinMax];
+    const int64_t ng = (int64_t)*ngroups;
+    for (int64_t g = blockIdx.x; g < ng; g += gridDim.x) {
+        uint2 gs = groups[g];
+        const int size = (int)gs.y;
+        int n2 = 1;
+        while (n2 < size) n2 <<= 1;
+        for (int i = threadIdx.x; i < n2; i += kFinThreads) {
+            s_idx[i] = (uint16_t)i;
+            if (i < size) {
+                uint32_t pos = npos[gs.x + i];
+                int64_t r = read_of(t.toff, t.n_reads, pos);
+                int64_t left = __ldg(t.toff + r + 1) - 1 - (int64_t)pos;
+                FinMember m;
+                m.b = (int64_t)pos - r + h;
+                m.rem = (int32_t)(left - (int64_t)h);
+                m.pos = pos;
+                s_m[i] = m;
+            }
+        }
+        __syncthreads();
+        for (int k = 2; k <= n2; k <<= 1) {
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                for (int i = threadIdx.x; i < n2; i += kFinThreads) {
+                    int ixj = i ^ j;
+                    if (ixj > i) {
+                        uint16_t a = s_idx[i], c = s_idx[ixj];
+                        bool up = (i & k) == 0;
+                        // padding members (index >= size) are larger than everything
+                        bool c_lt_a = a >= size ? (c < size) : (c < size && fin_less(t.packed, s_m[c], s_m[a]));
+                        bool a_lt_c = c >= size ? (a < size) : (a < size && fin_less(t.packed, s_m[a], s_m[c]));
+                        if (up ? c_lt_a : a_lt_c) {
+                            s_idx[i] = c;
+                            s_idx[ixj] = a;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        uint32_t slot0 = nslots[gs.x];
+        for (int i = threadIdx.x; i < size; i += kFinThreads)
+            if ((int64_t)slot0 + i < t.N) sa[slot0 + i] = s_m[s_idx[i]].pos;
+        __syncthreads();
+    }
+}
+
+__global__ void k_widen(const uint32_t *__restrict__ a, int64_t n, int64_t *__restrict__ b) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = a[i];
+}
+
+}  // namespace
+
+int h0_for(int n_inst, int *inst_bits) {
+    int ib = n_inst > 1 ? bits_for((uint64_t)(n_inst - 1)) : 0;
+    *inst_bits = ib;
+    int h0 = (64 - 5 - ib) / 2;
+    return h0 > 29 ? 29 : h0;
+}
+
+int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_opts *opts_in,
+                 cudaStream_t s) {
+    dnasa_opts opts{};
+    if (opts_in) opts = *opts_in;
+    const int tile_items = opts.tile_items ? opts.tile_items : radix_tile_default();
+    const int64_t finish_threshold =
+        opts.finish_threshold == 0 ? (int64_t)1 << 20 : opts.finish_threshold;
+    const int max_rounds = opts.max_rounds > 0 ? std::min(opts.max_rounds, 63) : 63;
+    const int64_t N = t.N;
+    int ib;
+    const int h0 = h0_for(t.n_inst, &ib);
+    const int inst_shift = 2 * h0 + 5;
+    const int key_bits0 = inst_shift + ib;
+    const int b = bits_for((uint64_t)(N - 1));
+
+    // ---- workspace
+    const size_t n = (size_t)N;
+    const int rr_tiles = ceil_div(N, kRrTile);
+    size_t need = 0;
+    auto add = [&](size_t bytes) { need += (bytes + 255) & ~size_t(255); };
+    add(n * 8); add(n * 8);                 // keys x2
+    add(n * 4); add(n * 4);                 // vals x2
+    add(n * 4);                             // rank
+    for (int i = 0; i < 6; ++i) add(n * 4); // lists A, B
+    add((n / 2 + 1) * 8);                   // groups
+    add((size_t)rr_tiles * 8);              // rerank status
+    add(radix_scratch_bytes(N, 64, tile_items));
+    DNASA_TRY(ws_reserve(ctx, need + 4096, s));
+    Arena a = ws_arena(ctx);
+    unsigned long long *keys[2] = {a.take<unsigned long long>(n), a.take<unsigned long long>(n)};
+    uint32_t *vals[2] = {a.take<uint32_t>(n), a.take<uint32_t>(n)};
+    uint32_t *rank = a.take<uint32_t>(n);
+    uint32_t *L[2][3];
+    for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 3; ++j) L[i][j] = a.take<uint32_t>(n);
+    uint2 *groups = a.take<uint2>(n / 2 + 1);
+    unsigned long long *rr_status = a.take<unsigned long long>((size_t)rr_tiles);
+    RadixScratch rs = radix_scratch_take(a, N, 64, tile_items);
+    if (!rs.hist || !rr_status) return fail(ctx, DNASA_OOM, "sa_build workspace");
+
+    DevCtrl *c = ctx->ctrl;
+    unsigned long long *cnt = c->count;
+    dnasa_trace &tr = ctx->trace;
+    memset(&tr, 0, sizeof(tr));
+    tr.h0 = h0;
+
+    auto reset_counters = [&]() -> int {
+        DNASA_CUDA(ctx, cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * 4, s));
+        DNASA_CUDA(ctx, cudaMemsetAsync(c->tile_ctr + 32, 0, sizeof(uint32_t) * 4, s));
+        DNASA_CUDA(ctx, cudaMemsetAsync(rr_status, 0, (size_t)rr_tiles * 8, s));
+        return DNASA_OK;
+    };
+    auto read_counters = [&](int64_t *kept, int64_t *ngroups, int64_t *maxgroup) -> int {
+        DNASA_CUDA(ctx, cudaMemcpyAsync(ctx->pinned, cnt, sizeof(unsigned long long) * 3,
+                                        cudaMemcpyDeviceToHost, s));
+        DNASA_TRY(check_device_status(ctx, s, "sa_build"));
+        volatile unsigned long long *pv = ctx->pinned;
+        *kept = (int64_t)pv[CNT_ACTIVE];
+        *ngroups = (int64_t)pv[CNT_GROUPS];
+        *maxgroup = (int64_t)pv[CNT_MAXGROUP];
+        return DNASA_OK;
+    };
+    RerankOut ro;
+    ro.N = N;
+    ro.sa = sa32;
+    ro.rank = rank;
+    ro.groups = groups;
+    ro.kept = cnt + CNT_ACTIVE;
+    ro.ngroups = cnt + CNT_GROUPS;
+    ro.maxgroup = cnt + CNT_MAXGROUP;
+
+    // ---- round 0: initial keys, sort, rerank
+    {
+        int warps = ceil_div(N, 32 * kInitItems);
+        k_init_keys<<<ceil_div(warps, kInitThreads / 32), kInitThreads, 0, s>>>(t, h0, inst_shift,
+                                                                              keys[0], vals[0]);
+        DNASA_CUDA(ctx, cudaGetLastError());
+        int which;
+        DNASA_TRY(radix_sort_pairs<unsigned long long>(ctx, rs, keys, vals, N, nullptr, key_bits0,
+                                                       false, tile_items, &which, s));
+        DNASA_TRY(reset_counters());
+        ro.nslots = L[0][0]; ro.npos = L[0][1]; ro.nhead = L[0][2];
+        k_rerank<true><<<rr_tiles, kRrThreads, 0, s>>>(keys[which], vals[which], nullptr, N, nullptr,
+                                                       h0, ro, rr_status, c->tile_ctr + 32, &c->err);
+        DNASA_CUDA(ctx, cudaGetLastError());
+    }
+    int64_t kept, ngroups, maxgroup;
+    DNASA_TRY(read_counters(&kept, &ngroups, &maxgroup));
+    tr.active[0] = kept;
+    int cur = 0;
+    uint64_t h = (uint64_t)h0;
+    int round = 0;
+    while (kept > 0) {
+        if (finish_threshold >= 0 && kept <= finish_threshold && maxgroup <= kFinMax) {
+            int grid = (int)std::min<int64_t>(ngroups, (int64_t)ctx->num_sms * 4);
+            k_finish<<<std::max(grid, 1), kFinThreads, 0, s>>>(t, groups, cnt + CNT_GROUPS, L[cur][1],
+                                                               L[cur][0], (uint32_t)h, sa32);
+            DNASA_CUDA(ctx, cudaGetLastError());
+            tr.finished_direct = 1;
+            break;
+        }
+        if (++round > max_rounds) return fail(ctx, DNASA_INVALID_ARG, "sa_build: max_rounds exceeded");
+        if (h >= (uint64_t)N) return fail(ctx, DNASA_CUDA_ERROR, "sa_build: doubling did not converge");
+        // keys for this round
+        int grid = (int)std::min<int64_t>(ceil_div(kept, 256), (int64_t)ctx->num_sms * 16);
+        k_gather<<<std::max(grid, 1), 256, 0, s>>>(L[cur][1], L[cur][2], kept, rank,
+                                                   (uint32_t)h, b, keys[0], vals[0], N, &c->err);
+        DNASA_CUDA(ctx, cudaGetLastError());
+        int which;
+        DNASA_TRY(radix_sort_pairs<unsigned long long>(ctx, rs, keys, vals, kept, nullptr, 2 * b,
+                                                       false, tile_items, &which, s));
+        DNASA_TRY(reset_counters());
+        ro.nslots = L[cur ^ 1][0]; ro.npos = L[cur ^ 1][1]; ro.nhead = L[cur ^ 1][2];
+        int tiles = ceil_div(kept, kRrTile);
+        k_rerank<false><<<tiles, kRrThreads, 0, s>>>(keys[which], vals[which], L[cur][0], kept,
+                                                     nullptr, h0, ro, rr_status, c->tile_ctr + 32,
+                                                     &c->err);
+        DNASA_CUDA(ctx, cudaGetLastError());
+        DNASA_TRY(read_counters(&kept, &ngroups, &maxgroup));
+        cur ^= 1;
+        h *= 2;
+        tr.rounds = round;
+        if (round < 64) tr.active[round] = kept;
+    }
+    return check_device_status(ctx, s, "sa_build");
+}
+
+int widen_u32_to_i64(dnasa_ctx *ctx, const uint32_t *a, int64_t n, int64_t *b, cudaStream_t s) {
+    int grid = (int)std::min<int64_t>(ceil_div(n, 256), (int64_t)ctx->num_sms * 16);
+    k_widen<<<std::max(grid, 1), 256, 0, s>>>(a, n, b);
+    DNASA_CUDA(ctx, cudaGetLastError());
+    return DNASA_OK;
+}
+
+}  // namespace dnasa

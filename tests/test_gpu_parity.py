@@ -1,0 +1,228 @@
+"""GPU-vs-oracle parity through the C ABI.  Everything is integer/index work,
+so the bar is bit-exact equality on every output array."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+from paper_1404_3456_gb300 import synth  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1404_3456_gb300 import binding
+
+    c = binding.Context(0)
+    yield c
+    c.close()
+
+
+def B():
+    from paper_1404_3456_gb300 import binding
+
+    return binding
+
+
+def dev(a: np.ndarray):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def random_text(rng, n_reads, lo, hi, periodic_frac=0.3, dup=True):
+    reads = []
+    for _ in range(n_reads):
+        n = int(rng.integers(lo, hi + 1))
+        if rng.random() < periodic_frac:
+            unit = synth.iid(rng, int(rng.integers(1, 6)))
+            r = np.tile(unit, n // unit.size + 1)[:n]
+        else:
+            r = synth.iid(rng, n)
+        reads.append(r)
+    if dup and n_reads >= 4:
+        reads[1] = reads[0].copy()
+        reads[2] = reads[0][1:].copy() if reads[0].size > 1 else reads[2]
+    return synth.join_reads(reads)
+
+
+def gpu_sa(ctx, text_np, dtype=torch.int32, opts=None):
+    text = dev(text_np)
+    sa, packed, toff, nr = B().suffix_array(ctx, text, dtype=dtype, opts=opts)
+    return sa, packed, toff, nr, text
+
+
+# ---------------------------------------------------------------- S1 pack
+
+
+def test_pack_offsets_and_codes(ctx):
+    rng = np.random.default_rng(1)
+    t = random_text(rng, 50, 1, 300)
+    text = dev(t)
+    packed, toff, nr = B().pack_text(ctx, text)
+    assert nr == int((t == ord("$")).sum())
+    assert np.array_equal(toff.cpu().numpy(), oracle.read_offsets(t))
+    # decode the 2-bit words and compare with the bases of the text
+    words = packed.cpu().numpy().view(np.uint64)
+    bases = t[t != ord("$")]
+    idx = np.arange(bases.size)
+    codes = (words[idx // 32] >> (62 - 2 * (idx % 32)).astype(np.uint64)) & np.uint64(3)
+    assert np.array_equal(np.frombuffer(b"ACGT", np.uint8)[codes.astype(np.int64)], bases)
+    assert np.all(words[(bases.size + 31) // 32:] == 0)
+
+
+@pytest.mark.parametrize("bad", [b"ACGN$", b"ACGT", b"AC$$GT$", b"$AC$"])
+def test_pack_rejects_bad_text(ctx, bad):
+    text = dev(np.frombuffer(bad, np.uint8))
+    with pytest.raises(B().DnasaError) as e:
+        B().pack_text(ctx, text)
+    assert e.value.status == B().BAD_ALPHABET
+
+
+# ---------------------------------------------------------------- S2-S6 suffix array
+
+
+@pytest.mark.parametrize("text", [b"$", b"A$", b"AAAAAAAA$", b"ACGTACGTACGT$", b"A$A$AA$",
+                                  b"T$G$C$A$", b"ACGT" * 40 + b"$"])
+def test_sa_small_texts(ctx, text):
+    t = np.frombuffer(text, np.uint8)
+    sa = gpu_sa(ctx, t)[0]
+    assert np.array_equal(sa.cpu().numpy().astype(np.int64), oracle.suffix_array(t))
+
+
+@pytest.mark.parametrize("seed,n_reads,lo,hi", [(0, 1, 100_000, 100_000), (1, 40, 1, 200),
+                                                (2, 300, 50, 2000), (3, 2000, 1, 60),
+                                                (4, 8, 20_000, 40_000)])
+def test_sa_random_multi_read(ctx, seed, n_reads, lo, hi):
+    rng = np.random.default_rng(seed)
+    t = random_text(rng, n_reads, lo, hi)
+    sa = gpu_sa(ctx, t)[0]
+    assert np.array_equal(sa.cpu().numpy().astype(np.int64), oracle.suffix_array(t))
+
+
+def test_sa_repeat_genome(ctx):
+    """Tandem arrays and element copies: deep doubling rounds, several tiles, ragged tail."""
+    rng = synth.rng_for(7, 11)
+    g = synth.genome_with_repeats(rng, 400_003, 0.05, (2, 50), (10, 200), 0.05, 300, 0.01)
+    t = synth.genome_text(g)
+    sa = gpu_sa(ctx, t)[0]
+    assert np.array_equal(sa.cpu().numpy().astype(np.int64), oracle.suffix_array(t))
+    tr = ctx.trace()
+    assert tr["rounds"] >= 2
+
+
+@pytest.mark.parametrize("finish", [-1, 1 << 40])
+def test_sa_finisher_and_doubling_agree(ctx, finish):
+    rng = synth.rng_for(8, 11)
+    g = synth.genome_with_repeats(rng, 200_000, 0.10, (2, 50), (10, 100), 0.05, 300, 0.01)
+    t = synth.genome_text(g)
+    opts = B().make_opts(finish_threshold=finish)
+    sa = gpu_sa(ctx, t, opts=opts)[0]
+    assert np.array_equal(sa.cpu().numpy().astype(np.int64), oracle.suffix_array(t))
+    assert ctx.trace()["finished_direct"] == (1 if finish > 0 else 0)
+
+
+@pytest.mark.parametrize("tile", [2048, 3840, 5120])
+def test_sa_tile_sizes(ctx, tile):
+    rng = np.random.default_rng(9)
+    t = random_text(rng, 500, 10, 600)
+    sa = gpu_sa(ctx, t, opts=B().make_opts(tile_items=tile))[0]
+    assert np.array_equal(sa.cpu().numpy().astype(np.int64), oracle.suffix_array(t))
+
+
+def test_sa_int64(ctx):
+    rng = np.random.default_rng(10)
+    t = random_text(rng, 30, 1, 500)
+    sa = gpu_sa(ctx, t, dtype=torch.int64)[0]
+    assert sa.dtype == torch.int64
+    assert np.array_equal(sa.cpu().numpy(), oracle.suffix_array(t))
+
+
+def test_sa_all_same_base(ctx):
+    t = synth.genome_text(np.full(50_000, ord("A"), np.uint8))
+    sa = gpu_sa(ctx, t)[0]
+    assert np.array_equal(sa.cpu().numpy().astype(np.int64), np.arange(t.size)[::-1])
+
+
+# ---------------------------------------------------------------- S7 LCP
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_lcp_parity(ctx, seed):
+    rng = np.random.default_rng(20 + seed)
+    t = random_text(rng, 200, 1, 800)
+    sa, packed, toff, nr, text = gpu_sa(ctx, t)
+    lcp = torch.empty_like(sa)
+    B().lcp_build(ctx, packed, toff, nr, t.size, sa, lcp)
+    want = oracle.lcp_kasai(t, oracle.suffix_array(t))
+    assert np.array_equal(lcp.cpu().numpy(), want)
+
+
+# ---------------------------------------------------------------- S8-S9 overlaps
+
+
+def overlaps_gpu(ctx, t, lmin):
+    sa, packed, toff, nr, text = gpu_sa(ctx, t)
+    lcp = torch.empty_like(sa)
+    B().lcp_build(ctx, packed, toff, nr, t.size, sa, lcp)
+    cap = 16 * nr + 16
+    edges = torch.empty((cap, 3), dtype=torch.int32, device="cuda")
+    contained = torch.empty(nr, dtype=torch.uint8, device="cuda")
+    ne = B().overlap_search(ctx, packed, toff, nr, t.size, sa, lcp, lmin, edges, contained)
+    e = edges[:ne].cpu().numpy()
+    return e, contained.cpu().numpy()
+
+
+@pytest.mark.parametrize("seed,lmin", [(0, 1), (1, 3), (2, 8), (3, 2)])
+def test_overlap_parity_random(ctx, seed, lmin):
+    rng = np.random.default_rng(30 + seed)
+    t = random_text(rng, 120, 1, 80, periodic_frac=0.4)
+    e, c = overlaps_gpu(ctx, t, lmin)
+    ej, ek, eL = oracle.overlaps_sorted(t, lmin)
+    assert np.array_equal(e[:, 0], ej) and np.array_equal(e[:, 1], ek) and np.array_equal(e[:, 2], eL)
+    assert np.array_equal(c, oracle.contained(t))
+
+
+def test_overlap_parity_tiny(ctx):
+    inst = synth.tiny(3)
+    e, c = overlaps_gpu(ctx, inst["text"], 31)
+    ej, ek, eL = oracle.overlaps_sorted(inst["text"], 31)
+    assert np.array_equal(e, np.stack([ej, ek, eL], 1))
+    assert not c.any()
+
+
+def test_overlap_parity_batched_instance(ctx):
+    inst = synth.batched_instance(5, 0, g_lo=3000, g_hi=5000)
+    e, c = overlaps_gpu(ctx, inst["text"], 31)
+    ej, ek, eL = oracle.overlaps_sorted(inst["text"], 31)
+    assert np.array_equal(e, np.stack([ej, ek, eL], 1))
+    assert np.array_equal(c, oracle.contained(inst["text"]))
+
+
+# ---------------------------------------------------------------- S10 assemble
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_assemble_tiny_recovers_genome(ctx, seed):
+    inst = synth.tiny(seed)
+    contigs = B().assemble_text(ctx, dev(inst["text"]), inst["min_overlap"])
+    assert contigs == [inst["genome"].tobytes()]
+
+
+def test_assemble_parity_with_oracle(ctx):
+    inst = synth.batched_instance(6, 1, g_lo=4000, g_hi=6000)
+    got = B().assemble_text(ctx, dev(inst["text"]), 31)
+    buf, off = oracle.assemble(inst["text"], 31)
+    assert got == oracle.contigs_as_list(buf, off)
+
+
+def test_assemble_worked_example_dna(ctx):
+    """The paper's Sec. III example re-spelt over ACGT (a->A, b->C, h->G, p->T, t->A is
+    not injective, so use a DNA instance with the same overlap structure)."""
+    reads = [b"ACGTTGCA", b"TTGCAGGA", b"CAGGATCC", b"GATCCTAA"]
+    t = np.frombuffer(b"$".join(reads) + b"$", np.uint8)
+    got = B().assemble_text(ctx, dev(t), 2)
+    buf, off = oracle.assemble(t, 2)
+    assert got == oracle.contigs_as_list(buf, off)
