@@ -1,0 +1,349 @@
+#!/usr/bin/env python
+"""Benchmark: suffix-array build (+ LCP) of a 64 Mbp synthetic genome on one GB300.
+
+Workload ("sa64m"): a seeded 64,000,000 bp genome -- 90 % i.i.d. uniform ACGT,
+5 % tandem arrays (period U{2..50}, U{10..200} copies), 5 % copies of one
+300 bp element with 1 % substitutions -- as one '$'-terminated fragment
+(N = 64,000,001 suffixes), 2-bit packed and resident in HBM before timing.
+One step = sa_build (int32 SA) + lcp_build (int32 LCP) through the C ABI.
+The working set (keys, values, ranks: ~3.5 GB) is far larger than the 129 MB
+L2, so no flush is needed between steps.
+
+Metric: Msuffix/s = N * ranks / (max-over-ranks seconds per step) / 1e6.
+The single-instance path does not shard across GPUs: with --gpus N every rank
+runs its own replica (weak scaling, no collective on the data path).
+
+Extra keys: roofline (the dominant kernel's algorithmic GB/s, timed live with
+CUDA events on its stream, against the measured HBM copy peak), cpu_baseline
+(the oracle on a bounded prefix of the same genome, single thread), e2e (the
+same step with host buffers: H2D of the packed text, D2H of SA + LCP), clocks
+sampled by nvidia-smi during the timed region, gpu_launches.
+
+--impl reference times the oracle (plain C, single thread) on a bounded prefix
+of the same genome, per step, and prints the same JSON line with
+"impl": "reference".
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SA build Msuffix/s (sa_build + lcp_build, 64 Mbp genome)"
+UNIT = "Msuffix/s"
+SAMPLE_CPU = 16_000_000   # oracle sample for cpu_baseline (~10-20 s single-threaded)
+SAMPLE_REF = 4_000_000    # oracle sample per --impl reference step (~3 s)
+G = 64_000_000
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="dnasa", choices=["dnasa", "reference"])
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--genome", type=int, default=G, help="genome length (default 64,000,000)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
+            int(os.environ.get("WORLD_SIZE", 1)))
+
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def genome_text(seed: int, size: int):
+    from paper_1404_3456_gb300 import synth
+
+    g = synth.sa64m_genome(seed, G)
+    if size < G:
+        g = g[:size]
+    return synth.genome_text(g)
+
+
+def cpu_oracle_rate(text: np.ndarray):
+    """Oracle SA + Kasai LCP of `text` on one host core; returns (Msuffix/s, seconds)."""
+    import oracle
+
+    t0 = time.perf_counter()
+    sa = oracle.suffix_array(text)
+    oracle.lcp_kasai(text, sa)
+    dt = time.perf_counter() - t0
+    return text.size / dt / 1e6, dt
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+
+    oracle.build()
+    sample = genome_text(args.seed, SAMPLE_REF)
+    for _ in range(args.warmup):
+        cpu_oracle_rate(sample)
+    times = []
+    for _ in range(args.steps):
+        _, dt = cpu_oracle_rate(sample)
+        times.append(dt)
+    ms = 1000.0 * sum(times) / len(times)
+    value = sample.size / (ms / 1000.0) / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8/int32", "data": "synthetic",
+        "config": {"workload": f"sa64m prefix: oracle SA + Kasai LCP of the first {SAMPLE_REF:,} "
+                               "bases of the 64 Mbp genome (bounded sample)",
+                   "genome_bp": SAMPLE_REF, "seed": args.seed},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"first {SAMPLE_REF:,} bp of the sa64m genome, per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+
+    rank, local_rank, world = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    torch.cuda.set_device(local_rank)
+    from paper_1404_3456_gb300 import binding
+
+    dev = torch.device("cuda", local_rank)
+    text_np = genome_text(args.seed, args.genome)
+    N = int(text_np.size)
+    ctx = binding.Context(local_rank)
+    stream = torch.cuda.current_stream()
+    text = torch.from_numpy(text_np).to(dev)
+    packed, toff, nr = binding.pack_text(ctx, text)
+    del text
+    sa = torch.empty(N, dtype=torch.int32, device=dev)
+    lcp = torch.empty(N, dtype=torch.int32, device=dev)
+
+    def step():
+        binding.sa_build(ctx, packed, toff, nr, N, sa)
+        binding.lcp_build(ctx, packed, toff, nr, N, sa, lcp)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    trace = ctx.trace()
+
+    # ---- timed region (device): K steps between two events on the stream
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    clocks = ClockSampler(local_rank)
+    barrier()
+    clocks.start()
+    l0 = ctx.launch_count()
+    ctx.profile(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    launches = ctx.launch_count() - l0
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+
+    # SA-only time of one more step, for information
+    s0 = torch.cuda.Event(enable_timing=True)
+    s1 = torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    binding.sa_build(ctx, packed, toff, nr, N, sa)
+    s1.record(stream)
+    torch.cuda.synchronize()
+    sa_only_ms = s0.elapsed_time(s1)
+
+    # ---- end to end: host buffers, copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        h_packed = packed.cpu().pin_memory()
+        h_toff = toff.cpu().pin_memory()
+        h_sa = torch.empty(N, dtype=torch.int32).pin_memory()
+        h_lcp = torch.empty(N, dtype=torch.int32).pin_memory()
+        d_packed = torch.empty_like(packed)
+        d_toff = torch.empty_like(toff)
+
+        def e2e_step():
+            d_packed.copy_(h_packed, non_blocking=True)
+            d_toff.copy_(h_toff, non_blocking=True)
+            binding.sa_build(ctx, d_packed, d_toff, nr, N, sa)
+            binding.lcp_build(ctx, d_packed, d_toff, nr, N, sa, lcp)
+            h_sa.copy_(sa, non_blocking=True)
+            h_lcp.copy_(lcp, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        x0 = torch.cuda.Event(enable_timing=True)
+        x1 = torch.cuda.Event(enable_timing=True)
+        x0.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        x1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = x0.elapsed_time(x1) / args.steps
+        e2e = {"ms": e2e_ms, "h2d": h_packed.numel() * 8 + h_toff.numel() * 8, "d2h": 8 * N}
+
+    if world > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([ms, e2e["ms"] if e2e else 0.0], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t[0])
+        if e2e:
+            e2e["ms"] = float(t[1])
+    value = N * world / (ms / 1000.0) / 1e6
+
+    if rank != 0:
+        return 0
+    # ---- roofline of the dominant kernel class
+    peak, peak_src = measured_peak()
+    dom = max(prof.items(), key=lambda kv: kv[1]["ms"]) if prof else None
+    roofline = None
+    if dom:
+        name, d = dom
+        achieved = d["bytes"] / (d["ms"] / 1000.0) / 1e9
+        traffic = None
+        tfile = os.path.join(ROOT, "profiles", "traffic.json")
+        if os.path.exists(tfile):
+            try:
+                tj = json.load(open(tfile))
+                if name in tj and tj[name].get("valid", False):
+                    # dram bytes per algorithmic byte from one ncu capture, scaled per launch
+                    traffic = tj[name]["dram_per_algorithmic_byte"] * d["bytes"] / d["launches"]
+            except Exception:
+                traffic = None
+        roofline = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak,
+                    "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_src,
+                    "traffic": traffic, "launches": d["launches"],
+                    "algorithmic_bytes_per_launch": d["bytes"] / d["launches"],
+                    "avg_launch_ms": d["ms"] / d["launches"]}
+    breakdown = {k: {"launches": v["launches"], "ms_per_step": v["ms"] / args.steps,
+                     "share": v["ms"] / max(1e-9, sum(x["ms"] for x in prof.values()))}
+                 for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])}
+    cpu = None
+    if not args.no_cpu_baseline:
+        sample = genome_text(args.seed, SAMPLE_CPU)
+        rate, dt = cpu_oracle_rate(sample)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"oracle SA + Kasai LCP of the first {SAMPLE_CPU:,} bp of the same "
+                         f"genome, one run, {dt:.1f} s"}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8/int32", "data": "synthetic",
+        "config": {"workload": f"sa64m: sa_build + lcp_build of a {args.genome:,} bp genome "
+                               f"(N = {N:,} suffixes), int32 SA and LCP",
+                   "genome_bp": args.genome, "seed": args.seed, "parallelism": f"replicas{world}",
+                   "l2": "working set >> L2 (no flush needed)",
+                   "rounds": trace["rounds"], "finished_direct": trace["finished_direct"],
+                   "active_per_round": trace["active"], "sa_only_ms": sa_only_ms},
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": ({"value": N * world / (e2e["ms"] / 1000.0) / 1e6, "unit": UNIT,
+                 "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"],
+                 "ms_per_step": e2e["ms"]} if e2e else None),
+        "gpu_launches": launches,
+        "clocks": clk,
+        "kernels": breakdown,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

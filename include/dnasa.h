@@ -104,6 +104,42 @@ int dnasa_get_trace(dnasa_ctx *ctx, dnasa_trace *out);
 /* Words a packed buffer for an N-symbol text needs (bases / 32 rounded up, + 2). */
 int64_t dnasa_packed_words(int64_t N);
 
+/* ---- profiling ---------------------------------------------------------------- */
+
+/* Kernel classes the profiler aggregates. */
+enum {
+    DNASA_PROF_ONESWEEP = 0,  /* one radix digit pass (decoupled look-back scatter) */
+    DNASA_PROF_HIST = 1,      /* digit histograms of a sort */
+    DNASA_PROF_RERANK = 2,    /* head flags, SA/rank writes, compaction */
+    DNASA_PROF_GATHER = 3,    /* doubling keys (rank[i], rank[i+h]) */
+    DNASA_PROF_INIT = 4,      /* initial packed keys */
+    DNASA_PROF_FINISH = 5,    /* direct-comparison finisher */
+    DNASA_PROF_LCP = 6,
+    DNASA_PROF_OVERLAP = 7,
+    DNASA_PROF_LAYOUT = 8,
+    DNASA_PROF_PACK = 9,
+    DNASA_PROF_OTHER = 10,
+    DNASA_PROF_KINDS = 11
+};
+
+/* Per kernel class: launches, summed device time (CUDA events recorded on the
+ * launching stream around each launch) and summed algorithmic bytes (what the
+ * kernel must read and write, a random 4-byte access counted as 4 bytes). */
+typedef struct {
+    int32_t kind;
+    int32_t launches;
+    double ms;
+    double bytes;
+} dnasa_prof_entry;
+
+/* Turns per-launch event recording on (enable != 0) or off; clears records. */
+int dnasa_profile(dnasa_ctx *ctx, int enable);
+/* Waits for the recorded events, writes one entry per kernel class that ran
+ * (at most max_entries; host array) and clears the records. */
+int dnasa_profile_read(dnasa_ctx *ctx, dnasa_prof_entry *out, int max_entries, int *n_out);
+/* Kernel launches issued through this context since it was created. */
+uint64_t dnasa_launch_count(dnasa_ctx *ctx);
+
 /* ---- S1: pack (Sec. III alphabet; the SA of Sec. IV is over this text) ------- */
 
 /* Validates text[0..N) and writes its packed form and fragment offsets.

@@ -42,6 +42,14 @@ class Trace(ctypes.Structure):
                 ("active", ctypes.c_int64 * 64)]
 
 
+class ProfEntry(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("launches", ctypes.c_int32), ("ms", ctypes.c_double),
+                ("bytes", ctypes.c_double)]
+
+
+PROF_KINDS = ["onesweep", "hist", "rerank", "gather", "init_keys", "finish", "lcp", "overlap",
+              "layout", "pack", "other"]
+
 _lock = threading.Lock()
 _lib = None
 
@@ -54,6 +62,9 @@ _SIGS = {
     "dnasa_sync_status": (_INT, [_P, _P]),
     "dnasa_get_trace": (_INT, [_P, ctypes.POINTER(Trace)]),
     "dnasa_packed_words": (_I64, [_I64]),
+    "dnasa_profile": (_INT, [_P, _INT]),
+    "dnasa_profile_read": (_INT, [_P, ctypes.POINTER(ProfEntry), _INT, ctypes.POINTER(_INT)]),
+    "dnasa_launch_count": (ctypes.c_uint64, [_P]),
     "dnasa_pack": (_INT, [_P, _P, _I64, _P, _P, _I64, ctypes.POINTER(_I64), _P]),
     "sa_build": (_INT, [_P, _P, _P, _I64, _I64, _P, _INT, ctypes.POINTER(Opts), _P]),
     "lcp_build": (_INT, [_P, _P, _P, _I64, _I64, _P, _INT, _P, _P]),
@@ -125,6 +136,21 @@ class Context:
         self.check(lib().dnasa_get_trace(self.handle, ctypes.byref(tr)))
         return dict(rounds=tr.rounds, finished_direct=tr.finished_direct, h0=tr.h0,
                     active=list(tr.active[: tr.rounds + 1]))
+
+    def profile(self, enable: bool = True):
+        """Start (or stop) recording CUDA events around every kernel launch."""
+        self.check(lib().dnasa_profile(self.handle, 1 if enable else 0))
+
+    def profile_read(self) -> dict:
+        """{kernel class: dict(launches, ms, bytes)} since profile(True); clears."""
+        arr = (ProfEntry * len(PROF_KINDS))()
+        n = ctypes.c_int(0)
+        self.check(lib().dnasa_profile_read(self.handle, arr, len(PROF_KINDS), ctypes.byref(n)))
+        return {PROF_KINDS[e.kind]: dict(launches=e.launches, ms=e.ms, bytes=e.bytes)
+                for e in arr[: n.value]}
+
+    def launch_count(self) -> int:
+        return int(lib().dnasa_launch_count(self.handle))
 
     def close(self):
         if getattr(self, "handle", None):

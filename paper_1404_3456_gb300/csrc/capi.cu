@@ -78,7 +78,10 @@ int sa_view(dnasa_ctx *ctx, const void *sa, int idx_width, int64_t N, DevBuf &tm
     }
     DNASA_TRY(dev_alloc(ctx, tmp, (size_t)N * 4, s));
     int grid = (int)std::min<int64_t>(ceil_div(N, 256), (int64_t)ctx->num_sms * 16);
-    k_narrow<<<std::max(grid, 1), 256, 0, s>>>((const int64_t *)sa, N, (uint32_t *)tmp.p);
+    {
+        LaunchScope ls_(ctx, PK_OTHER, s, 12.0 * N);
+        k_narrow<<<std::max(grid, 1), 256, 0, s>>>((const int64_t *)sa, N, (uint32_t *)tmp.p);
+    }
     DNASA_CUDA(ctx, cudaGetLastError());
     *out = (const uint32_t *)tmp.p;
     return DNASA_OK;

@@ -49,6 +49,18 @@ struct Arena {
 
 }  // namespace dnasa
 
+namespace dnasa {
+// Kernel classes the profiler aggregates (same numbering as DNASA_PROF_* in dnasa.h).
+enum ProfKind { PK_ONESWEEP = 0, PK_HIST = 1, PK_RERANK = 2, PK_GATHER = 3, PK_INIT = 4,
+                PK_FINISH = 5, PK_LCP = 6, PK_OVERLAP = 7, PK_LAYOUT = 8, PK_PACK = 9,
+                PK_OTHER = 10, PK_COUNT = 11 };
+struct ProfRec {
+    int kind;
+    cudaEvent_t a, b;
+    double bytes;
+};
+}  // namespace dnasa
+
 struct dnasa_ctx {
     int device = 0;
     size_t ws_cap = 0;        // 0 = unbounded
@@ -62,6 +74,11 @@ struct dnasa_ctx {
     unsigned long long *lb_buf = nullptr;  // onesweep look-back status words (device)
     size_t lb_words = 0;
     uint32_t lb_epoch = 0;
+    // profiling: launch counter (always on) and, when enabled, an event pair per launch
+    unsigned long long launches = 0;
+    bool prof_on = false;
+    std::vector<dnasa::ProfRec> prof;
+    std::vector<cudaEvent_t> ev_pool;
 };
 
 namespace dnasa {
@@ -80,6 +97,17 @@ bool is_device_ptr(dnasa_ctx *ctx, const void *p);
 // Reads the device error flags (synchronizes s) and maps them to a status;
 // clears them.
 int check_device_status(dnasa_ctx *ctx, cudaStream_t s, const char *where);
+
+// Counts one kernel launch of class `kind` and, when profiling is on, brackets
+// it with CUDA events on its stream; `bytes` is the launch's algorithmic
+// traffic.  Construct immediately before the launch, destroy right after it.
+struct LaunchScope {
+    dnasa_ctx *ctx;
+    int idx = -1;
+    cudaStream_t s;
+    LaunchScope(dnasa_ctx *c, int kind, cudaStream_t st, double bytes);
+    ~LaunchScope();
+};
 
 #define DNASA_CUDA(ctx, call)                                         \
     do {                                                              \

@@ -59,10 +59,13 @@ bool is_device_ptr(dnasa_ctx *ctx, const void *p) {
 }
 
 int check_device_status(dnasa_ctx *ctx, cudaStream_t s, const char *where) {
-    DNASA_CUDA(ctx, cudaMemcpyAsync(ctx->pinned, &ctx->ctrl->err, sizeof(uint32_t),
+    // the error word has its own pinned slot (63) so that a caller's readback
+    // into the low slots, enqueued just before, is not overwritten
+    uint32_t *slot = reinterpret_cast<uint32_t *>(ctx->pinned + 63);
+    DNASA_CUDA(ctx, cudaMemcpyAsync(slot, &ctx->ctrl->err, sizeof(uint32_t),
                                     cudaMemcpyDeviceToHost, s));
     DNASA_CUDA(ctx, cudaStreamSynchronize(s));
-    uint32_t err = (uint32_t)(*(volatile uint32_t *)ctx->pinned);
+    uint32_t err = *(volatile uint32_t *)slot;
     if (err == 0) return DNASA_OK;
     DNASA_CUDA(ctx, cudaMemsetAsync(&ctx->ctrl->err, 0, sizeof(uint32_t), s));
     DNASA_CUDA(ctx, cudaStreamSynchronize(s));
@@ -71,6 +74,39 @@ int check_device_status(dnasa_ctx *ctx, cudaStream_t s, const char *where) {
     if (err & DERR_ALPHABET) return fail(ctx, DNASA_BAD_ALPHABET, w + ": byte outside A/C/G/T/'$'");
     if (err & DERR_EMPTY_READ) return fail(ctx, DNASA_BAD_ALPHABET, w + ": empty fragment or text not '$'-terminated");
     return fail(ctx, DNASA_CUDA_ERROR, w + ": device index check failed");
+}
+
+// ------------------------------------------------------------------ profiling
+static cudaEvent_t ev_get(dnasa_ctx *ctx) {
+    if (!ctx->ev_pool.empty()) {
+        cudaEvent_t e = ctx->ev_pool.back();
+        ctx->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+LaunchScope::LaunchScope(dnasa_ctx *c, int kind, cudaStream_t st, double bytes) : ctx(c), s(st) {
+    ++ctx->launches;
+    if (!ctx->prof_on) return;
+    ProfRec r;
+    r.kind = kind;
+    r.bytes = bytes;
+    r.a = ev_get(ctx);
+    r.b = ev_get(ctx);
+    if (!r.a || !r.b) return;
+    cudaEventRecord(r.a, s);
+    idx = (int)ctx->prof.size();
+    ctx->prof.push_back(r);
+}
+
+LaunchScope::~LaunchScope() {
+    if (idx >= 0) cudaEventRecord(ctx->prof[idx].b, s);
 }
 
 // ------------------------------------------------------------------ small scans
@@ -145,9 +181,18 @@ int compact_flags(dnasa_ctx *ctx, Arena &a, const uint8_t *flags, int64_t n, uin
     int tiles = ceil_div(n, kCompactTile);
     int64_t *tc = a.take<int64_t>((size_t)tiles + 1);
     if (!tc) return fail(ctx, DNASA_OOM, "compaction scratch");
-    k_flag_count<<<tiles, kCompactThreads, 0, s>>>(flags, n, tc);
-    k_scan_small<<<1, 1024, 0, s>>>(tc, tiles, (int64_t *)d_count);
-    k_flag_scatter<<<tiles, kCompactThreads, 0, s>>>(flags, n, tc, out);
+    {
+        LaunchScope ls_(ctx, PK_OTHER, s, (double)n);
+        k_flag_count<<<tiles, kCompactThreads, 0, s>>>(flags, n, tc);
+    }
+    {
+        LaunchScope ls_(ctx, PK_OTHER, s, 0);
+        k_scan_small<<<1, 1024, 0, s>>>(tc, tiles, (int64_t *)d_count);
+    }
+    {
+        LaunchScope ls_(ctx, PK_OTHER, s, (double)n);
+        k_flag_scatter<<<tiles, kCompactThreads, 0, s>>>(flags, n, tc, out);
+    }
     DNASA_CUDA(ctx, cudaGetLastError());
     return DNASA_OK;
 }
@@ -246,12 +291,24 @@ int pack_impl(dnasa_ctx *ctx, const uint8_t *text, int64_t N, uint64_t *packed, 
     int64_t *tc = a.take<int64_t>((size_t)tiles + 1);
     uint8_t *codes = a.take<uint8_t>((size_t)N + 64);
     unsigned long long *cnt = &ctx->ctrl->count[CNT_DOLLARS];
-    k_pack_count<<<tiles, kPackThreads, 0, s>>>(text, N, tc, &ctx->ctrl->err);
-    k_scan_small<<<1, 1024, 0, s>>>(tc, tiles, (int64_t *)cnt);
-    k_pack_emit<<<tiles, kPackThreads, 0, s>>>(text, N, tc, toff, toff_cap, codes);
+    {
+        LaunchScope ls_(ctx, PK_PACK, s, (double)N);
+        k_pack_count<<<tiles, kPackThreads, 0, s>>>(text, N, tc, &ctx->ctrl->err);
+    }
+    {
+        LaunchScope ls_(ctx, PK_OTHER, s, 0);
+        k_scan_small<<<1, 1024, 0, s>>>(tc, tiles, (int64_t *)cnt);
+    }
+    {
+        LaunchScope ls_(ctx, PK_PACK, s, 2.0 * N);
+        k_pack_emit<<<tiles, kPackThreads, 0, s>>>(text, N, tc, toff, toff_cap, codes);
+    }
     int64_t nwords = dnasa_packed_words(N);
-    k_pack_words<<<ceil_div(nwords, 256), 256, 0, s>>>(codes, (const int64_t *)cnt, N, nwords,
-                                                      packed);
+    {
+        LaunchScope ls_(ctx, PK_PACK, s, 1.25 * N);
+        k_pack_words<<<ceil_div(nwords, 256), 256, 0, s>>>(codes, (const int64_t *)cnt, N, nwords,
+                                                          packed);
+    }
     DNASA_CUDA(ctx, cudaGetLastError());
     DNASA_CUDA(ctx, cudaMemcpyAsync(ctx->pinned, cnt, 8, cudaMemcpyDeviceToHost, s));
     DNASA_TRY(check_device_status(ctx, s, "dnasa_pack"));
@@ -301,6 +358,8 @@ void dnasa_destroy(dnasa_ctx *ctx) {
     if (ctx->lb_buf) cudaFree(ctx->lb_buf);
     if (ctx->ctrl) cudaFree(ctx->ctrl);
     if (ctx->pinned) cudaFreeHost(ctx->pinned);
+    for (auto &r : ctx->prof) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+    for (auto e : ctx->ev_pool) cudaEventDestroy(e);
     delete ctx;
 }
 
@@ -310,6 +369,42 @@ int dnasa_sync_status(dnasa_ctx *ctx, void *stream) {
     if (!ctx) return DNASA_INVALID_ARG;
     return check_device_status(ctx, (cudaStream_t)stream, "dnasa_sync_status");
 }
+
+int dnasa_profile(dnasa_ctx *ctx, int enable) {
+    if (!ctx) return DNASA_INVALID_ARG;
+    for (auto &r : ctx->prof) {
+        ctx->ev_pool.push_back(r.a);
+        ctx->ev_pool.push_back(r.b);
+    }
+    ctx->prof.clear();
+    ctx->prof_on = enable != 0;
+    return DNASA_OK;
+}
+
+int dnasa_profile_read(dnasa_ctx *ctx, dnasa_prof_entry *out, int max_entries, int *n_out) {
+    if (!ctx || !out || !n_out || max_entries < 0) return DNASA_INVALID_ARG;
+    dnasa_prof_entry agg[PK_COUNT];
+    for (int k = 0; k < PK_COUNT; ++k) agg[k] = dnasa_prof_entry{k, 0, 0.0, 0.0};
+    for (auto &r : ctx->prof) {
+        float ms = 0.f;
+        cudaError_t e = cudaEventSynchronize(r.b);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, r.a, r.b);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "dnasa_profile_read");
+        agg[r.kind].launches += 1;
+        agg[r.kind].ms += ms;
+        agg[r.kind].bytes += r.bytes;
+        ctx->ev_pool.push_back(r.a);
+        ctx->ev_pool.push_back(r.b);
+    }
+    ctx->prof.clear();
+    int n = 0;
+    for (int k = 0; k < PK_COUNT && n < max_entries; ++k)
+        if (agg[k].launches) out[n++] = agg[k];
+    *n_out = n;
+    return DNASA_OK;
+}
+
+uint64_t dnasa_launch_count(dnasa_ctx *ctx) { return ctx ? ctx->launches : 0; }
 
 int dnasa_get_trace(dnasa_ctx *ctx, dnasa_trace *out) {
     if (!ctx || !out) return DNASA_INVALID_ARG;

@@ -199,7 +199,10 @@ int layout_impl(dnasa_ctx *ctx, const TextDesc &t, int64_t max_reads_per_inst,
     // an overlap L is shorter than the longest fragment
     unsigned long long *cnt = ctx->ctrl->count;
     DNASA_CUDA(ctx, cudaMemsetAsync(cnt + CNT_TMP, 0, 8, s));
-    k_max_len<<<grid_for(ctx, nr), 256, 0, s>>>(t, cnt + CNT_TMP);
+    {
+        LaunchScope ls_(ctx, PK_LAYOUT, s, 0);
+        k_max_len<<<grid_for(ctx, nr), 256, 0, s>>>(t, cnt + CNT_TMP);
+    }
     DNASA_CUDA(ctx, cudaMemcpyAsync(ctx->pinned, cnt + CNT_TMP, 8, cudaMemcpyDeviceToHost, s));
     DNASA_TRY(check_device_status(ctx, s, "assemble/layout"));
     const int lb = bits_for((uint64_t)ctx->pinned[0]);
@@ -238,9 +241,15 @@ int layout_impl(dnasa_ctx *ctx, const TextDesc &t, int64_t max_reads_per_inst,
     int64_t nsel = 0;
     int which = 0;
     if (ne > 0) {
-        k_edge_filter<<<grid_for(ctx, ne), 256, 0, s>>>(edges, ne, contained, flags);
+        {
+            LaunchScope ls_(ctx, PK_LAYOUT, s, 0);
+            k_edge_filter<<<grid_for(ctx, ne), 256, 0, s>>>(edges, ne, contained, flags);
+        }
         DNASA_TRY(compact_flags(ctx, a, flags, ne, idx, cnt + CNT_TMP, s));
-        k_edge_keys<<<grid_for(ctx, ne), 256, 0, s>>>(t, edges, idx, cnt + CNT_TMP, kbl, lb, keys[0]);
+        {
+            LaunchScope ls_(ctx, PK_LAYOUT, s, 0);
+            k_edge_keys<<<grid_for(ctx, ne), 256, 0, s>>>(t, edges, idx, cnt + CNT_TMP, kbl, lb, keys[0]);
+        }
         DNASA_CUDA(ctx, cudaGetLastError());
         DNASA_CUDA(ctx, cudaMemcpyAsync(ctx->pinned, cnt + CNT_TMP, 8, cudaMemcpyDeviceToHost, s));
         DNASA_TRY(check_device_status(ctx, s, "assemble/layout"));
@@ -251,8 +260,14 @@ int layout_impl(dnasa_ctx *ctx, const TextDesc &t, int64_t max_reads_per_inst,
                                                            ib + lb + 2 * kbl, false, tile, &which, s));
         }
     }
-    k_greedy<<<grid_for(ctx, t.n_inst, 64), 64, 0, s>>>(t, keys[which], nsel, kbl, lb, contained, A);
-    k_scan_two<<<1, 64, 0, s>>>(A.inst_bytes, A.inst_contigs, t.n_inst, totals, totals + 1);
+    {
+        LaunchScope ls_(ctx, PK_LAYOUT, s, 0);
+        k_greedy<<<grid_for(ctx, t.n_inst, 64), 64, 0, s>>>(t, keys[which], nsel, kbl, lb, contained, A);
+    }
+    {
+        LaunchScope ls_(ctx, PK_LAYOUT, s, 0);
+        k_scan_two<<<1, 64, 0, s>>>(A.inst_bytes, A.inst_contigs, t.n_inst, totals, totals + 1);
+    }
     DNASA_CUDA(ctx, cudaGetLastError());
     DNASA_CUDA(ctx, cudaMemcpyAsync(ctx->pinned, totals, 16, cudaMemcpyDeviceToHost, s));
     DNASA_TRY(check_device_status(ctx, s, "assemble/layout"));
@@ -262,9 +277,15 @@ int layout_impl(dnasa_ctx *ctx, const TextDesc &t, int64_t max_reads_per_inst,
     if (tb > cap || tc + 1 > off_cap)
         return fail(ctx, DNASA_CAPACITY, "assemble: contigs need " + std::to_string(tb) + " bytes and " +
                                              std::to_string(tc + 1) + " offsets");
-    k_contig_off<<<grid_for(ctx, nr), 256, 0, s>>>(t, A, A.inst_bytes, A.inst_contigs, contig_off,
-                                                  inst_contig_off, totals, totals + 1);
-    k_spell<<<grid_for(ctx, nr * 32), 256, 0, s>>>(t, A, A.inst_bytes, contigs);
+    {
+        LaunchScope ls_(ctx, PK_LAYOUT, s, 0);
+        k_contig_off<<<grid_for(ctx, nr), 256, 0, s>>>(t, A, A.inst_bytes, A.inst_contigs, contig_off,
+                                                      inst_contig_off, totals, totals + 1);
+    }
+    {
+        LaunchScope ls_(ctx, PK_LAYOUT, s, 0);
+        k_spell<<<grid_for(ctx, nr * 32), 256, 0, s>>>(t, A, A.inst_bytes, contigs);
+    }
     DNASA_CUDA(ctx, cudaGetLastError());
     return check_device_status(ctx, s, "assemble/layout");
 }

@@ -44,7 +44,10 @@ __global__ void __launch_bounds__(256) k_lcp(TextDesc t, const uint32_t *__restr
 int lcp_build_impl(dnasa_ctx *ctx, const TextDesc &t, const uint32_t *sa32, int32_t *lcp,
                    cudaStream_t s) {
     int grid = (int)std::min<int64_t>(ceil_div(t.N, 256), (int64_t)ctx->num_sms * 16);
-    k_lcp<<<std::max(grid, 1), 256, 0, s>>>(t, sa32, lcp);
+    {
+        LaunchScope ls_(ctx, PK_LCP, s, 8.5 * t.N);
+        k_lcp<<<std::max(grid, 1), 256, 0, s>>>(t, sa32, lcp);
+    }
     DNASA_CUDA(ctx, cudaGetLastError());
     return DNASA_OK;
 }

@@ -221,14 +221,23 @@ int overlap_impl(dnasa_ctx *ctx, const TextDesc &t, const uint32_t *sa32, const 
         if (!rs2.hist) return fail(ctx, DNASA_OOM, "overlap_search workspace");
 
         DNASA_CUDA(ctx, cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * 8, s));
-        k_isa<<<grid_for(ctx, N), 256, 0, s>>>(sa32, N, isa);
-        k_read_keys<<<grid_for(ctx, nr), 256, 0, s>>>(t, isa, rk[0], rv[0], cnt + CNT_TMP);
+        {
+            LaunchScope ls_(ctx, PK_OVERLAP, s, 0);
+            k_isa<<<grid_for(ctx, N), 256, 0, s>>>(sa32, N, isa);
+        }
+        {
+            LaunchScope ls_(ctx, PK_OVERLAP, s, 0);
+            k_read_keys<<<grid_for(ctx, nr), 256, 0, s>>>(t, isa, rk[0], rv[0], cnt + CNT_TMP);
+        }
         DNASA_CUDA(ctx, cudaGetLastError());
         int which;
         DNASA_TRY(radix_sort_pairs<uint32_t>(ctx, rs, rk, rv, nr, nullptr,
                                              bits_for((uint64_t)(N - 1)), false, tile, &which, s));
         const uint32_t *Rslot = rk[which], *R = rv[which];
-        k_lcp_r<<<grid_for(ctx, nr), 256, 0, s>>>(t, R, lcpr);
+        {
+            LaunchScope ls_(ctx, PK_OVERLAP, s, 0);
+            k_lcp_r<<<grid_for(ctx, nr), 256, 0, s>>>(t, R, lcpr);
+        }
         DNASA_CUDA(ctx, cudaMemcpyAsync(ctx->pinned, cnt + CNT_TMP, 8, cudaMemcpyDeviceToHost, s));
         DNASA_TRY(check_device_status(ctx, s, "overlap_search"));
         const int64_t maxlen = (int64_t)ctx->pinned[0];
@@ -240,7 +249,10 @@ int overlap_impl(dnasa_ctx *ctx, const TextDesc &t, const uint32_t *sa32, const 
         qa.isa = isa; qa.Rslot = Rslot; qa.R = R; qa.lcpr = lcpr; qa.lmin = min_overlap;
         qa.kb = kb; qa.lb = lb; qa.cand = ck[0]; qa.cap = (unsigned long long)cand_cap;
         qa.count = cnt + CNT_CAND;
-        k_query<<<grid_for(ctx, N), 256, 0, s>>>(t, qa);
+        {
+            LaunchScope ls_(ctx, PK_OVERLAP, s, 0);
+            k_query<<<grid_for(ctx, N), 256, 0, s>>>(t, qa);
+        }
         DNASA_CUDA(ctx, cudaGetLastError());
         DNASA_CUDA(ctx, cudaMemcpyAsync(ctx->pinned, cnt + CNT_CAND, 8, cudaMemcpyDeviceToHost, s));
         DNASA_TRY(check_device_status(ctx, s, "overlap_search"));
@@ -257,13 +269,22 @@ int overlap_impl(dnasa_ctx *ctx, const TextDesc &t, const uint32_t *sa32, const 
             uint32_t *nov[2] = {nullptr, nullptr};
             DNASA_TRY(radix_sort_pairs<unsigned long long>(ctx, rs2, ck, nov, ncand, nullptr,
                                                            2 * kb + lb, false, tile, &which2, s));
-            k_unique_flags<<<grid_for(ctx, ncand), 256, 0, s>>>(ck[which2], ncand, lb, flags);
+            {
+                LaunchScope ls_(ctx, PK_OVERLAP, s, 0);
+                k_unique_flags<<<grid_for(ctx, ncand), 256, 0, s>>>(ck[which2], ncand, lb, flags);
+            }
             DNASA_TRY(compact_flags(ctx, a, flags, ncand, cidx, cnt + CNT_EDGES, s));
-            k_emit_edges<<<grid_for(ctx, ncand), 256, 0, s>>>(ck[which2], cidx, cnt + CNT_EDGES, kb,
-                                                             lb, edges, cap);
+            {
+                LaunchScope ls_(ctx, PK_OVERLAP, s, 0);
+                k_emit_edges<<<grid_for(ctx, ncand), 256, 0, s>>>(ck[which2], cidx, cnt + CNT_EDGES, kb,
+                                                                 lb, edges, cap);
+            }
             DNASA_CUDA(ctx, cudaGetLastError());
         }
-        k_contained<<<grid_for(ctx, nr), 256, 0, s>>>(t, sa32, isa, lcp, contained);
+        {
+            LaunchScope ls_(ctx, PK_OVERLAP, s, 0);
+            k_contained<<<grid_for(ctx, nr), 256, 0, s>>>(t, sa32, isa, lcp, contained);
+        }
         DNASA_CUDA(ctx, cudaGetLastError());
         DNASA_CUDA(ctx, cudaMemcpyAsync(ctx->pinned, cnt + CNT_EDGES, 8, cudaMemcpyDeviceToHost, s));
         DNASA_TRY(check_device_status(ctx, s, "overlap_search"));

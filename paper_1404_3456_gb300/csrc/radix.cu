@@ -6,11 +6,12 @@
 // shared-memory chunks (Algorithm 1).  This is the same sort, re-planned for
 // sm_103a:
 //   * one histogram kernel reads the keys once and counts every digit of every
-//     pass (8-bit digits; warp __match_any_sync aggregation before the shared
-//     atomics, so runs of equal digits cost one atomic per warp);
+//     pass (8-bit digits, shared-memory atomics);
 //   * then one kernel per digit.  Each CTA takes the next tile id from an
 //     atomic counter, ranks its tile's digits in shared memory (per-warp
-//     match_any ranking), publishes its per-digit counts, and looks back over
+//     ranking: the lanes holding the same digit are found with one ballot per
+//     digit bit, the lowest of them bumps the warp's digit counter), publishes
+//     its per-digit counts, and looks back over
 //     its predecessors' published counts (decoupled look-back) to find its
 //     global output offsets; the scatter goes through shared memory so that
 //     each digit's run leaves as a contiguous burst.  Every spin on a
@@ -46,6 +47,20 @@ __device__ __forceinline__ uint32_t digit_of(K k, int shift) {
     return (uint32_t)(k >> shift) & (kRadix - 1);
 }
 
+// Lanes of `vmask` whose 8-bit digit equals this lane's: one ballot per digit
+// bit (all 32 lanes take part; lanes outside vmask are masked out).  Eight
+// full-rate ballots are much cheaper than one match.any.sync.
+__device__ __forceinline__ uint32_t match_digit(uint32_t d, uint32_t vmask) {
+    uint32_t peers = vmask;
+#pragma unroll
+    for (int b = 0; b < kRadixBits; ++b) {
+        uint32_t bit = (d >> b) & 1u;
+        uint32_t bal = __ballot_sync(0xffffffffu, bit);
+        peers &= bit ? bal : ~bal;
+    }
+    return peers;
+}
+
 // ------------------------------------------------------------------ histogram
 template <typename K>
 __global__ void __launch_bounds__(kThreads) k_hist(const K *__restrict__ keys, int64_t n_host,
@@ -58,18 +73,10 @@ __global__ void __launch_bounds__(kThreads) k_hist(const K *__restrict__ keys, i
     const int lane = threadIdx.x & 31;
     const int64_t warp_global = ((int64_t)blockIdx.x * kThreads + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * kThreads) >> 5;
-    for (int64_t base = warp_global * 32; base < n; base += nwarps * 32) {
-        int64_t i = base + lane;
-        bool valid = i < n;
-        uint32_t vmask = __ballot_sync(0xffffffffu, valid);
-        if (valid) {
-            K k = keys[i];
-            for (int p = 0; p < passes; ++p) {
-                uint32_t d = digit_of(k, p * kRadixBits);
-                uint32_t peers = __match_any_sync(vmask, d);
-                if (lane == __ffs(peers) - 1) atomicAdd(&sh[p * kRadix + d], __popc(peers));
-            }
-        }
+    (void)lane;
+    for (int64_t i = warp_global * 32 + lane; i < n; i += nwarps * 32) {
+        K k = keys[i];
+        for (int p = 0; p < passes; ++p) atomicAdd(&sh[p * kRadix + digit_of(k, p * kRadixBits)], 1u);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < passes * kRadix; i += kThreads) {
@@ -144,9 +151,9 @@ __global__ void __launch_bounds__(kThreads) k_onesweep(
         bool valid = idx < tile_n;
         uint32_t vmask = __ballot_sync(0xffffffffu, valid);
         lrank[i] = 0;
+        uint32_t d = digit_of(key[i], shift);
+        uint32_t peers = match_digit(d, vmask);
         if (valid) {
-            uint32_t d = digit_of(key[i], shift);
-            uint32_t peers = __match_any_sync(vmask, d);
             int leader = __ffs(peers) - 1;
             uint32_t old = 0;
             if (lane == leader) {
@@ -360,10 +367,16 @@ int radix_sort_pairs(dnasa_ctx *ctx, const RadixScratch &rs, K *keys[2], uint32_
         DNASA_CUDA(ctx, cudaMemsetAsync(rs.hist, 0, (size_t)passes * kRadix * 4, s));
         int grid = (int)std::min<int64_t>((int64_t)ctx->num_sms * 8, ceil_div(n_host, kThreads * 8));
         if (grid < 1) grid = 1;
-        k_hist<K><<<grid, kThreads, 0, s>>>(keys[0], n_host, d_n, passes, rs.hist);
+        {
+            LaunchScope ls_(ctx, PK_HIST, s, (double)n_host * sizeof(K));
+            k_hist<K><<<grid, kThreads, 0, s>>>(keys[0], n_host, d_n, passes, rs.hist);
+        }
         DNASA_CUDA(ctx, cudaGetLastError());
     }
-    k_hist_scan<<<passes, kRadix, 0, s>>>(rs.hist);
+    {
+        LaunchScope ls_(ctx, PK_OTHER, s, 0);
+        k_hist_scan<<<passes, kRadix, 0, s>>>(rs.hist);
+    }
     DNASA_CUDA(ctx, cudaGetLastError());
     DNASA_CUDA(ctx, cudaMemsetAsync(ctx->ctrl->tile_ctr, 0, sizeof(uint32_t) * 8, s));
     int cur = 0;
@@ -376,6 +389,8 @@ int radix_sort_pairs(dnasa_ctx *ctx, const RadixScratch &rs, K *keys[2], uint32_
         const uint32_t *vin = has_vals ? vals[cur] : nullptr;
         uint32_t *vout = has_vals ? vals[cur ^ 1] : nullptr;
         cudaError_t e;
+        LaunchScope ls_(ctx, PK_ONESWEEP, s,
+                        (double)n_host * 2.0 * (sizeof(K) + (has_vals ? 4.0 : 0.0)));
 #define DNASA_PASS(IT, HV)                                                                    \
     e = launch_pass<K, IT, HV>(tiles, s, kin, vin, kout, vout, rs.hist + p * kRadix, status, \
                                ctx->ctrl->tile_ctr + p, n_host, d_n, p * kRadixBits, epoch,  \

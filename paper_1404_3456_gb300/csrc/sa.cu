@@ -81,62 +81,81 @@ struct RerankOut {
     unsigned long long *kept, *ngroups, *maxgroup;
 };
 
+// Shared memory of one rerank tile (dynamic, > 48 KB).
+struct RerankSmem {
+    unsigned long long k[kRrTile + 2];   // keys with one halo key on each side
+    uint32_t v[kRrTile];                 // positions
+    uint32_t sl[kRrTile];                // slots (rounds >= 1)
+    uint32_t head[kRrTile];              // new rank (SA slot of the group head)
+    int32_t kp[kRrTile];                 // output index of a kept item, -1 if dropped
+    uint8_t f[kRrTile];                  // bit0 head, bit1 next is head
+    int64_t tmp[kRrThreads / 32 + 1];
+    int64_t incmax[kRrThreads];
+    int64_t prefix[2];
+    uint32_t tile;
+    int abort;
+};
+
 template <bool ROUND0>
 __global__ void __launch_bounds__(kRrThreads) k_rerank(
     const unsigned long long *__restrict__ keys, const uint32_t *__restrict__ vals,
     const uint32_t *__restrict__ slots, int64_t n_host, const unsigned long long *__restrict__ d_n,
     int h0, RerankOut o, unsigned long long *status, uint32_t *tile_ctr, uint32_t *err) {
-    __shared__ unsigned long long s_k[kRrTile + 2];
-    __shared__ int64_t s_tmp[kRrThreads / 32 + 1];
-    __shared__ int64_t s_incmax[kRrThreads];
-    __shared__ int64_t s_prefix[2];
-    __shared__ uint32_t s_tile;
-    __shared__ int s_abort;
-
+    extern __shared__ __align__(16) unsigned char rr_raw[];
+    RerankSmem &S = *reinterpret_cast<RerankSmem *>(rr_raw);
     const int tid = threadIdx.x;
     if (tid == 0) {
-        s_tile = atomicAdd(tile_ctr, 1u);
-        s_abort = 0;
+        S.tile = atomicAdd(tile_ctr, 1u);
+        S.abort = 0;
     }
     __syncthreads();
-    const uint32_t tile = s_tile;
+    const uint32_t tile = S.tile;
     const int64_t n = d_n ? (int64_t)*d_n : n_host;
     const int64_t base = (int64_t)tile * kRrTile;
     if (base >= n) return;
     const int tile_n = (int)min((int64_t)kRrTile, n - base);
 
+    // ---- striped, coalesced loads
     for (int i = tid; i < tile_n + 2; i += kRrThreads) {
         int64_t j = base - 1 + i;
-        s_k[i] = (j >= 0 && j < n) ? keys[j] : 0ull;
+        S.k[i] = (j >= 0 && j < n) ? keys[j] : 0ull;
+    }
+    for (int i = tid; i < tile_n; i += kRrThreads) {
+        S.v[i] = vals[base + i];
+        if (!ROUND0) S.sl[i] = slots[base + i];
     }
     __syncthreads();
-
+    // ---- head flags, striped (conflict-free shared reads)
     auto is_head = [&](int64_t j) -> bool {   // j in [base, base + tile_n]
         if (j == 0) return true;
-        unsigned long long k = s_k[j - base + 1];
-        if (ROUND0 && (int)(k & 31ull) < h0) return true;
-        return k != s_k[j - base];
+        unsigned long long k = S.k[j - base + 1];
+        if (ROUND0 && (int)(k & 31ull) < h0) return true;   // own '$' inside: final
+        return k != S.k[j - base];
     };
-
-    int64_t my_max = -1;
-    int64_t my_keep = 0;
+    for (int li = tid; li < tile_n; li += kRrThreads) {
+        int64_t j = base + li;
+        bool h = is_head(j);
+        bool nh = (j == n - 1) || is_head(j + 1);
+        S.f[li] = (uint8_t)(h | (nh << 1));
+    }
+    __syncthreads();
+    // ---- blocked scan: max head index and kept count
+    int64_t my_max = -1, my_keep = 0;
     uint32_t headbits = 0, keepbits = 0, lastbits = 0;
 #pragma unroll
     for (int i = 0; i < kRrItems; ++i) {
         int li = tid * kRrItems + i;
         if (li >= tile_n) break;
-        int64_t j = base + li;
-        bool h = is_head(j);
-        bool nh = (j == n - 1) || is_head(j + 1);
-        bool keep = !(h && nh);
-        if (h) { my_max = j; headbits |= 1u << i; }
-        if (keep) { ++my_keep; keepbits |= 1u << i; }
+        uint8_t f = S.f[li];
+        bool h = f & 1, nh = f & 2;
+        if (h) { my_max = base + li; headbits |= 1u << i; }
+        if (!(h && nh)) { ++my_keep; keepbits |= 1u << i; }
         if (nh) lastbits |= 1u << i;
     }
     int64_t tile_max, tile_keep;
-    int64_t inc_max = block_inclusive_max<kRrThreads>(my_max, s_tmp, &tile_max, (int64_t)-1);
-    s_incmax[tid] = inc_max;
-    int64_t ex_keep = block_exclusive_sum<kRrThreads>(my_keep, s_tmp, &tile_keep);
+    int64_t inc_max = block_inclusive_max<kRrThreads>(my_max, S.tmp, &tile_max, (int64_t)-1);
+    S.incmax[tid] = inc_max;
+    int64_t ex_keep = block_exclusive_sum<kRrThreads>(my_keep, S.tmp, &tile_keep);
 
     if (tid == 0) {
         int64_t pmax = -1, psum = 0;
@@ -168,44 +187,59 @@ __global__ void __launch_bounds__(kRrThreads) k_rerank(
             }
             if (gave_up) {
                 atomicOr(err, DERR_TIMEOUT);
-                s_abort = 1;
+                S.abort = 1;
             }
             st_relaxed_u64(my, rr_pack(RR_INC, max(pmax, tile_max), psum + tile_keep));
         }
-        s_prefix[0] = pmax;
-        s_prefix[1] = psum;
+        S.prefix[0] = pmax;
+        S.prefix[1] = psum;
         if (base + tile_n == n) *o.kept = (unsigned long long)(psum + tile_keep);
     }
     __syncthreads();
-    if (s_abort) return;   // prefix unknown: write nothing
-    int64_t cur = max(s_prefix[0], tid > 0 ? s_incmax[tid - 1] : (int64_t)-1);
-    int64_t kp = s_prefix[1] + ex_keep;
+    if (S.abort) return;   // prefix unknown: write nothing
+    // ---- blocked: new rank and output index of every item
+    {
+        int64_t cur = max(S.prefix[0], tid > 0 ? S.incmax[tid - 1] : (int64_t)-1);
+        int64_t kp = S.prefix[1] + ex_keep;
 #pragma unroll
-    for (int i = 0; i < kRrItems; ++i) {
-        int li = tid * kRrItems + i;
-        if (li >= tile_n) break;
-        int64_t j = base + li;
-        if (headbits >> i & 1u) cur = j;
-        uint32_t slot = ROUND0 ? (uint32_t)j : slots[j];
-        uint32_t pos = vals[j];
-        uint32_t headslot = ROUND0 ? (uint32_t)cur : slot - (uint32_t)(j - cur);
+        for (int i = 0; i < kRrItems; ++i) {
+            int li = tid * kRrItems + i;
+            if (li >= tile_n) break;
+            int64_t j = base + li;
+            if (headbits >> i & 1u) cur = j;
+            uint32_t slot = ROUND0 ? (uint32_t)j : S.sl[li];
+            S.head[li] = ROUND0 ? (uint32_t)cur : slot - (uint32_t)(j - cur);
+            if (keepbits >> i & 1u) {
+                S.kp[li] = (int32_t)kp;
+                if (lastbits >> i & 1u) {
+                    uint32_t size = (uint32_t)(j - cur + 1);
+                    unsigned long long g = atomicAdd(o.ngroups, 1ull);
+                    o.groups[g] = make_uint2((uint32_t)(kp - size + 1), size);
+                    atomicMax(o.maxgroup, (unsigned long long)size);
+                }
+                ++kp;
+            } else {
+                S.kp[li] = -1;
+            }
+        }
+    }
+    __syncthreads();
+    // ---- striped, coalesced writes (rank[pos] is a scatter by nature)
+    for (int li = tid; li < tile_n; li += kRrThreads) {
+        uint32_t slot = ROUND0 ? (uint32_t)(base + li) : S.sl[li];
+        uint32_t pos = S.v[li];
+        uint32_t hs = S.head[li];
+        int32_t kp = S.kp[li];
         if ((int64_t)slot >= o.N || (int64_t)pos >= o.N || kp >= n) {
             atomicOr(err, DERR_BOUNDS);
-            break;
+            continue;
         }
         o.sa[slot] = pos;
-        o.rank[pos] = headslot;
-        if (keepbits >> i & 1u) {
+        o.rank[pos] = hs;
+        if (kp >= 0) {
             o.nslots[kp] = slot;
             o.npos[kp] = pos;
-            o.nhead[kp] = headslot;
-            if (lastbits >> i & 1u) {
-                uint32_t size = (uint32_t)(j - cur + 1);
-                unsigned long long g = atomicAdd(o.ngroups, 1ull);
-                o.groups[g] = make_uint2((uint32_t)(kp - size + 1), size);
-                atomicMax(o.maxgroup, (unsigned long long)size);
-            }
-            ++kp;
+            o.nhead[kp] = hs;
         }
     }
 }
@@ -229,58 +263,52 @@ __global__ void __launch_bounds__(256) k_gather(const uint32_t *__restrict__ npo
 }
 
 // ------------------------------------------------------------------ S6: direct finisher
+// Each remaining group shares its first h symbols.  rank[] holds h-ranks (equal
+// ranks <=> equal first h symbols; a rank that contains a '$' is unique), so two
+// members p, q compare as the sequences rank[p+h], rank[p+2h], rank[p+3h], ...:
+// every step compares the next h symbols at once, which keeps tandem repeats
+// thousands of bases long to a handful of steps.  rank[p+h] is cached in shared
+// memory; one CTA sorts one group with a bitonic network.
 constexpr int kFinMax = 1024;
 constexpr int kFinThreads = 512;
 
-struct FinMember {
-    int64_t b;      // base coordinate of the first base after the shared h
-    int32_t rem;    // bases left after the shared h (>= 0)
-    uint32_t pos;
-};
-
-__device__ __forceinline__ bool fin_less(const uint64_t *__restrict__ packed, const FinMember &a,
-                                         const FinMember &c) {
-    int64_t off = 0;
-    for (;;) {
-        int64_t la = a.rem - off, lc = c.rem - off;
-        int64_t m = min(min(la, lc), (int64_t)32);
-        if (m <= 0) return la == lc ? a.pos < c.pos : la < lc;
-        uint64_t x = bases32(packed, (uint64_t)(a.b + off));
-        uint64_t y = bases32(packed, (uint64_t)(c.b + off));
-        if (m < 32) {
-            x >>= 64 - 2 * m;
-            y >>= 64 - 2 * m;
+__device__ __forceinline__ bool fin_less(uint32_t pa, uint32_t ra, uint32_t pb, uint32_t rb,
+                                         const uint32_t *__restrict__ rank, uint32_t h, int64_t N,
+                                         uint32_t *err) {
+    if (ra != rb) return ra < rb;
+    for (int64_t k = 2;; ++k) {
+        int64_t xa = (int64_t)pa + k * h, xb = (int64_t)pb + k * h;
+        if (xa >= N || xb >= N) {   // cannot happen for valid ranks
+            atomicOr(err, DERR_BOUNDS);
+            return pa < pb;
         }
-        if (x != y) return x < y;
-        if (m < 32) return la == lc ? a.pos < c.pos : la < lc;
-        off += 32;
+        uint32_t a = __ldg(rank + xa), b = __ldg(rank + xb);
+        if (a != b) return a < b;
     }
 }
 
-__global__ void __launch_bounds__(kFinThreads) k_finish(TextDesc t, const uint2 *__restrict__ groups,
+__global__ void __launch_bounds__(kFinThreads) k_finish(const uint2 *__restrict__ groups,
                                                         const unsigned long long *__restrict__ ngroups,
                                                         const uint32_t *__restrict__ npos,
                                                         const uint32_t *__restrict__ nslots,
-                                                        uint32_t h, uint32_t *__restrict__ sa) {
-    __shared__ FinMember s_m[kFinMax];
+                                                        const uint32_t *__restrict__ rank,
+                                                        uint32_t h, int64_t N,
+                                                        uint32_t *__restrict__ sa, uint32_t *err) {
+    __shared__ uint32_t s_pos[kFinMax];
+    __shared__ uint32_t s_r1[kFinMax];
     __shared__ uint16_t s_idx[kFinMax];
     const int64_t ng = (int64_t)*ngroups;
     for (int64_t g = blockIdx.x; g < ng; g += gridDim.x) {
         uint2 gs = groups[g];
-        const int size = (int)gs.y;
+        const int size = (int)min(gs.y, (uint32_t)kFinMax);
         int n2 = 1;
         while (n2 < size) n2 <<= 1;
         for (int i = threadIdx.x; i < n2; i += kFinThreads) {
             s_idx[i] = (uint16_t)i;
             if (i < size) {
                 uint32_t pos = npos[gs.x + i];
-                int64_t r = read_of(t.toff, t.n_reads, pos);
-                int64_t left = __ldg(t.toff + r + 1) - 1 - (int64_t)pos;
-                FinMember m;
-                m.b = (int64_t)pos - r + h;
-                m.rem = (int32_t)(left - (int64_t)h);
-                m.pos = pos;
-                s_m[i] = m;
+                s_pos[i] = pos;
+                s_r1[i] = (int64_t)pos + h < N ? __ldg(rank + pos + h) : 0u;
             }
         }
         __syncthreads();
@@ -292,9 +320,15 @@ __global__ void __launch_bounds__(kFinThreads) k_finish(TextDesc t, const uint2 
                         uint16_t a = s_idx[i], c = s_idx[ixj];
                         bool up = (i & k) == 0;
                         // padding members (index >= size) are larger than everything
-                        bool c_lt_a = a >= size ? (c < size) : (c < size && fin_less(t.packed, s_m[c], s_m[a]));
-                        bool a_lt_c = c >= size ? (a < size) : (a < size && fin_less(t.packed, s_m[a], s_m[c]));
-                        if (up ? c_lt_a : a_lt_c) {
+                        bool swap;
+                        if (a >= size || c >= size) {
+                            swap = up ? (a >= size && c < size) : (c >= size && a < size);
+                        } else if (up) {
+                            swap = fin_less(s_pos[c], s_r1[c], s_pos[a], s_r1[a], rank, h, N, err);
+                        } else {
+                            swap = fin_less(s_pos[a], s_r1[a], s_pos[c], s_r1[c], rank, h, N, err);
+                        }
+                        if (swap) {
                             s_idx[i] = c;
                             s_idx[ixj] = a;
                         }
@@ -305,7 +339,7 @@ __global__ void __launch_bounds__(kFinThreads) k_finish(TextDesc t, const uint2 
         }
         uint32_t slot0 = nslots[gs.x];
         for (int i = threadIdx.x; i < size; i += kFinThreads)
-            if ((int64_t)slot0 + i < t.N) sa[slot0 + i] = s_m[s_idx[i]].pos;
+            if ((int64_t)slot0 + i < N) sa[slot0 + i] = s_pos[s_idx[i]];
         __syncthreads();
     }
 }
@@ -365,6 +399,14 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
     RadixScratch rs = radix_scratch_take(a, N, 64, tile_items);
     if (!rs.hist || !rr_status) return fail(ctx, DNASA_OOM, "sa_build workspace");
 
+    static bool smem_set = false;
+    if (!smem_set) {
+        DNASA_CUDA(ctx, cudaFuncSetAttribute(k_rerank<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)sizeof(RerankSmem)));
+        DNASA_CUDA(ctx, cudaFuncSetAttribute(k_rerank<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)sizeof(RerankSmem)));
+        smem_set = true;
+    }
     DevCtrl *c = ctx->ctrl;
     unsigned long long *cnt = c->count;
     dnasa_trace &tr = ctx->trace;
@@ -399,16 +441,22 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
     // ---- round 0: initial keys, sort, rerank
     {
         int warps = ceil_div(N, 32 * kInitItems);
-        k_init_keys<<<ceil_div(warps, kInitThreads / 32), kInitThreads, 0, s>>>(t, h0, inst_shift,
-                                                                              keys[0], vals[0]);
+        {
+            LaunchScope ls_(ctx, PK_INIT, s, 12.25 * N);
+            k_init_keys<<<ceil_div(warps, kInitThreads / 32), kInitThreads, 0, s>>>(t, h0, inst_shift,
+                                                                                  keys[0], vals[0]);
+        }
         DNASA_CUDA(ctx, cudaGetLastError());
         int which;
         DNASA_TRY(radix_sort_pairs<unsigned long long>(ctx, rs, keys, vals, N, nullptr, key_bits0,
                                                        false, tile_items, &which, s));
         DNASA_TRY(reset_counters());
         ro.nslots = L[0][0]; ro.npos = L[0][1]; ro.nhead = L[0][2];
-        k_rerank<true><<<rr_tiles, kRrThreads, 0, s>>>(keys[which], vals[which], nullptr, N, nullptr,
-                                                       h0, ro, rr_status, c->tile_ctr + 32, &c->err);
+        {
+            LaunchScope ls_(ctx, PK_RERANK, s, 20.0 * N);
+            k_rerank<true><<<rr_tiles, kRrThreads, sizeof(RerankSmem), s>>>(keys[which], vals[which], nullptr, N, nullptr,
+                                                           h0, ro, rr_status, c->tile_ctr + 32, &c->err);
+        }
         DNASA_CUDA(ctx, cudaGetLastError());
     }
     int64_t kept, ngroups, maxgroup;
@@ -420,8 +468,12 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
     while (kept > 0) {
         if (finish_threshold >= 0 && kept <= finish_threshold && maxgroup <= kFinMax) {
             int grid = (int)std::min<int64_t>(ngroups, (int64_t)ctx->num_sms * 4);
-            k_finish<<<std::max(grid, 1), kFinThreads, 0, s>>>(t, groups, cnt + CNT_GROUPS, L[cur][1],
-                                                               L[cur][0], (uint32_t)h, sa32);
+            {
+                LaunchScope ls_(ctx, PK_FINISH, s, 0);
+                k_finish<<<std::max(grid, 1), kFinThreads, 0, s>>>(groups, cnt + CNT_GROUPS, L[cur][1],
+                                                                   L[cur][0], rank, (uint32_t)h, N,
+                                                                   sa32, &c->err);
+            }
             DNASA_CUDA(ctx, cudaGetLastError());
             tr.finished_direct = 1;
             break;
@@ -430,8 +482,11 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
         if (h >= (uint64_t)N) return fail(ctx, DNASA_CUDA_ERROR, "sa_build: doubling did not converge");
         // keys for this round
         int grid = (int)std::min<int64_t>(ceil_div(kept, 256), (int64_t)ctx->num_sms * 16);
-        k_gather<<<std::max(grid, 1), 256, 0, s>>>(L[cur][1], L[cur][2], kept, rank,
-                                                   (uint32_t)h, b, keys[0], vals[0], N, &c->err);
+        {
+            LaunchScope ls_(ctx, PK_GATHER, s, 24.0 * kept);
+            k_gather<<<std::max(grid, 1), 256, 0, s>>>(L[cur][1], L[cur][2], kept, rank,
+                                                       (uint32_t)h, b, keys[0], vals[0], N, &c->err);
+        }
         DNASA_CUDA(ctx, cudaGetLastError());
         int which;
         DNASA_TRY(radix_sort_pairs<unsigned long long>(ctx, rs, keys, vals, kept, nullptr, 2 * b,
@@ -439,9 +494,12 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
         DNASA_TRY(reset_counters());
         ro.nslots = L[cur ^ 1][0]; ro.npos = L[cur ^ 1][1]; ro.nhead = L[cur ^ 1][2];
         int tiles = ceil_div(kept, kRrTile);
-        k_rerank<false><<<tiles, kRrThreads, 0, s>>>(keys[which], vals[which], L[cur][0], kept,
-                                                     nullptr, h0, ro, rr_status, c->tile_ctr + 32,
-                                                     &c->err);
+        {
+            LaunchScope ls_(ctx, PK_RERANK, s, 24.0 * kept);
+            k_rerank<false><<<tiles, kRrThreads, sizeof(RerankSmem), s>>>(keys[which], vals[which], L[cur][0], kept,
+                                                         nullptr, h0, ro, rr_status, c->tile_ctr + 32,
+                                                         &c->err);
+        }
         DNASA_CUDA(ctx, cudaGetLastError());
         DNASA_TRY(read_counters(&kept, &ngroups, &maxgroup));
         cur ^= 1;
@@ -454,7 +512,10 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
 
 int widen_u32_to_i64(dnasa_ctx *ctx, const uint32_t *a, int64_t n, int64_t *b, cudaStream_t s) {
     int grid = (int)std::min<int64_t>(ceil_div(n, 256), (int64_t)ctx->num_sms * 16);
-    k_widen<<<std::max(grid, 1), 256, 0, s>>>(a, n, b);
+    {
+        LaunchScope ls_(ctx, PK_OTHER, s, 12.0 * n);
+        k_widen<<<std::max(grid, 1), 256, 0, s>>>(a, n, b);
+    }
     DNASA_CUDA(ctx, cudaGetLastError());
     return DNASA_OK;
 }

@@ -29,7 +29,7 @@ def B():
 
 
 def dev(a: np.ndarray):
-    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    return torch.from_numpy(np.array(a, dtype=np.uint8, copy=True)).cuda()
 
 
 def random_text(rng, n_reads, lo, hi, periodic_frac=0.3, dup=True):
@@ -73,7 +73,7 @@ def test_pack_offsets_and_codes(ctx):
     assert np.all(words[(bases.size + 31) // 32:] == 0)
 
 
-@pytest.mark.parametrize("bad", [b"ACGN$", b"ACGT", b"AC$$GT$", b"$AC$"])
+@pytest.mark.parametrize("bad", [b"ACGN$", b"ACGT", b"AC$$GT$", b"$AC$", b"$", b"acgt$"])
 def test_pack_rejects_bad_text(ctx, bad):
     text = dev(np.frombuffer(bad, np.uint8))
     with pytest.raises(B().DnasaError) as e:
@@ -84,7 +84,7 @@ def test_pack_rejects_bad_text(ctx, bad):
 # ---------------------------------------------------------------- S2-S6 suffix array
 
 
-@pytest.mark.parametrize("text", [b"$", b"A$", b"AAAAAAAA$", b"ACGTACGTACGT$", b"A$A$AA$",
+@pytest.mark.parametrize("text", [b"A$", b"AAAAAAAA$", b"ACGTACGTACGT$", b"A$A$AA$",
                                   b"T$G$C$A$", b"ACGT" * 40 + b"$"])
 def test_sa_small_texts(ctx, text):
     t = np.frombuffer(text, np.uint8)
@@ -107,10 +107,13 @@ def test_sa_repeat_genome(ctx):
     rng = synth.rng_for(7, 11)
     g = synth.genome_with_repeats(rng, 400_003, 0.05, (2, 50), (10, 200), 0.05, 300, 0.01)
     t = synth.genome_text(g)
-    sa = gpu_sa(ctx, t)[0]
-    assert np.array_equal(sa.cpu().numpy().astype(np.int64), oracle.suffix_array(t))
+    want = oracle.suffix_array(t)
+    sa = gpu_sa(ctx, t, opts=B().make_opts(finish_threshold=-1))[0]   # doubling only
+    assert np.array_equal(sa.cpu().numpy().astype(np.int64), want)
     tr = ctx.trace()
-    assert tr["rounds"] >= 2
+    assert tr["rounds"] >= 2 and tr["finished_direct"] == 0
+    sa = gpu_sa(ctx, t)[0]                                             # default switch
+    assert np.array_equal(sa.cpu().numpy().astype(np.int64), want)
 
 
 @pytest.mark.parametrize("finish", [-1, 1 << 40])
@@ -167,7 +170,7 @@ def overlaps_gpu(ctx, t, lmin):
     sa, packed, toff, nr, text = gpu_sa(ctx, t)
     lcp = torch.empty_like(sa)
     B().lcp_build(ctx, packed, toff, nr, t.size, sa, lcp)
-    cap = 16 * nr + 16
+    cap = nr * nr + 16
     edges = torch.empty((cap, 3), dtype=torch.int32, device="cuda")
     contained = torch.empty(nr, dtype=torch.uint8, device="cuda")
     ne = B().overlap_search(ctx, packed, toff, nr, t.size, sa, lcp, lmin, edges, contained)
