@@ -63,14 +63,15 @@ typedef struct dnasa_ctx dnasa_ctx;
 
 /* Options of the suffix-array build.  Zero in any field selects the default. */
 typedef struct {
-    int32_t digit_bits;        /* radix digit width of the LSD passes: 8 (default) */
-    int32_t tile_items;        /* items per onesweep tile: 3840 (default); other: 1920, 7680 */
+    int32_t digit_bits;        /* radix digit width of the LSD passes: 8 (default; the only one) */
+    int32_t tile_items;        /* items per onesweep tile: 3840 (default), 2048 or 5120 */
     int64_t finish_threshold;  /* when the suffixes still unsorted after a doubling round
                                   number at most this many, and every unsorted group has at
                                   most 1024 members, the rest is sorted by direct comparison
                                   of packed words; -1 = never; 0 = default */
-    int32_t max_rounds;        /* safety bound on doubling rounds (default 64) */
-    int32_t reserved;
+    int32_t max_rounds;        /* safety bound on doubling rounds (default 63) */
+    int32_t lookback;          /* look-back loads in flight per digit in a onesweep pass:
+                                  8 (default) or 1 */
 } dnasa_opts;
 
 /* One suffix-prefix overlap: the last L bases of fragment j equal the first L
@@ -139,6 +140,18 @@ int dnasa_profile(dnasa_ctx *ctx, int enable);
 int dnasa_profile_read(dnasa_ctx *ctx, dnasa_prof_entry *out, int max_entries, int *n_out);
 /* Kernel launches issued through this context since it was created. */
 uint64_t dnasa_launch_count(dnasa_ctx *ctx);
+
+/* ---- radix sort utility (Sec. IV radix sort; Algorithm 1 semantics) ---------- */
+
+/* Stable LSD radix sort of n (key, value) pairs by key bits [0, key_bits), with
+ * the same onesweep kernels the suffix-array build runs on.  Equal keys keep
+ * their input order, as the 1-bit split passes of Algorithm 1 do.
+ *   keys        device uint64[n], sorted in place
+ *   vals        device uint32[n] permuted with the keys, or NULL (keys only)
+ *   key_bits    1..64; tile_items and lookback as in dnasa_opts (0 = default)
+ * Enqueues only.  n < 2^32. */
+int dnasa_sort_pairs(dnasa_ctx *ctx, uint64_t *keys, uint32_t *vals, int64_t n, int key_bits,
+                     int tile_items, int lookback, void *stream);
 
 /* ---- S1: pack (Sec. III alphabet; the SA of Sec. IV is over this text) ------- */
 

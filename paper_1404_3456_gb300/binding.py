@@ -33,7 +33,7 @@ class DnasaError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("digit_bits", ctypes.c_int32), ("tile_items", ctypes.c_int32),
                 ("finish_threshold", ctypes.c_int64), ("max_rounds", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("lookback", ctypes.c_int32)]
 
 
 class Trace(ctypes.Structure):
@@ -65,6 +65,7 @@ _SIGS = {
     "dnasa_profile": (_INT, [_P, _INT]),
     "dnasa_profile_read": (_INT, [_P, ctypes.POINTER(ProfEntry), _INT, ctypes.POINTER(_INT)]),
     "dnasa_launch_count": (ctypes.c_uint64, [_P]),
+    "dnasa_sort_pairs": (_INT, [_P, _P, _P, _I64, _INT, _INT, _INT, _P]),
     "dnasa_pack": (_INT, [_P, _P, _I64, _P, _P, _I64, ctypes.POINTER(_I64), _P]),
     "sa_build": (_INT, [_P, _P, _P, _I64, _I64, _P, _INT, ctypes.POINTER(Opts), _P]),
     "lcp_build": (_INT, [_P, _P, _P, _I64, _I64, _P, _INT, _P, _P]),
@@ -164,8 +165,8 @@ class Context:
             pass
 
 
-def make_opts(digit_bits=0, tile_items=0, finish_threshold=0, max_rounds=0):
-    return Opts(digit_bits, tile_items, finish_threshold, max_rounds, 0)
+def make_opts(digit_bits=0, tile_items=0, finish_threshold=0, max_rounds=0, lookback=0):
+    return Opts(digit_bits, tile_items, finish_threshold, max_rounds, lookback)
 
 
 # ---------------------------------------------------------------- entry points
@@ -173,6 +174,13 @@ def make_opts(digit_bits=0, tile_items=0, finish_threshold=0, max_rounds=0):
 
 def packed_words(N: int) -> int:
     return int(lib().dnasa_packed_words(N))
+
+
+def dnasa_sort_pairs(ctx: Context, keys, vals=None, key_bits: int = 64, tile_items: int = 0,
+                     lookback: int = 0, stream=None):
+    """Stable radix sort in place: keys int64 (bit pattern of uint64), vals int32/uint32."""
+    ctx.check(lib().dnasa_sort_pairs(ctx.handle, _ptr(keys), _ptr(vals) if vals is not None else None,
+                                     keys.numel(), key_bits, tile_items, lookback, _stream(stream)))
 
 
 def dnasa_pack(ctx: Context, text, packed, toff, stream=None) -> int:

@@ -169,6 +169,8 @@ int sa_build(dnasa_ctx *ctx, const uint64_t *packed, const int64_t *toff, int64_
         return fail(ctx, DNASA_INVALID_ARG, "sa_build: tile_items must be 0, 2048, 3840 or 5120");
     if (opts && opts->digit_bits != 0 && opts->digit_bits != 8)
         return fail(ctx, DNASA_INVALID_ARG, "sa_build: digit_bits must be 0 or 8");
+    if (opts && opts->lookback != 0 && opts->lookback != 1 && opts->lookback != 8)
+        return fail(ctx, DNASA_INVALID_ARG, "sa_build: lookback must be 0, 1 or 8");
     cudaSetDevice(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
     TextDesc t = one_instance(packed, toff, n_reads, N);

@@ -105,7 +105,23 @@ __global__ void __launch_bounds__(kRadix) k_hist_scan(uint32_t *__restrict__ ghi
 }
 
 // ------------------------------------------------------------------ one digit pass
-template <typename K, int ITEMS, bool HAS_VALS>
+__device__ __forceinline__ void cp_async4(void *smem_dst, const void *gmem_src) {
+    unsigned sa = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_wait_all() {
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_all;" ::: "memory");
+}
+
+// Phases of one tile (the look-back latency is the only wait left on the path
+// between ranking and the global writes):
+//   1. take a tile id; start the values' loads into shared memory (cp.async);
+//   2. load keys; count the tile's digits; publish them (AGG);
+//   3. rank every key within its warp (stable); tile-local digit offsets;
+//   4. scatter keys, then values, into shared memory in digit order;
+//   5. look back over the predecessors' counts; publish the inclusive prefix;
+//   6. write keys and values, each digit's run as one contiguous burst.
+template <typename K, int ITEMS, bool HAS_VALS, int LBW>
 __global__ void __launch_bounds__(kThreads) k_onesweep(
     const K *__restrict__ kin, const uint32_t *__restrict__ vin, K *__restrict__ kout,
     uint32_t *__restrict__ vout, const uint32_t *__restrict__ bucket, unsigned long long *status,
@@ -124,97 +140,63 @@ __global__ void __launch_bounds__(kThreads) k_onesweep(
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) {
         s_misc[kWarps] = atomicAdd(tile_ctr, 1u);
-        s_misc[kWarps + 1] = 0;   // set when a look-back gave up: skip the scatter
+        s_misc[kWarps + 1] = 0;   // set when a look-back gave up: skip the writes
     }
     for (int i = tid; i < kWarps * kRadix; i += kThreads) s_whist[i] = 0;
+    for (int i = tid; i < kRadix; i += kThreads) s_count[i] = 0;
     __syncthreads();
     const uint32_t tile = s_misc[kWarps];
     const int64_t n = d_n ? (int64_t)*d_n : n_host;
     const int64_t base = (int64_t)tile * TILE;
     if (base >= n) return;   // uniform over the CTA; later tiles are empty too
     const int tile_n = (int)min((int64_t)TILE, n - base);
-
-    // ---- load (warp-striped: warp w owns [w*32*ITEMS, (w+1)*32*ITEMS) of the tile)
-    K key[ITEMS];
-    uint16_t lrank[ITEMS];
+    // warp-striped layout: warp w owns [w*32*ITEMS, (w+1)*32*ITEMS) of the tile
     const int wbase = warp * 32 * ITEMS;
+
+    // ---- 1. values start arriving in shared memory while the keys are ranked
+    if (HAS_VALS) {
+#pragma unroll
+        for (int i = 0; i < ITEMS; ++i) {
+            int idx = wbase + i * 32 + lane;
+            if (idx < tile_n) cp_async4(s_vals + idx, vin + base + idx);
+        }
+    }
+    // ---- 2. keys; the tile's digit counts, published before any ranking work
+    K key[ITEMS];
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
         int idx = wbase + i * 32 + lane;
         key[i] = idx < tile_n ? kin[base + idx] : K(0);
     }
-    // ---- rank within the warp, item by item (keeps tile order: stable)
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        int idx = wbase + i * 32 + lane;
+        if (idx < tile_n) atomicAdd(&s_count[digit_of(key[i], shift)], 1u);
+    }
+    __syncthreads();
+    for (int d = tid; d < kRadix; d += kThreads)
+        st_relaxed_u64(status + (size_t)tile * kRadix + d,
+                       lb_word(tile == 0 ? FLAG_INC : FLAG_AGG, epoch, s_count[d]));
+    // ---- 3. rank within the warp, item by item (tile order: stable).  The lanes
+    // holding the same digit are found by ballots; the lowest of them bumps the
+    // warp's counter for that digit and broadcasts the old count.
+    uint16_t lrank[ITEMS];
     uint32_t *wh = s_whist + warp * kRadix;
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
         int idx = wbase + i * 32 + lane;
         bool valid = idx < tile_n;
         uint32_t vmask = __ballot_sync(0xffffffffu, valid);
-        lrank[i] = 0;
         uint32_t d = digit_of(key[i], shift);
         uint32_t peers = match_digit(d, vmask);
-        if (valid) {
-            int leader = __ffs(peers) - 1;
-            uint32_t old = 0;
-            if (lane == leader) {
-                old = wh[d];
-                wh[d] = old + __popc(peers);
-            }
-            old = __shfl_sync(peers, old, leader);
-            lrank[i] = (uint16_t)(old + __popc(peers & lanemask_lt()));
-        }
+        int leader = peers ? __ffs(peers) - 1 : 0;
+        uint32_t old = 0;
+        if (valid && lane == leader) old = atomicAdd(&wh[d], (uint32_t)__popc(peers));
+        old = __shfl_sync(0xffffffffu, old, leader);
+        lrank[i] = (uint16_t)(old + __popc(peers & lanemask_lt()));
         __syncwarp();
     }
-    __syncthreads();
-    // ---- per digit: exclusive scan over warps, tile count
-    for (int d = tid; d < kRadix; d += kThreads) {
-        uint32_t run = 0;
-#pragma unroll
-        for (int w = 0; w < kWarps; ++w) {
-            uint32_t c = s_whist[w * kRadix + d];
-            s_whist[w * kRadix + d] = run;
-            run += c;
-        }
-        s_count[d] = run;
-    }
-    __syncthreads();
-    // ---- publish, look back, and form the global base of each digit
-    for (int d = tid; d < kRadix; d += kThreads) {
-        uint32_t c = s_count[d];
-        unsigned long long *my = status + (size_t)tile * kRadix + d;
-        unsigned long long excl = 0;
-        if (tile == 0) {
-            st_relaxed_u64(my, lb_word(FLAG_INC, epoch, c));
-        } else {
-            st_relaxed_u64(my, lb_word(FLAG_AGG, epoch, c));
-            int64_t t = (int64_t)tile - 1;
-            uint32_t spins = 0;
-            bool gave_up = false;
-            while (t >= 0) {
-                unsigned long long w = ld_relaxed_u64(status + (size_t)t * kRadix + d);
-                uint32_t we = (uint32_t)(w >> 54) & 0xFF;
-                unsigned long long flag = w & (3ull << 62);
-                if (flag == 0 || we != (epoch & 0xFF)) {
-                    if (++spins > kSpinLimit || ((spins & 1023) == 0 && ld_relaxed_u32(err) != 0)) {
-                        gave_up = true;
-                        break;
-                    }
-                    __nanosleep(32);
-                    continue;
-                }
-                excl += w & VAL_MASK;
-                if (flag == FLAG_INC) break;
-                --t;
-            }
-            if (gave_up) {
-                atomicOr(err, DERR_TIMEOUT);
-                s_misc[kWarps + 1] = 1;
-            }
-            st_relaxed_u64(my, lb_word(FLAG_INC, epoch, excl + c));
-        }
-        s_gbase[d] = bucket[d] + (uint32_t)excl;
-    }
-    // ---- tile-local exclusive scan of the digit counts (kThreads == kRadix)
+    // tile-local start of each digit (kThreads == kRadix: one digit per thread)
     {
         uint32_t v = s_count[tid];
         uint32_t x = v;
@@ -228,10 +210,17 @@ __global__ void __launch_bounds__(kThreads) k_onesweep(
         uint32_t off = 0;
         for (int w = 0; w < warp; ++w) off += s_misc[w];
         s_start[tid] = off + x - v;
+        // exclusive scan over warps of this digit's per-warp counts
+        uint32_t run = 0;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) {
+            uint32_t c = s_whist[w * kRadix + tid];
+            s_whist[w * kRadix + tid] = run;
+            run += c;
+        }
     }
     __syncthreads();
-    if (s_misc[kWarps + 1]) return;   // offsets unknown: write nothing
-    // ---- scatter keys into shared memory in digit order
+    // ---- 4. keys, then values, into shared memory in digit order
     uint16_t lpos[ITEMS];
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
@@ -244,26 +233,76 @@ __global__ void __launch_bounds__(kThreads) k_onesweep(
             s_keys[p] = key[i];
         }
     }
-    __syncthreads();
-    if (tid < kRadix) s_gbase[tid] -= s_start[tid];
-    __syncthreads();
-    for (int idx = tid; idx < tile_n; idx += kThreads) {
-        K k = s_keys[idx];
-        uint32_t o = s_gbase[digit_of(k, shift)] + (uint32_t)idx;
-        if (o < (uint64_t)n) kout[o] = k;
-        else atomicOr(err, DERR_BOUNDS);
-    }
     if (HAS_VALS) {
+        cp_async_commit_wait_all();
+        __syncthreads();
+        uint32_t v[ITEMS];
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) {
             int idx = wbase + i * 32 + lane;
-            if (idx < tile_n) s_vals[lpos[i]] = vin[base + idx];
+            v[i] = idx < tile_n ? s_vals[idx] : 0u;
         }
         __syncthreads();
-        for (int idx = tid; idx < tile_n; idx += kThreads) {
-            K k = s_keys[idx];
-            uint32_t o = s_gbase[digit_of(k, shift)] + (uint32_t)idx;
-            if (o < (uint64_t)n) vout[o] = s_vals[idx];
+#pragma unroll
+        for (int i = 0; i < ITEMS; ++i) {
+            int idx = wbase + i * 32 + lane;
+            if (idx < tile_n) s_vals[lpos[i]] = v[i];
+        }
+    }
+    // ---- 5. look back and form the global base of each digit
+    {
+        const int d = tid;
+        const uint32_t c = s_count[d];
+        unsigned long long excl = 0;
+        if (tile != 0) {
+            // probe LBW predecessors per round trip: LBW independent loads in
+            // flight, then consume them nearest first
+            int64_t t = (int64_t)tile - 1;
+            uint32_t spins = 0;
+            bool gave_up = false;
+            bool done = false;
+            while (!done) {
+                unsigned long long w[LBW];
+#pragma unroll
+                for (int k = 0; k < LBW; ++k)
+                    w[k] = t - k >= 0 ? ld_relaxed_u64(status + (size_t)(t - k) * kRadix + d)
+                                      : lb_word(FLAG_INC, epoch, 0);   // before tile 0: nothing
+                int k = 0;
+                for (; k < LBW; ++k) {
+                    uint32_t we = (uint32_t)(w[k] >> 54) & 0xFF;
+                    unsigned long long flag = w[k] & (3ull << 62);
+                    if (flag == 0 || we != (epoch & 0xFF)) break;   // not published yet
+                    excl += w[k] & VAL_MASK;
+                    if (flag == FLAG_INC) { done = true; break; }
+                }
+                if (done) break;
+                if (k == LBW) { t -= LBW; continue; }
+                t -= k;                                            // wait on tile t
+                if (++spins > kSpinLimit || ((spins & 1023) == 0 && ld_relaxed_u32(err) != 0)) {
+                    gave_up = true;
+                    break;
+                }
+                __nanosleep(32);
+            }
+            if (gave_up) {
+                atomicOr(err, DERR_TIMEOUT);
+                s_misc[kWarps + 1] = 1;
+            }
+            st_relaxed_u64(status + (size_t)tile * kRadix + d, lb_word(FLAG_INC, epoch, excl + c));
+        }
+        s_gbase[d] = bucket[d] + (uint32_t)excl - s_start[d];
+    }
+    __syncthreads();
+    if (s_misc[kWarps + 1]) return;   // offsets unknown: write nothing
+    // ---- 6. global writes
+    for (int idx = tid; idx < tile_n; idx += kThreads) {
+        K k = s_keys[idx];
+        uint32_t o = s_gbase[digit_of(k, shift)] + (uint32_t)idx;
+        if (o < (uint64_t)n) {
+            kout[o] = k;
+            if (HAS_VALS) vout[o] = s_vals[idx];
+        } else {
+            atomicOr(err, DERR_BOUNDS);
         }
     }
 }
@@ -275,13 +314,13 @@ size_t onesweep_smem() {
            (size_t)(kWarps * kRadix + 3 * kRadix + kWarps + 2) * 4;
 }
 
-template <typename K, int ITEMS, bool HAS_VALS>
+template <typename K, int ITEMS, bool HAS_VALS, int LBW>
 cudaError_t launch_pass(int tiles, cudaStream_t s, const K *kin, const uint32_t *vin, K *kout,
                         uint32_t *vout, const uint32_t *bucket, unsigned long long *status,
                         uint32_t *tile_ctr, int64_t n_host, const unsigned long long *d_n,
                         int shift, uint32_t epoch, uint32_t *err) {
     size_t smem = onesweep_smem<K, ITEMS, HAS_VALS>();
-    auto kern = k_onesweep<K, ITEMS, HAS_VALS>;
+    auto kern = k_onesweep<K, ITEMS, HAS_VALS, LBW>;
     static bool configured = false;  // per instantiation; same value on every device
     if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -353,7 +392,7 @@ static int lb_prepare(dnasa_ctx *ctx, size_t words, cudaStream_t s, unsigned lon
 template <typename K>
 int radix_sort_pairs(dnasa_ctx *ctx, const RadixScratch &rs, K *keys[2], uint32_t *vals[2],
                      int64_t n_host, const unsigned long long *d_n, int key_bits, bool hist_ready,
-                     int tile_items, int *which, cudaStream_t s) {
+                     int tile_items, int *which, cudaStream_t s, int lbw) {
     *which = 0;
     if (n_host <= 0) return DNASA_OK;
     if (key_bits > (int)(8 * sizeof(K))) return fail(ctx, DNASA_INVALID_ARG, "radix: key_bits");
@@ -392,7 +431,10 @@ int radix_sort_pairs(dnasa_ctx *ctx, const RadixScratch &rs, K *keys[2], uint32_
         LaunchScope ls_(ctx, PK_ONESWEEP, s,
                         (double)n_host * 2.0 * (sizeof(K) + (has_vals ? 4.0 : 0.0)));
 #define DNASA_PASS(IT, HV)                                                                    \
-    e = launch_pass<K, IT, HV>(tiles, s, kin, vin, kout, vout, rs.hist + p * kRadix, status, \
+    e = lbw == 1 ? launch_pass<K, IT, HV, 1>(tiles, s, kin, vin, kout, vout, rs.hist + p * kRadix,  \
+                                             status, ctx->ctrl->tile_ctr + p, n_host, d_n,          \
+                                             p * kRadixBits, epoch, &ctx->ctrl->err)                \
+                 : launch_pass<K, IT, HV, 8>(tiles, s, kin, vin, kout, vout, rs.hist + p * kRadix, status, \
                                ctx->ctrl->tile_ctr + p, n_host, d_n, p * kRadixBits, epoch,  \
                                &ctx->ctrl->err)
         if (has_vals) {
@@ -414,13 +456,51 @@ int radix_sort_pairs(dnasa_ctx *ctx, const RadixScratch &rs, K *keys[2], uint32_
 
 template int radix_sort_pairs<uint32_t>(dnasa_ctx *, const RadixScratch &, uint32_t *[2],
                                         uint32_t *[2], int64_t, const unsigned long long *, int,
-                                        bool, int, int *, cudaStream_t);
+                                        bool, int, int *, cudaStream_t, int);
 template int radix_sort_pairs<unsigned long long>(dnasa_ctx *, const RadixScratch &,
                                                   unsigned long long *[2], uint32_t *[2], int64_t,
                                                   const unsigned long long *, int, bool, int,
-                                                  int *, cudaStream_t);
+                                                  int *, cudaStream_t, int);
 
 // Histogram accumulation entry used by fused producers: nothing here; the
 // producer kernels call radix_digit_count() below.
 
 }  // namespace dnasa
+
+using namespace dnasa;
+
+extern "C" int dnasa_sort_pairs(dnasa_ctx *ctx, uint64_t *keys, uint32_t *vals, int64_t n,
+                                int key_bits, int tile_items, int lookback, void *stream) {
+    if (!ctx) return DNASA_INVALID_ARG;
+    ctx->last_error.clear();
+    if (n < 0 || n >= (int64_t(1) << 32) || key_bits < 1 || key_bits > 64)
+        return fail(ctx, DNASA_INVALID_ARG, "dnasa_sort_pairs: need 0 <= n < 2^32, 1 <= key_bits <= 64");
+    if (tile_items != 0 && tile_items != 2048 && tile_items != 3840 && tile_items != 5120)
+        return fail(ctx, DNASA_INVALID_ARG, "dnasa_sort_pairs: tile_items must be 0, 2048, 3840 or 5120");
+    if (lookback != 0 && lookback != 1 && lookback != 8)
+        return fail(ctx, DNASA_INVALID_ARG, "dnasa_sort_pairs: lookback must be 0, 1 or 8");
+    if (n == 0) return DNASA_OK;
+    if (!is_device_ptr(ctx, keys) || (vals && !is_device_ptr(ctx, vals)))
+        return fail(ctx, DNASA_INVALID_ARG, "dnasa_sort_pairs: keys and vals must be device pointers");
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int tile = tile_items ? tile_items : radix_tile_default();
+    size_t need = ((size_t)n * 8 + 255) / 256 * 256 + ((size_t)n * 4 + 255) / 256 * 256 +
+                  radix_scratch_bytes(n, key_bits, tile) + 4096;
+    DNASA_TRY(ws_reserve(ctx, need, s));
+    Arena a = ws_arena(ctx);
+    unsigned long long *kalt = a.take<unsigned long long>((size_t)n);
+    uint32_t *valt = a.take<uint32_t>((size_t)n);
+    RadixScratch rs = radix_scratch_take(a, n, key_bits, tile);
+    unsigned long long *kk[2] = {reinterpret_cast<unsigned long long *>(keys), kalt};
+    uint32_t *vv[2] = {vals, vals ? valt : nullptr};
+    int which = 0;
+    DNASA_TRY(radix_sort_pairs<unsigned long long>(ctx, rs, kk, vv, n, nullptr, key_bits, false,
+                                                   tile, &which, s, lookback ? lookback : 8));
+    if (which == 1) {
+        DNASA_CUDA(ctx, cudaMemcpyAsync(keys, kalt, (size_t)n * 8, cudaMemcpyDeviceToDevice, s));
+        if (vals)
+            DNASA_CUDA(ctx, cudaMemcpyAsync(vals, valt, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
+    }
+    return DNASA_OK;
+}

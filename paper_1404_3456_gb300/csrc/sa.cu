@@ -16,6 +16,7 @@
 // singletons and compacts the rest.  When few suffixes remain, a finisher
 // sorts each remaining group by comparing packed words directly.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 
 #include "block.cuh"
@@ -83,11 +84,15 @@ struct RerankOut {
 
 // Shared memory of one rerank tile (dynamic, > 48 KB).
 struct RerankSmem {
-    unsigned long long k[kRrTile + 2];   // keys with one halo key on each side
+    union {
+        unsigned long long k[kRrTile + 2];   // keys with one halo key on each side
+        struct {                             // reused once the head flags are known
+            uint32_t head[kRrTile];          // new rank (SA slot of the group head)
+            int32_t kp[kRrTile];             // output index of a kept item, -1 if dropped
+        } o;
+    } u;
     uint32_t v[kRrTile];                 // positions
     uint32_t sl[kRrTile];                // slots (rounds >= 1)
-    uint32_t head[kRrTile];              // new rank (SA slot of the group head)
-    int32_t kp[kRrTile];                 // output index of a kept item, -1 if dropped
     uint8_t f[kRrTile];                  // bit0 head, bit1 next is head
     int64_t tmp[kRrThreads / 32 + 1];
     int64_t incmax[kRrThreads];
@@ -118,7 +123,7 @@ __global__ void __launch_bounds__(kRrThreads) k_rerank(
     // ---- striped, coalesced loads
     for (int i = tid; i < tile_n + 2; i += kRrThreads) {
         int64_t j = base - 1 + i;
-        S.k[i] = (j >= 0 && j < n) ? keys[j] : 0ull;
+        S.u.k[i] = (j >= 0 && j < n) ? keys[j] : 0ull;
     }
     for (int i = tid; i < tile_n; i += kRrThreads) {
         S.v[i] = vals[base + i];
@@ -128,9 +133,9 @@ __global__ void __launch_bounds__(kRrThreads) k_rerank(
     // ---- head flags, striped (conflict-free shared reads)
     auto is_head = [&](int64_t j) -> bool {   // j in [base, base + tile_n]
         if (j == 0) return true;
-        unsigned long long k = S.k[j - base + 1];
+        unsigned long long k = S.u.k[j - base + 1];
         if (ROUND0 && (int)(k & 31ull) < h0) return true;   // own '$' inside: final
-        return k != S.k[j - base];
+        return k != S.u.k[j - base];
     };
     for (int li = tid; li < tile_n; li += kRrThreads) {
         int64_t j = base + li;
@@ -157,20 +162,26 @@ __global__ void __launch_bounds__(kRrThreads) k_rerank(
     S.incmax[tid] = inc_max;
     int64_t ex_keep = block_exclusive_sum<kRrThreads>(my_keep, S.tmp, &tile_keep);
 
-    if (tid == 0) {
-        int64_t pmax = -1, psum = 0;
+    // ---- decoupled look-back, one warp: 32 predecessors per probe
+    if (tid < 32) {
+        const int lane = tid;
         unsigned long long *my = status + tile;
+        int64_t pmax = -1, psum = 0;
         if (tile == 0) {
-            st_relaxed_u64(my, rr_pack(RR_INC, tile_max, tile_keep));
+            if (lane == 0) st_relaxed_u64(my, rr_pack(RR_INC, tile_max, tile_keep));
         } else {
-            st_relaxed_u64(my, rr_pack(RR_AGG, tile_max, tile_keep));
-            int64_t tt = (int64_t)tile - 1;
+            if (lane == 0) st_relaxed_u64(my, rr_pack(RR_AGG, tile_max, tile_keep));
+            int64_t wend = tile;   // window = tiles [wend - 32, wend - 1], lane l -> wend - 1 - l
             uint32_t spins = 0;
             bool gave_up = false;
-            while (tt >= 0) {
-                unsigned long long w = ld_relaxed_u64(status + tt);
+            for (;;) {
+                int64_t tt = wend - 1 - lane;
+                unsigned long long w = tt >= 0 ? ld_relaxed_u64(status + tt) : RR_INC;  // virtual INC
                 unsigned long long flag = w & (3ull << 62);
-                if (flag == 0) {
+                uint32_t notready = __ballot_sync(0xffffffffu, flag == 0);
+                uint32_t inc = __ballot_sync(0xffffffffu, flag == RR_INC);
+                uint32_t need = inc ? ((inc & (0u - inc)) << 1) - 1u : 0xffffffffu;  // lanes up to nearest INC
+                if (notready & need) {
                     if (++spins > kSpinLimit || ((spins & 1023) == 0 && ld_relaxed_u32(err) != 0)) {
                         gave_up = true;
                         break;
@@ -178,22 +189,32 @@ __global__ void __launch_bounds__(kRrThreads) k_rerank(
                     __nanosleep(32);
                     continue;
                 }
-                int64_t hv = (int64_t)((w >> 31) & 0x7FFFFFFFull) - 1;
-                int64_t kv = (int64_t)(w & 0x7FFFFFFFull);
+                bool take = (need >> lane) & 1u;
+                int64_t hv = take && tt >= 0 ? (int64_t)((w >> 31) & 0x7FFFFFFFull) - 1 : -1;
+                int64_t kv = take && tt >= 0 ? (int64_t)(w & 0x7FFFFFFFull) : 0;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    hv = max(hv, __shfl_xor_sync(0xffffffffu, hv, o));
+                    kv += __shfl_xor_sync(0xffffffffu, kv, o);
+                }
                 pmax = max(pmax, hv);
                 psum += kv;
-                if (flag == RR_INC) break;
-                --tt;
+                if (inc) break;
+                wend -= 32;
             }
-            if (gave_up) {
-                atomicOr(err, DERR_TIMEOUT);
-                S.abort = 1;
+            if (lane == 0) {
+                if (gave_up) {
+                    atomicOr(err, DERR_TIMEOUT);
+                    S.abort = 1;
+                }
+                st_relaxed_u64(my, rr_pack(RR_INC, max(pmax, tile_max), psum + tile_keep));
             }
-            st_relaxed_u64(my, rr_pack(RR_INC, max(pmax, tile_max), psum + tile_keep));
         }
-        S.prefix[0] = pmax;
-        S.prefix[1] = psum;
-        if (base + tile_n == n) *o.kept = (unsigned long long)(psum + tile_keep);
+        if (lane == 0) {
+            S.prefix[0] = pmax;
+            S.prefix[1] = psum;
+            if (base + tile_n == n) *o.kept = (unsigned long long)(psum + tile_keep);
+        }
     }
     __syncthreads();
     if (S.abort) return;   // prefix unknown: write nothing
@@ -208,9 +229,9 @@ __global__ void __launch_bounds__(kRrThreads) k_rerank(
             int64_t j = base + li;
             if (headbits >> i & 1u) cur = j;
             uint32_t slot = ROUND0 ? (uint32_t)j : S.sl[li];
-            S.head[li] = ROUND0 ? (uint32_t)cur : slot - (uint32_t)(j - cur);
+            S.u.o.head[li] = ROUND0 ? (uint32_t)cur : slot - (uint32_t)(j - cur);
             if (keepbits >> i & 1u) {
-                S.kp[li] = (int32_t)kp;
+                S.u.o.kp[li] = (int32_t)kp;
                 if (lastbits >> i & 1u) {
                     uint32_t size = (uint32_t)(j - cur + 1);
                     unsigned long long g = atomicAdd(o.ngroups, 1ull);
@@ -219,7 +240,7 @@ __global__ void __launch_bounds__(kRrThreads) k_rerank(
                 }
                 ++kp;
             } else {
-                S.kp[li] = -1;
+                S.u.o.kp[li] = -1;
             }
         }
     }
@@ -228,8 +249,8 @@ __global__ void __launch_bounds__(kRrThreads) k_rerank(
     for (int li = tid; li < tile_n; li += kRrThreads) {
         uint32_t slot = ROUND0 ? (uint32_t)(base + li) : S.sl[li];
         uint32_t pos = S.v[li];
-        uint32_t hs = S.head[li];
-        int32_t kp = S.kp[li];
+        uint32_t hs = S.u.o.head[li];
+        int32_t kp = S.u.o.kp[li];
         if ((int64_t)slot >= o.N || (int64_t)pos >= o.N || kp >= n) {
             atomicOr(err, DERR_BOUNDS);
             continue;
@@ -352,11 +373,19 @@ __global__ void k_widen(const uint32_t *__restrict__ a, int64_t n, int64_t *__re
 
 }  // namespace
 
-int h0_for(int n_inst, int *inst_bits) {
+// Symbols in the initial key.  Enough that i.i.d. text leaves few suffixes
+// unsorted (4^h0 >= 32 * symbols per instance: expected colliding pairs at most
+// N/64), then as many as fit in the same number of 8-bit passes: the key is
+// [instance | 2*h0 bits of bases | 5 bits of lc], and its passes are the cost.
+int h0_for(int64_t N, int n_inst, int *inst_bits) {
     int ib = n_inst > 1 ? bits_for((uint64_t)(n_inst - 1)) : 0;
     *inst_bits = ib;
-    int h0 = (64 - 5 - ib) / 2;
-    return h0 > 29 ? 29 : h0;
+    double per = (double)N / (double)(n_inst > 0 ? n_inst : 1);
+    int hmin = (int)std::ceil((std::log2(std::max(per, 2.0)) + 5.0) / 2.0);
+    hmin = std::max(8, std::min(hmin, 29));
+    int passes = (ib + 2 * hmin + 5 + 7) / 8;
+    int h0 = (8 * passes - 5 - ib) / 2;
+    return std::max(1, std::min(h0, 29));
 }
 
 int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_opts *opts_in,
@@ -367,9 +396,10 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
     const int64_t finish_threshold =
         opts.finish_threshold == 0 ? (int64_t)1 << 20 : opts.finish_threshold;
     const int max_rounds = opts.max_rounds > 0 ? std::min(opts.max_rounds, 63) : 63;
+    const int lbw = opts.lookback == 1 ? 1 : 8;
     const int64_t N = t.N;
     int ib;
-    const int h0 = h0_for(t.n_inst, &ib);
+    const int h0 = h0_for(N, t.n_inst, &ib);
     const int inst_shift = 2 * h0 + 5;
     const int key_bits0 = inst_shift + ib;
     const int b = bits_for((uint64_t)(N - 1));
@@ -449,7 +479,7 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
         DNASA_CUDA(ctx, cudaGetLastError());
         int which;
         DNASA_TRY(radix_sort_pairs<unsigned long long>(ctx, rs, keys, vals, N, nullptr, key_bits0,
-                                                       false, tile_items, &which, s));
+                                                       false, tile_items, &which, s, lbw));
         DNASA_TRY(reset_counters());
         ro.nslots = L[0][0]; ro.npos = L[0][1]; ro.nhead = L[0][2];
         {
@@ -490,7 +520,7 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
         DNASA_CUDA(ctx, cudaGetLastError());
         int which;
         DNASA_TRY(radix_sort_pairs<unsigned long long>(ctx, rs, keys, vals, kept, nullptr, 2 * b,
-                                                       false, tile_items, &which, s));
+                                                       false, tile_items, &which, s, lbw));
         DNASA_TRY(reset_counters());
         ro.nslots = L[cur ^ 1][0]; ro.npos = L[cur ^ 1][1]; ro.nhead = L[cur ^ 1][2];
         int tiles = ceil_div(kept, kRrTile);

@@ -229,3 +229,36 @@ def test_assemble_worked_example_dna(ctx):
     got = B().assemble_text(ctx, dev(t), 2)
     buf, off = oracle.assemble(t, 2)
     assert got == oracle.contigs_as_list(buf, off)
+
+
+# ---------------------------------------------------------------- radix sort (Algorithm 1)
+
+
+@pytest.mark.parametrize("n,bits,tile,lb,with_vals", [
+    (1, 64, 0, 0, True), (1000, 8, 2048, 1, True), (100_003, 63, 3840, 8, True),
+    (300_000, 52, 5120, 8, True), (70_000, 32, 0, 1, False), (3840 * 5 + 17, 17, 3840, 1, True)])
+def test_sort_pairs_equals_split_sort(ctx, n, bits, tile, lb, with_vals):
+    """The onesweep radix sort equals Algorithm 1's 1-bit stable splits."""
+    rng = np.random.default_rng(n + bits)
+    keys = rng.integers(0, 2**63, size=n, dtype=np.uint64) * np.uint64(2) + rng.integers(0, 2, n).astype(np.uint64)
+    if bits < 64:
+        keys &= np.uint64((1 << bits) - 1)
+    keys[: n // 4] = keys[0]          # a long run of equal keys: order must be kept
+    keys[n // 2: n // 2 + n // 8] = keys[-1]
+    vals = np.arange(n, dtype=np.uint32)
+    k_t = torch.from_numpy(keys.view(np.int64).copy()).cuda()
+    v_t = torch.from_numpy(vals.view(np.int32).copy()).cuda() if with_vals else None
+    B().dnasa_sort_pairs(ctx, k_t, v_t, key_bits=bits, tile_items=tile, lookback=lb)
+    want_k, want_v = oracle.split_sort(keys, vals.astype(np.uint64), 0, bits)
+    assert np.array_equal(k_t.cpu().numpy().view(np.uint64), want_k)
+    if with_vals:
+        assert np.array_equal(v_t.cpu().numpy().view(np.uint32).astype(np.uint64), want_v)
+
+
+def test_sa_lookback_variants_agree(ctx):
+    rng = np.random.default_rng(11)
+    t = random_text(rng, 400, 10, 1000)
+    want = oracle.suffix_array(t)
+    for lb in (1, 8):
+        sa = gpu_sa(ctx, t, opts=B().make_opts(lookback=lb))[0]
+        assert np.array_equal(sa.cpu().numpy().astype(np.int64), want)
