@@ -178,7 +178,9 @@ __global__ void k_max_len(TextDesc t, unsigned long long *out) {
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < t.n_reads;
          r += (int64_t)gridDim.x * blockDim.x)
         m = max(m, (unsigned long long)frag_len(t.toff, r));
-    atomicMax(out, m);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
 }
 
 inline int grid_for(dnasa_ctx *ctx, int64_t n, int threads = 256) {

@@ -15,27 +15,95 @@ namespace dnasa {
 
 namespace {
 
+constexpr int kShortBases = 64;   // resolved by one thread; longer LCPs go to a warp
+
+struct PairInfo {
+    uint64_t bp, bq;
+    int64_t m;      // bases left in the shorter of the two suffixes
+};
+
+__device__ __forceinline__ bool instance_start(const TextDesc &t, int64_t j) {
+    if (t.n_inst <= 1) return false;
+    int64_t i = upper_index(t.inst_toff, 0, t.n_inst, j);
+    return __ldg(t.inst_toff + i) == j;
+}
+
+__device__ __forceinline__ PairInfo pair_info(const TextDesc &t, const uint32_t *__restrict__ sa,
+                                              int64_t j) {
+    int64_t p = sa[j - 1], q = sa[j];
+    int64_t rp = read_of(t.toff, t.n_reads, p);
+    int64_t rq = read_of(t.toff, t.n_reads, q);
+    PairInfo r;
+    r.m = min(__ldg(t.toff + rp + 1) - 1 - p, __ldg(t.toff + rq + 1) - 1 - q);
+    r.bp = (uint64_t)(p - rp);
+    r.bq = (uint64_t)(q - rq);
+    return r;
+}
+
+// One thread per adjacent pair: the first 64 bases.  Pairs still equal there
+// (repeats) are queued for k_lcp_long.
 __global__ void __launch_bounds__(256) k_lcp(TextDesc t, const uint32_t *__restrict__ sa,
-                                             int32_t *__restrict__ lcp) {
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < t.N;
-         j += (int64_t)gridDim.x * blockDim.x) {
-        if (j == 0) { lcp[0] = 0; continue; }
-        if (t.n_inst > 1) {
-            int64_t i = upper_index(t.inst_toff, 0, t.n_inst, j);
-            if (__ldg(t.inst_toff + i) == j) { lcp[j] = 0; continue; }
+                                             int32_t *__restrict__ lcp, uint32_t *__restrict__ longq,
+                                             unsigned long long *__restrict__ nlong) {
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane; b < t.N; b += stride) {
+        int64_t j = b + lane;
+        bool queue = false;
+        if (j < t.N) {
+            if (j == 0 || instance_start(t, j)) {
+                lcp[j] = 0;
+            } else {
+                PairInfo pi = pair_info(t, sa, j);
+                int64_t h = 0;
+                bool done = false;
+#pragma unroll
+                for (int w = 0; w < kShortBases / 32; ++w) {
+                    if (h >= pi.m) { done = true; break; }
+                    uint64_t d = bases32(t.packed, pi.bp + h) ^ bases32(t.packed, pi.bq + h);
+                    if (d) { h += __clzll((long long)d) >> 1; done = true; break; }
+                    h += 32;
+                }
+                if (done || h >= pi.m) lcp[j] = (int32_t)min(h, pi.m);
+                else queue = true;
+            }
         }
-        int64_t p = sa[j - 1], q = sa[j];
-        int64_t rp = read_of(t.toff, t.n_reads, p);
-        int64_t rq = read_of(t.toff, t.n_reads, q);
-        int64_t m = min(__ldg(t.toff + rp + 1) - 1 - p, __ldg(t.toff + rq + 1) - 1 - q);
-        uint64_t bp = (uint64_t)(p - rp), bq = (uint64_t)(q - rq);
-        int64_t h = 0;
-        while (h < m) {
-            uint64_t d = bases32(t.packed, bp + h) ^ bases32(t.packed, bq + h);
-            if (d) { h += __clzll((long long)d) >> 1; break; }
-            h += 32;
+        uint32_t qm = __ballot_sync(0xffffffffu, queue);
+        if (qm) {
+            unsigned long long qb = 0;
+            if (lane == 0) qb = atomicAdd(nlong, (unsigned long long)__popc(qm));
+            qb = __shfl_sync(0xffffffffu, qb, 0);
+            if (queue) longq[qb + __popc(qm & lanemask_lt())] = (uint32_t)j;
         }
-        lcp[j] = (int32_t)min(h, m);
+    }
+}
+
+// One thread per queued pair (the LCP is over 64 bases: repeats): four words
+// (128 bases) per round trip, their eight loads issued together.
+__global__ void __launch_bounds__(256) k_lcp_long(TextDesc t, const uint32_t *__restrict__ sa,
+                                                  int32_t *__restrict__ lcp,
+                                                  const uint32_t *__restrict__ longq,
+                                                  const unsigned long long *__restrict__ nlong) {
+    const int64_t nq = (int64_t)*nlong;
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nq;
+         w += (int64_t)gridDim.x * blockDim.x) {
+        int64_t j = longq[w];
+        PairInfo pi = pair_info(t, sa, j);
+        int64_t res = pi.m;
+        for (int64_t h = kShortBases; h < pi.m; h += 4 * 32) {
+            uint64_t d[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                int64_t o = h + 32 * u;   // past the shorter suffix's end: a "mismatch" at o
+                d[u] = o < pi.m ? bases32(t.packed, pi.bp + o) ^ bases32(t.packed, pi.bq + o) : ~0ull;
+            }
+            int64_t at = -1;
+#pragma unroll
+            for (int u = 3; u >= 0; --u)
+                if (d[u]) at = h + 32 * u + (__clzll((long long)d[u]) >> 1);
+            if (at >= 0) { res = min(at, pi.m); break; }
+        }
+        lcp[j] = (int32_t)res;
     }
 }
 
@@ -43,10 +111,19 @@ __global__ void __launch_bounds__(256) k_lcp(TextDesc t, const uint32_t *__restr
 
 int lcp_build_impl(dnasa_ctx *ctx, const TextDesc &t, const uint32_t *sa32, int32_t *lcp,
                    cudaStream_t s) {
+    DNASA_TRY(ws_reserve(ctx, ((size_t)t.N * 4 + 255) / 256 * 256 + 4096, s));
+    Arena a = ws_arena(ctx);
+    uint32_t *longq = a.take<uint32_t>((size_t)t.N);
+    unsigned long long *nlong = ctx->ctrl->count + CNT_TMP;
+    DNASA_CUDA(ctx, cudaMemsetAsync(nlong, 0, 8, s));
     int grid = (int)std::min<int64_t>(ceil_div(t.N, 256), (int64_t)ctx->num_sms * 16);
     {
         LaunchScope ls_(ctx, PK_LCP, s, 8.5 * t.N);
-        k_lcp<<<std::max(grid, 1), 256, 0, s>>>(t, sa32, lcp);
+        k_lcp<<<std::max(grid, 1), 256, 0, s>>>(t, sa32, lcp, longq, nlong);
+    }
+    {
+        LaunchScope ls_(ctx, PK_LCP, s, 0.0);
+        k_lcp_long<<<ctx->num_sms * 16, 256, 0, s>>>(t, sa32, lcp, longq, nlong);
     }
     DNASA_CUDA(ctx, cudaGetLastError());
     return DNASA_OK;

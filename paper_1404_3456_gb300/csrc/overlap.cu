@@ -49,12 +49,16 @@ __global__ void k_isa(const uint32_t *__restrict__ sa, int64_t N, uint32_t *__re
 
 __global__ void k_read_keys(TextDesc t, const uint32_t *__restrict__ isa, uint32_t *__restrict__ key,
                             uint32_t *__restrict__ val, unsigned long long *maxlen) {
+    unsigned long long m = 0;
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < t.n_reads;
          r += (int64_t)gridDim.x * blockDim.x) {
         key[r] = isa[__ldg(t.toff + r)];
         val[r] = (uint32_t)r;
-        atomicMax(maxlen, (unsigned long long)frag_len(t.toff, r));
+        m = max(m, (unsigned long long)frag_len(t.toff, r));
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(maxlen, m);
 }
 
 __device__ __forceinline__ int64_t inst_of_read(const TextDesc &t, int64_t r) {
@@ -83,44 +87,65 @@ struct QueryArgs {
     unsigned long long *count;
 };
 
+// Walks the fragment starts that have X = r_j[q - toff[j] ..] as a prefix and
+// calls emit(k) for each overlap (j, k, |X|).  Returns false when q is no query.
+template <typename F>
+__device__ __forceinline__ void query_walk(const TextDesc &t, const QueryArgs &a, int64_t q, F emit) {
+    int64_t j = read_of(t.toff, t.n_reads, q);
+    int64_t start = __ldg(t.toff + j);
+    int64_t o = q - start;
+    int64_t L = __ldg(t.toff + j + 1) - 1 - q;   // bases of X = r_j[o..]
+    if (o < 1 || L < a.lmin) return;
+    uint32_t s = a.isa[q];
+    int64_t ri0 = 0, ri1 = t.n_reads;
+    if (t.n_inst > 1) {
+        int64_t inst = inst_of_read(t, j);
+        ri0 = __ldg(t.inst_roff + inst);
+        ri1 = __ldg(t.inst_roff + inst + 1);
+    }
+    int64_t lo = ri0, hi = ri1;                  // first fragment start after X's slot
+    while (lo < hi) {
+        int64_t m = (lo + hi) >> 1;
+        if (__ldg(a.Rslot + m) < s) lo = m + 1; else hi = m;
+    }
+    if (lo >= ri1) return;
+    int64_t k = __ldg(a.R + lo);
+    if (frag_len(t.toff, k) < L) return;
+    if (common_bases(t.packed, (uint64_t)(q - j), (uint64_t)(__ldg(t.toff + k) - k), L) < L) return;
+    for (int64_t kk = lo; kk < ri1; ++kk) {
+        if (kk > lo && __ldg(a.lcpr + kk) < L) break;
+        k = __ldg(a.R + kk);
+        if (k != j && L < frag_len(t.toff, k)) emit(j, k, L);
+    }
+}
+
+// One thread per text position.  Each warp counts its overlaps, claims room
+// with one atomic, then walks again to write them.
 __global__ void __launch_bounds__(256) k_query(TextDesc t, QueryArgs a) {
     const unsigned long long lmask = (1ull << a.lb) - 1ull;
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < t.N;
-         q += (int64_t)gridDim.x * blockDim.x) {
-        int64_t j = read_of(t.toff, t.n_reads, q);
-        int64_t start = __ldg(t.toff + j);
-        int64_t o = q - start;
-        int64_t L = __ldg(t.toff + j + 1) - 1 - q;   // bases of X = r_j[o..]
-        if (o < 1 || L < a.lmin) continue;
-        uint32_t s = a.isa[q];
-        int64_t ri0 = 0, ri1 = t.n_reads;
-        if (t.n_inst > 1) {
-            int64_t inst = inst_of_read(t, j);
-            ri0 = __ldg(t.inst_roff + inst);
-            ri1 = __ldg(t.inst_roff + inst + 1);
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane; b < t.N; b += stride) {
+        int64_t q = b + lane;
+        uint32_t c = 0;
+        if (q < t.N) query_walk(t, a, q, [&](int64_t, int64_t, int64_t) { ++c; });
+        uint32_t inc = c;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, inc, off);
+            if (lane >= off) inc += y;
         }
-        int64_t lo = ri0, hi = ri1;                  // first R slot > s
-        while (lo < hi) {
-            int64_t m = (lo + hi) >> 1;
-            if (__ldg(a.Rslot + m) < s) lo = m + 1; else hi = m;
-        }
-        if (lo >= ri1) continue;
-        int64_t k = __ldg(a.R + lo);
-        int64_t lk = frag_len(t.toff, k);
-        if (lk < L) continue;
-        int64_t m = common_bases(t.packed, (uint64_t)(q - j), (uint64_t)(__ldg(t.toff + k) - k), L);
-        if (m < L) continue;
-        for (int64_t kk = lo; kk < ri1; ++kk) {
-            if (kk > lo && __ldg(a.lcpr + kk) < L) break;
-            k = __ldg(a.R + kk);
-            lk = frag_len(t.toff, k);
-            if (k != j && L < lk) {
+        unsigned long long base = 0;
+        if (lane == 31 && inc) base = atomicAdd(a.count, (unsigned long long)inc);
+        base = __shfl_sync(0xffffffffu, base, 31) + (inc - c);
+        if (c) {
+            query_walk(t, a, q, [&](int64_t j, int64_t k, int64_t L) {
                 unsigned long long key = ((unsigned long long)j << (a.kb + a.lb)) |
                                          ((unsigned long long)k << a.lb) |
                                          (lmask - (unsigned long long)L);
-                unsigned long long idx = atomicAdd(a.count, 1ull);
-                if (idx < a.cap) a.cand[idx] = key;
-            }
+                if (base < a.cap) a.cand[base] = key;
+                ++base;
+            });
         }
     }
 }

@@ -74,12 +74,21 @@ __device__ __forceinline__ unsigned long long rr_pack(unsigned long long flag, i
     return flag | ((unsigned long long)(head + 1) << 31) | (unsigned long long)keep;
 }
 
+// rank[] writes are staged by position bucket (2^bshift positions each) and
+// applied bucket by bucket afterwards (k_rank_apply): a random 4-byte write into
+// an array larger than L2 costs a random read-modify-write of a whole DRAM
+// sector, while writes applied one 8 MB bucket at a time merge in L2.
+constexpr int kMaxBuckets = 1024;
+
 struct RerankOut {
     int64_t N;          // text length: bound of every SA slot and text position
     uint32_t *sa, *rank;
     uint32_t *nslots, *npos, *nhead;
     uint2 *groups;
     unsigned long long *kept, *ngroups, *maxgroup;
+    uint2 *stage;       // [N]: bucket b's (pos, rank) pairs start at b << bshift
+    uint32_t *bucket_fill;   // [kMaxBuckets]
+    int bshift;
 };
 
 // Shared memory of one rerank tile (dynamic, > 48 KB).
@@ -97,8 +106,12 @@ struct RerankSmem {
     int64_t tmp[kRrThreads / 32 + 1];
     int64_t incmax[kRrThreads];
     int64_t prefix[2];
+    int64_t win_h[kRrThreads / 32], win_k[kRrThreads / 32];
+    uint32_t win_nr[kRrThreads / 32], win_inc[kRrThreads / 32];
+    uint32_t bcnt[kMaxBuckets];          // per-bucket counts of this tile, then global bases
     uint32_t tile;
     int abort;
+    int stop;
 };
 
 template <bool ROUND0>
@@ -162,55 +175,78 @@ __global__ void __launch_bounds__(kRrThreads) k_rerank(
     S.incmax[tid] = inc_max;
     int64_t ex_keep = block_exclusive_sum<kRrThreads>(my_keep, S.tmp, &tile_keep);
 
-    // ---- decoupled look-back, one warp: 32 predecessors per probe
-    if (tid < 32) {
-        const int lane = tid;
-        unsigned long long *my = status + tile;
+    // ---- decoupled look-back with the whole CTA: thread i probes tile - 1 - i,
+    // so one round trip covers 256 predecessors.  (The inclusive prefix can
+    // advance at most one window per round trip; a 32-wide window capped the
+    // kernel at 32 tiles per status round trip.)
+    {
+        const int lane = tid & 31, warp = tid >> 5;
+        if (tid == 0)
+            st_relaxed_u64(status + tile, rr_pack(tile == 0 ? RR_INC : RR_AGG, tile_max, tile_keep));
         int64_t pmax = -1, psum = 0;
-        if (tile == 0) {
-            if (lane == 0) st_relaxed_u64(my, rr_pack(RR_INC, tile_max, tile_keep));
-        } else {
-            if (lane == 0) st_relaxed_u64(my, rr_pack(RR_AGG, tile_max, tile_keep));
-            int64_t wend = tile;   // window = tiles [wend - 32, wend - 1], lane l -> wend - 1 - l
-            uint32_t spins = 0;
-            bool gave_up = false;
-            for (;;) {
-                int64_t tt = wend - 1 - lane;
-                unsigned long long w = tt >= 0 ? ld_relaxed_u64(status + tt) : RR_INC;  // virtual INC
-                unsigned long long flag = w & (3ull << 62);
-                uint32_t notready = __ballot_sync(0xffffffffu, flag == 0);
-                uint32_t inc = __ballot_sync(0xffffffffu, flag == RR_INC);
-                uint32_t need = inc ? ((inc & (0u - inc)) << 1) - 1u : 0xffffffffu;  // lanes up to nearest INC
-                if (notready & need) {
-                    if (++spins > kSpinLimit || ((spins & 1023) == 0 && ld_relaxed_u32(err) != 0)) {
-                        gave_up = true;
-                        break;
-                    }
-                    __nanosleep(32);
-                    continue;
-                }
-                bool take = (need >> lane) & 1u;
-                int64_t hv = take && tt >= 0 ? (int64_t)((w >> 31) & 0x7FFFFFFFull) - 1 : -1;
-                int64_t kv = take && tt >= 0 ? (int64_t)(w & 0x7FFFFFFFull) : 0;
+        int64_t wend = tile;          // window = tiles [wend - 256, wend - 1]
+        uint32_t spins = 0;
+        bool gave_up = false;
+        while (tile != 0) {
+            int64_t tt = wend - 1 - tid;
+            unsigned long long w = tt >= 0 ? ld_relaxed_u64(status + tt) : RR_INC;  // virtual INC
+            unsigned long long flag = w & (3ull << 62);
+            uint32_t nr = __ballot_sync(0xffffffffu, flag == 0);
+            uint32_t inc = __ballot_sync(0xffffffffu, flag == RR_INC);
+            if (lane == 0) {
+                S.win_nr[warp] = nr;
+                S.win_inc[warp] = inc;
+            }
+            if (tid == 0) S.stop = (spins & 1023) == 1023 && ld_relaxed_u32(err) != 0;
+            __syncthreads();
+            const bool stop = S.stop;   // read before the next barrier: tid 0 rewrites it later
+            // nearest INC over the window (lowest thread index), and readiness before it
+            int near = kRrThreads;
+            bool blocked = false;
+            for (int v = 0; v < kRrThreads / 32; ++v) {
+                uint32_t iv = S.win_inc[v], nv = S.win_nr[v];
+                uint32_t need = iv ? ((iv & (0u - iv)) << 1) - 1u : 0xffffffffu;
+                if (nv & need) { blocked = true; break; }
+                if (iv) { near = v * 32 + __ffs(iv) - 1; break; }
+            }
+            if (!blocked) {
+                bool take = tid <= near && tt >= 0;
+                int64_t hv = take ? (int64_t)((w >> 31) & 0x7FFFFFFFull) - 1 : -1;
+                int64_t kv = take ? (int64_t)(w & 0x7FFFFFFFull) : 0;
 #pragma unroll
                 for (int o = 16; o > 0; o >>= 1) {
                     hv = max(hv, __shfl_xor_sync(0xffffffffu, hv, o));
                     kv += __shfl_xor_sync(0xffffffffu, kv, o);
                 }
-                pmax = max(pmax, hv);
-                psum += kv;
-                if (inc) break;
-                wend -= 32;
-            }
-            if (lane == 0) {
-                if (gave_up) {
-                    atomicOr(err, DERR_TIMEOUT);
-                    S.abort = 1;
+                if (lane == 0) {
+                    S.win_h[warp] = hv;
+                    S.win_k[warp] = kv;
                 }
-                st_relaxed_u64(my, rr_pack(RR_INC, max(pmax, tile_max), psum + tile_keep));
             }
+            __syncthreads();
+            if (blocked) {   // uniform: every thread read the same shared words
+                if (++spins > kSpinLimit || stop) {
+                    gave_up = true;
+                    break;
+                }
+                __nanosleep(64);
+                continue;
+            }
+            for (int v = 0; v < kRrThreads / 32; ++v) {
+                pmax = max(pmax, S.win_h[v]);
+                psum += S.win_k[v];
+            }
+            __syncthreads();   // window arrays are rewritten by the next probe
+            if (near < kRrThreads) break;
+            wend -= kRrThreads;
         }
-        if (lane == 0) {
+        if (tid == 0) {
+            if (gave_up) {
+                atomicOr(err, DERR_TIMEOUT);
+                S.abort = 1;
+            }
+            if (tile != 0)
+                st_relaxed_u64(status + tile, rr_pack(RR_INC, max(pmax, tile_max), psum + tile_keep));
             S.prefix[0] = pmax;
             S.prefix[1] = psum;
             if (base + tile_n == n) *o.kept = (unsigned long long)(psum + tile_keep);
@@ -218,10 +254,25 @@ __global__ void __launch_bounds__(kRrThreads) k_rerank(
     }
     __syncthreads();
     if (S.abort) return;   // prefix unknown: write nothing
-    // ---- blocked: new rank and output index of every item
+    // ---- blocked: new rank and output index of every item.  A kept item that
+    // ends its group records (first kept index, size) in the group list; the
+    // list slots and the largest size are claimed with one atomic per warp.
     {
         int64_t cur = max(S.prefix[0], tid > 0 ? S.incmax[tid - 1] : (int64_t)-1);
         int64_t kp = S.prefix[1] + ex_keep;
+        const int lane = tid & 31;
+        uint32_t gend = keepbits & lastbits;
+        uint32_t ng = __popc(gend);
+        uint32_t ng_inc = ng;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, ng_inc, off);
+            if (lane >= off) ng_inc += y;
+        }
+        unsigned long long gbase = 0;
+        if (lane == 31 && ng_inc) gbase = atomicAdd(o.ngroups, (unsigned long long)ng_inc);
+        gbase = __shfl_sync(0xffffffffu, gbase, 31) + (ng_inc - ng);
+        uint32_t my_maxsize = 0;
 #pragma unroll
         for (int i = 0; i < kRrItems; ++i) {
             int li = tid * kRrItems + i;
@@ -234,34 +285,78 @@ __global__ void __launch_bounds__(kRrThreads) k_rerank(
                 S.u.o.kp[li] = (int32_t)kp;
                 if (lastbits >> i & 1u) {
                     uint32_t size = (uint32_t)(j - cur + 1);
-                    unsigned long long g = atomicAdd(o.ngroups, 1ull);
-                    o.groups[g] = make_uint2((uint32_t)(kp - size + 1), size);
-                    atomicMax(o.maxgroup, (unsigned long long)size);
+                    o.groups[gbase++] = make_uint2((uint32_t)(kp - size + 1), size);
+                    my_maxsize = max(my_maxsize, size);
                 }
                 ++kp;
             } else {
                 S.u.o.kp[li] = -1;
             }
         }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1)
+            my_maxsize = max(my_maxsize, __shfl_xor_sync(0xffffffffu, my_maxsize, off));
+        if (lane == 0 && my_maxsize) atomicMax(o.maxgroup, (unsigned long long)my_maxsize);
     }
     __syncthreads();
-    // ---- striped, coalesced writes (rank[pos] is a scatter by nature)
-    for (int li = tid; li < tile_n; li += kRrThreads) {
+    // ---- striped, coalesced writes; rank[pos] goes to its position bucket
+    const int nb = (int)((o.N + (1ll << o.bshift) - 1) >> o.bshift);
+    for (int b = tid; b < nb; b += kRrThreads) S.bcnt[b] = 0;
+    __syncthreads();
+    uint32_t bidx[kRrItems];
+#pragma unroll
+    for (int i = 0; i < kRrItems; ++i) {
+        int li = tid + i * kRrThreads;
+        bidx[i] = 0;
+        if (li < tile_n) bidx[i] = atomicAdd(&S.bcnt[S.v[li] >> o.bshift], 1u);
+    }
+    __syncthreads();
+    for (int b = tid; b < nb; b += kRrThreads) {
+        uint32_t c = S.bcnt[b];
+        if (c) S.bcnt[b] = atomicAdd(&o.bucket_fill[b], c);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < kRrItems; ++i) {
+        int li = tid + i * kRrThreads;
+        if (li >= tile_n) break;
         uint32_t slot = ROUND0 ? (uint32_t)(base + li) : S.sl[li];
         uint32_t pos = S.v[li];
         uint32_t hs = S.u.o.head[li];
         int32_t kp = S.u.o.kp[li];
-        if ((int64_t)slot >= o.N || (int64_t)pos >= o.N || kp >= n) {
+        uint32_t b = pos >> o.bshift;
+        uint64_t st = ((uint64_t)b << o.bshift) + S.bcnt[b] + bidx[i];
+        if ((int64_t)slot >= o.N || (int64_t)pos >= o.N || kp >= n || (int64_t)st >= o.N) {
             atomicOr(err, DERR_BOUNDS);
             continue;
         }
         o.sa[slot] = pos;
-        o.rank[pos] = hs;
+        o.stage[st] = make_uint2(pos, hs);
         if (kp >= 0) {
             o.nslots[kp] = slot;
             o.npos[kp] = pos;
             o.nhead[kp] = hs;
         }
+    }
+}
+
+// Applies the staged rank writes, bucket-major: CTA c handles bucket
+// c / per_bucket, chunk c % per_bucket (CTAs are issued roughly in index order,
+// so one bucket's 8 MB of rank[] is written at a time).
+constexpr int kApplyItems = 4096;
+__global__ void __launch_bounds__(256) k_rank_apply(const uint2 *__restrict__ stage,
+                                                    const uint32_t *__restrict__ bucket_fill,
+                                                    int bshift, int per_bucket, int64_t N,
+                                                    uint32_t *__restrict__ rank, uint32_t *err) {
+    const int b = blockIdx.x / per_bucket;
+    const int chunk = blockIdx.x % per_bucket;
+    const uint32_t fill = bucket_fill[b];
+    const uint64_t b0 = (uint64_t)b << bshift;
+    for (uint32_t i = chunk * kApplyItems + threadIdx.x;
+         i < fill && i < (uint32_t)(chunk + 1) * kApplyItems; i += 256) {
+        uint2 pr = stage[b0 + i];
+        if ((int64_t)pr.x < N && (pr.x >> bshift) == (uint32_t)b) rank[pr.x] = pr.y;
+        else atomicOr(err, DERR_BOUNDS);
     }
 }
 
@@ -415,6 +510,7 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
     for (int i = 0; i < 6; ++i) add(n * 4); // lists A, B
     add((n / 2 + 1) * 8);                   // groups
     add((size_t)rr_tiles * 8);              // rerank status
+    add((size_t)kMaxBuckets * 4);           // rank-write bucket fill counts
     add(radix_scratch_bytes(N, 64, tile_items));
     DNASA_TRY(ws_reserve(ctx, need + 4096, s));
     Arena a = ws_arena(ctx);
@@ -426,6 +522,7 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
         for (int j = 0; j < 3; ++j) L[i][j] = a.take<uint32_t>(n);
     uint2 *groups = a.take<uint2>(n / 2 + 1);
     unsigned long long *rr_status = a.take<unsigned long long>((size_t)rr_tiles);
+    uint32_t *bucket_fill = a.take<uint32_t>((size_t)kMaxBuckets);
     RadixScratch rs = radix_scratch_take(a, N, 64, tile_items);
     if (!rs.hist || !rr_status) return fail(ctx, DNASA_OOM, "sa_build workspace");
 
@@ -447,6 +544,20 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
         DNASA_CUDA(ctx, cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * 4, s));
         DNASA_CUDA(ctx, cudaMemsetAsync(c->tile_ctr + 32, 0, sizeof(uint32_t) * 4, s));
         DNASA_CUDA(ctx, cudaMemsetAsync(rr_status, 0, (size_t)rr_tiles * 8, s));
+        DNASA_CUDA(ctx, cudaMemsetAsync(bucket_fill, 0, (size_t)kMaxBuckets * 4, s));
+        return DNASA_OK;
+    };
+    // position buckets of 2^bshift (>= 2M) positions, at most kMaxBuckets of them
+    int bshift = 21;
+    while (((N - 1) >> bshift) + 1 > kMaxBuckets) ++bshift;
+    const int nbuckets = (int)(((N - 1) >> bshift) + 1);
+    auto apply_ranks = [&](int64_t n_items, int stage_buf) -> int {
+        int64_t per = std::min<int64_t>((int64_t)1 << bshift, n_items);
+        int per_bucket = std::max(1, ceil_div(per, kApplyItems));
+        LaunchScope ls_(ctx, PK_RERANK, s, 12.0 * n_items);
+        k_rank_apply<<<nbuckets * per_bucket, 256, 0, s>>>(
+            reinterpret_cast<const uint2 *>(keys[stage_buf]), bucket_fill, bshift, per_bucket, N,
+            rank, &c->err);
         return DNASA_OK;
     };
     auto read_counters = [&](int64_t *kept, int64_t *ngroups, int64_t *maxgroup) -> int {
@@ -467,6 +578,8 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
     ro.kept = cnt + CNT_ACTIVE;
     ro.ngroups = cnt + CNT_GROUPS;
     ro.maxgroup = cnt + CNT_MAXGROUP;
+    ro.bucket_fill = bucket_fill;
+    ro.bshift = bshift;
 
     // ---- round 0: initial keys, sort, rerank
     {
@@ -482,11 +595,14 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
                                                        false, tile_items, &which, s, lbw));
         DNASA_TRY(reset_counters());
         ro.nslots = L[0][0]; ro.npos = L[0][1]; ro.nhead = L[0][2];
+        ro.stage = reinterpret_cast<uint2 *>(keys[which ^ 1]);   // the free key buffer
         {
             LaunchScope ls_(ctx, PK_RERANK, s, 20.0 * N);
             k_rerank<true><<<rr_tiles, kRrThreads, sizeof(RerankSmem), s>>>(keys[which], vals[which], nullptr, N, nullptr,
                                                            h0, ro, rr_status, c->tile_ctr + 32, &c->err);
         }
+        DNASA_CUDA(ctx, cudaGetLastError());
+        DNASA_TRY(apply_ranks(N, which ^ 1));
         DNASA_CUDA(ctx, cudaGetLastError());
     }
     int64_t kept, ngroups, maxgroup;
@@ -523,6 +639,7 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
                                                        false, tile_items, &which, s, lbw));
         DNASA_TRY(reset_counters());
         ro.nslots = L[cur ^ 1][0]; ro.npos = L[cur ^ 1][1]; ro.nhead = L[cur ^ 1][2];
+        ro.stage = reinterpret_cast<uint2 *>(keys[which ^ 1]);
         int tiles = ceil_div(kept, kRrTile);
         {
             LaunchScope ls_(ctx, PK_RERANK, s, 24.0 * kept);
@@ -530,6 +647,8 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
                                                          nullptr, h0, ro, rr_status, c->tile_ctr + 32,
                                                          &c->err);
         }
+        DNASA_CUDA(ctx, cudaGetLastError());
+        DNASA_TRY(apply_ranks(kept, which ^ 1));
         DNASA_CUDA(ctx, cudaGetLastError());
         DNASA_TRY(read_counters(&kept, &ngroups, &maxgroup));
         cur ^= 1;

@@ -112,8 +112,11 @@ def test_sa_repeat_genome(ctx):
     assert np.array_equal(sa.cpu().numpy().astype(np.int64), want)
     tr = ctx.trace()
     assert tr["rounds"] >= 2 and tr["finished_direct"] == 0
-    sa = gpu_sa(ctx, t)[0]                                             # default switch
+    sa, packed, toff, nr, _ = gpu_sa(ctx, t)                           # default switch
     assert np.array_equal(sa.cpu().numpy().astype(np.int64), want)
+    lcp = torch.empty_like(sa)
+    B().lcp_build(ctx, packed, toff, nr, t.size, sa, lcp)              # long LCPs: warp path
+    assert np.array_equal(lcp.cpu().numpy(), oracle.lcp_kasai(t, want))
 
 
 @pytest.mark.parametrize("finish", [-1, 1 << 40])
