@@ -153,6 +153,28 @@ uint64_t dnasa_launch_count(dnasa_ctx *ctx);
 int dnasa_sort_pairs(dnasa_ctx *ctx, uint64_t *keys, uint32_t *vals, int64_t n, int key_bits,
                      int tile_items, int lookback, void *stream);
 
+/* ---- allocation-free radix sort ------------------------------------------------ */
+
+/* Largest n dnasa_sort_pairs_noalloc accepts. */
+#define DNASA_NOALLOC_MAX_ITEMS (1 << 20)
+
+/* The paper has no counterpart to this entry point; it exists for callers that
+ * cannot allocate device memory -- code running under a host framework whose
+ * caching allocator already holds the GPU's memory, or latency-bound loops in
+ * which a cudaMalloc/cudaFree (and the device synchronization it implies) is not
+ * acceptable.  It sorts like dnasa_sort_pairs (same kernels, same stable order)
+ * but needs no context and allocates nothing: its scratch is one fixed device
+ * array of about 12.6 MB inside the library, which every device that loads the
+ * library keeps until the process exits.
+ *   keys, vals, key_bits   as for dnasa_sort_pairs (vals may be NULL)
+ *   n                      0 <= n <= DNASA_NOALLOC_MAX_ITEMS, else DNASA_CAPACITY
+ * The first call on a device looks up the scratch array's device address (with
+ * that device current); make that first call before any stream capture.  All
+ * calls share the one scratch array, so calls whose work overlaps on the GPU
+ * (for example on two streams at once) race; serialize them.  Synchronizes the
+ * stream before returning; DNASA_DEVICE_TIMEOUT if a bounded device wait gave up. */
+int dnasa_sort_pairs_noalloc(uint64_t *keys, uint32_t *vals, int64_t n, int key_bits, void *stream);
+
 /* ---- S1: pack (Sec. III alphabet; the SA of Sec. IV is over this text) ------- */
 
 /* Validates text[0..N) and writes its packed form and fragment offsets.

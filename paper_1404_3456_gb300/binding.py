@@ -66,6 +66,7 @@ _SIGS = {
     "dnasa_profile_read": (_INT, [_P, ctypes.POINTER(ProfEntry), _INT, ctypes.POINTER(_INT)]),
     "dnasa_launch_count": (ctypes.c_uint64, [_P]),
     "dnasa_sort_pairs": (_INT, [_P, _P, _P, _I64, _INT, _INT, _INT, _P]),
+    "dnasa_sort_pairs_noalloc": (_INT, [_P, _P, _I64, _INT, _P]),
     "dnasa_pack": (_INT, [_P, _P, _I64, _P, _P, _I64, ctypes.POINTER(_I64), _P]),
     "sa_build": (_INT, [_P, _P, _P, _I64, _I64, _P, _INT, ctypes.POINTER(Opts), _P]),
     "lcp_build": (_INT, [_P, _P, _P, _I64, _I64, _P, _INT, _P, _P]),
@@ -181,6 +182,18 @@ def dnasa_sort_pairs(ctx: Context, keys, vals=None, key_bits: int = 64, tile_ite
     """Stable radix sort in place: keys int64 (bit pattern of uint64), vals int32/uint32."""
     ctx.check(lib().dnasa_sort_pairs(ctx.handle, _ptr(keys), _ptr(vals) if vals is not None else None,
                                      keys.numel(), key_bits, tile_items, lookback, _stream(stream)))
+
+
+NOALLOC_MAX_ITEMS = 1 << 20   # DNASA_NOALLOC_MAX_ITEMS in dnasa.h
+
+
+def dnasa_sort_pairs_noalloc(keys, vals=None, key_bits: int = 64, stream=None):
+    """dnasa_sort_pairs without a context or any allocation (n <= NOALLOC_MAX_ITEMS);
+    raises DnasaError with the C status on failure."""
+    rc = lib().dnasa_sort_pairs_noalloc(_ptr(keys), _ptr(vals) if vals is not None else None,
+                                        keys.numel(), key_bits, _stream(stream))
+    if rc != 0:
+        raise DnasaError(rc, "dnasa_sort_pairs_noalloc failed")
 
 
 def dnasa_pack(ctx: Context, text, packed, toff, stream=None) -> int:

@@ -504,3 +504,114 @@ extern "C" int dnasa_sort_pairs(dnasa_ctx *ctx, uint64_t *keys, uint32_t *vals, 
     }
     return DNASA_OK;
 }
+
+// ------------------------------------------------------------------ allocation-free sort
+// Some callers cannot call cudaMalloc: code running under a host framework whose
+// caching allocator has already reserved the device memory (a fresh cudaMalloc
+// can fail or fragment that reservation), and latency-bound loops where an
+// allocation's implicit device synchronization is not acceptable.  For them,
+// dnasa_sort_pairs_noalloc runs the same radix-sort kernels on scratch that lives
+// in the file-scope device array below: at most kNoAllocMaxItems pairs, about
+// 12.6 MB that every device which loads this library keeps until the process
+// exits.  All calls share that one array and it keeps the previous call's
+// contents, so each call clears what must start at zero, and calls that overlap
+// on the GPU (concurrent streams) race with each other.
+namespace dnasa {
+namespace noalloc {
+
+constexpr int64_t kNoAllocMaxItems = DNASA_NOALLOC_MAX_ITEMS;
+constexpr int kNoAllocItemsPerThread = 15;                            // 3840-item tiles
+constexpr int kNoAllocTile = kThreads * kNoAllocItemsPerThread;
+constexpr int kNoAllocTiles = (int)((kNoAllocMaxItems + kNoAllocTile - 1) / kNoAllocTile);
+
+struct NoAllocScratch {
+    unsigned long long keys[kNoAllocMaxItems];                  // alternate key buffer
+    uint32_t vals[kNoAllocMaxItems];                            // alternate value buffer
+    unsigned long long status[(size_t)kNoAllocTiles * kRadix];  // look-back words
+    uint32_t hist[8 * kRadix];                                  // digit counts, then offsets
+    uint32_t tile_ctr[8];                                       // one tile counter per pass
+    uint32_t err;                                               // DERR_* flags of the call
+};
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoAllocScratch)];
+
+// Device address of g_noalloc_scratch per device ordinal, found once per device.
+static NoAllocScratch *g_noalloc_addr[64];
+
+__global__ void k_noalloc_clear(NoAllocScratch *S, int tiles) {
+    const int64_t words = (int64_t)tiles * kRadix;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < words;
+         i += (int64_t)gridDim.x * blockDim.x)
+        S->status[i] = 0ull;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < 8 * kRadix; i += gridDim.x * blockDim.x)
+        S->hist[i] = 0u;
+    if (blockIdx.x == 0 && threadIdx.x < 8) S->tile_ctr[threadIdx.x] = 0u;
+    if (blockIdx.x == 0 && threadIdx.x == 0) S->err = 0u;
+}
+
+template <bool HAS_VALS>
+int noalloc_sort(NoAllocScratch *S, unsigned long long *keys, uint32_t *vals, int64_t n,
+                 int key_bits, int num_sms, cudaStream_t s) {
+    const int passes = (key_bits + kRadixBits - 1) / kRadixBits;
+    const int tiles = ceil_div(n, kNoAllocTile);
+    k_noalloc_clear<<<std::max(1, std::min(tiles, 64)), 256, 0, s>>>(S, tiles);
+    int grid = std::max(1, (int)std::min<int64_t>((int64_t)num_sms * 8, ceil_div(n, kThreads * 8)));
+    k_hist<unsigned long long><<<grid, kThreads, 0, s>>>(keys, n, nullptr, passes, S->hist);
+    k_hist_scan<<<passes, kRadix, 0, s>>>(S->hist);
+    if (cudaGetLastError() != cudaSuccess) return DNASA_CUDA_ERROR;
+    unsigned long long *kb[2] = {keys, S->keys};
+    uint32_t *vb[2] = {vals, S->vals};
+    int cur = 0;
+    for (int p = 0; p < passes; ++p) {
+        cudaError_t e = launch_pass<unsigned long long, kNoAllocItemsPerThread, HAS_VALS, 8>(
+            tiles, s, kb[cur], HAS_VALS ? vb[cur] : nullptr, kb[cur ^ 1],
+            HAS_VALS ? vb[cur ^ 1] : nullptr, S->hist + p * kRadix, S->status, S->tile_ctr + p, n,
+            nullptr, p * kRadixBits, (uint32_t)(p + 1), &S->err);
+        if (e != cudaSuccess) return DNASA_CUDA_ERROR;
+        cur ^= 1;
+    }
+    if (cur == 1) {   // result sits in the scratch buffers: copy it back
+        if (cudaMemcpyAsync(keys, S->keys, (size_t)n * 8, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+            return DNASA_CUDA_ERROR;
+        if (HAS_VALS &&
+            cudaMemcpyAsync(vals, S->vals, (size_t)n * 4, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+            return DNASA_CUDA_ERROR;
+    }
+    uint32_t err = 0;
+    if (cudaMemcpyAsync(&err, &S->err, sizeof(err), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return DNASA_CUDA_ERROR;
+    if (err & DERR_TIMEOUT) return DNASA_DEVICE_TIMEOUT;
+    return err ? DNASA_CUDA_ERROR : DNASA_OK;
+}
+
+}  // namespace noalloc
+}  // namespace dnasa
+
+using namespace dnasa::noalloc;
+
+extern "C" int dnasa_sort_pairs_noalloc(uint64_t *keys, uint32_t *vals, int64_t n, int key_bits,
+                                        void *stream) {
+    if (n < 0 || key_bits < 1 || key_bits > 64) return DNASA_INVALID_ARG;
+    if (n > kNoAllocMaxItems) return DNASA_CAPACITY;
+    if (n == 0) return DNASA_OK;
+    if (!keys) return DNASA_INVALID_ARG;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return DNASA_CUDA_ERROR;
+    if (!g_noalloc_addr[dev]) {
+        // First call on this device: look up the array's device address (with
+        // this device current).  Make this first call before any stream capture.
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return DNASA_CUDA_ERROR;
+        }
+        g_noalloc_addr[dev] = reinterpret_cast<NoAllocScratch *>(p);
+    }
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned long long *k = reinterpret_cast<unsigned long long *>(keys);
+    return vals ? noalloc_sort<true>(g_noalloc_addr[dev], k, vals, n, key_bits, sms, s)
+                : noalloc_sort<false>(g_noalloc_addr[dev], k, nullptr, n, key_bits, sms, s);
+}
