@@ -297,10 +297,14 @@ def main():
         tfile = os.path.join(ROOT, "profiles", "traffic.json")
         if os.path.exists(tfile):
             try:
-                tj = json.load(open(tfile))
-                if name in tj and tj[name].get("valid", False):
-                    # dram bytes per algorithmic byte from one ncu capture, scaled per launch
-                    traffic = tj[name]["dram_per_algorithmic_byte"] * d["bytes"] / d["launches"]
+                import hashlib
+
+                tj = json.load(open(tfile)).get(name)
+                src = os.path.join(ROOT, tj["source"]) if tj else None
+                if tj and tj.get("valid") and src and os.path.exists(src):
+                    # the counters hold only while the kernel source is the captured one
+                    if hashlib.sha1(open(src, "rb").read()).hexdigest() == tj["source_sha1"]:
+                        traffic = tj["dram_per_algorithmic_byte"] * d["bytes"] / d["launches"]
             except Exception:
                 traffic = None
         roofline = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak,
