@@ -242,6 +242,34 @@ int assemble(dnasa_ctx *ctx, const uint8_t *text, int64_t N, int32_t min_overlap
              uint8_t *contigs, int64_t cap, int64_t *contig_off, int64_t off_cap,
              int64_t *n_contigs, int64_t *needed, void *stream);
 
+/* ---- S11: batched -- many independent fragment sets in one pass ------------- */
+
+/* Suffix arrays of n_inst independent fragment texts stored one after another
+ * (instance i = text[inst_off[i] .. inst_off[i+1]), itself '$'-terminated
+ * fragments), built together: every kernel of the build runs once over all
+ * instances, with the instance number as the most significant part of the
+ * initial key, so that each instance's suffixes land in its own slot range.
+ *   packed, toff, n_reads, N   as for sa_build, over the concatenated text
+ *   inst_off   host, n_inst + 1 offsets: 0, ..., N, each a fragment start
+ *   sa         device int32[N]: sa[inst_off[i] + j] = position, inside instance
+ *              i, of instance i's j-th smallest suffix (its own SA, local coords)
+ * Synchronizes the stream once per doubling round (as sa_build). */
+int sa_build_batched(dnasa_ctx *ctx, const uint64_t *packed, const int64_t *toff, int64_t n_reads,
+                     int64_t N, const int64_t *inst_off, int32_t n_inst, int32_t *sa,
+                     const dnasa_opts *opts, void *stream);
+
+/* The whole method (as assemble) on n_inst independent fragment texts at once.
+ * No overlap, containment or chain ever joins two instances.  Contigs are
+ * written instance by instance; inst_contig_off (device, n_inst + 1 int64, may
+ * be NULL) receives the index of each instance's first contig, so instance i
+ * owns contigs [inst_contig_off[i], inst_contig_off[i+1]).  Fragment indices
+ * inside an instance, and hence its result, are the same as when the instance
+ * is assembled alone.  Other arguments as for assemble.  Synchronizes. */
+int assemble_batched(dnasa_ctx *ctx, const uint8_t *texts, const int64_t *inst_off, int32_t n_inst,
+                     int32_t min_overlap, const dnasa_opts *opts, uint8_t *contigs, int64_t cap,
+                     int64_t *contig_off, int64_t off_cap, int64_t *inst_contig_off,
+                     int64_t *n_contigs, int64_t *needed, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

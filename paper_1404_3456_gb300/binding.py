@@ -74,6 +74,9 @@ _SIGS = {
                               ctypes.POINTER(_I64), _P, _P]),
     "assemble": (_INT, [_P, _P, _I64, _I32, _P, _I64, _P, _I64, ctypes.POINTER(_I64),
                         ctypes.POINTER(_I64), _P]),
+    "sa_build_batched": (_INT, [_P, _P, _P, _I64, _I64, _P, _I32, _P, ctypes.POINTER(Opts), _P]),
+    "assemble_batched": (_INT, [_P, _P, _P, _I32, _I32, ctypes.POINTER(Opts), _P, _I64, _P, _I64,
+                                _P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), _P]),
 }
 
 
@@ -270,3 +273,55 @@ def assemble_text(ctx: Context, text: torch.Tensor, min_overlap: int, stream=Non
     buf = contigs[:nb].cpu().numpy().tobytes()
     o = off[: nc + 1].cpu().tolist()
     return [buf[o[i]: o[i + 1]] for i in range(nc)]
+
+
+def _host_i64(offsets):
+    import numpy as np
+
+    a = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+    return a, a.ctypes.data_as(ctypes.c_void_p)
+
+
+def sa_build_batched(ctx: Context, packed, toff, n_reads: int, N: int, inst_off, sa,
+                     opts: Opts | None = None, stream=None):
+    """Per-instance suffix arrays (local coordinates) of concatenated instance texts."""
+    arr, p = _host_i64(inst_off)
+    ctx.check(lib().sa_build_batched(ctx.handle, _ptr(packed), _ptr(toff), n_reads, N, p,
+                                     arr.size - 1, _ptr(sa),
+                                     ctypes.byref(opts) if opts is not None else None,
+                                     _stream(stream)))
+
+
+def assemble_batched(ctx: Context, texts, inst_off, min_overlap: int, contigs, contig_off,
+                     inst_contig_off=None, opts: Opts | None = None, stream=None):
+    """Returns (n_contigs, bytes)."""
+    arr, p = _host_i64(inst_off)
+    nc = ctypes.c_int64(0)
+    need = ctypes.c_int64(0)
+    ctx.check(lib().assemble_batched(ctx.handle, _ptr(texts), p, arr.size - 1, min_overlap,
+                                     ctypes.byref(opts) if opts is not None else None,
+                                     _ptr(contigs), contigs.numel(), _ptr(contig_off),
+                                     contig_off.numel(),
+                                     _ptr(inst_contig_off) if inst_contig_off is not None else None,
+                                     ctypes.byref(nc), ctypes.byref(need), _stream(stream)))
+    return nc.value, need.value
+
+
+def assemble_texts_batched(ctx: Context, texts_np, min_overlap: int, opts=None, stream=None):
+    """Contigs of several fragment texts (numpy uint8 arrays), assembled in one
+    batched call; returns one list of contig bytes per instance."""
+    import numpy as np
+
+    sizes = [int(t.size) for t in texts_np]
+    inst_off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    joined = torch.from_numpy(np.concatenate(texts_np)).cuda()
+    N = int(inst_off[-1])
+    contigs = torch.empty(max(N, 1), dtype=torch.uint8, device="cuda")
+    off = torch.empty(N // 2 + 2, dtype=torch.int64, device="cuda")
+    ioff = torch.empty(len(texts_np) + 1, dtype=torch.int64, device="cuda")
+    nc, nb = assemble_batched(ctx, joined, inst_off, min_overlap, contigs, off, ioff, opts, stream)
+    buf = contigs[:nb].cpu().numpy().tobytes()
+    o = off[: nc + 1].cpu().tolist()
+    io = ioff.cpu().tolist()
+    return [[buf[o[c]: o[c + 1]] for c in range(io[i], io[i + 1])] for i in range(len(texts_np))]
+

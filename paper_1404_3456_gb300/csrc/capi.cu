@@ -87,6 +87,64 @@ int sa_view(dnasa_ctx *ctx, const void *sa, int idx_width, int64_t N, DevBuf &tm
     return DNASA_OK;
 }
 
+// inst_roff[i] = the fragment that starts at text offset inst_toff[i] (flags an
+// instance boundary that is not a fragment start).
+__global__ void k_inst_roff(const int64_t *__restrict__ toff, int64_t n_reads,
+                            const int64_t *__restrict__ inst_toff, int32_t n_inst,
+                            int64_t *__restrict__ inst_roff, uint32_t *err) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= n_inst;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t x = inst_toff[i];
+        int64_t lo = 0, hi = n_reads + 1;     // first r with toff[r] >= x
+        while (lo < hi) {
+            int64_t m = (lo + hi) >> 1;
+            if (toff[m] < x) lo = m + 1; else hi = m;
+        }
+        if (lo > n_reads || toff[lo] != x) atomicOr(err, DERR_BOUNDS);
+        inst_roff[i] = lo;
+    }
+}
+
+// SA slots of instance i are [inst_toff[i], inst_toff[i+1]); rewrite positions
+// in the instance's own coordinates.
+__global__ void k_localize(uint32_t *__restrict__ sa, int64_t N, const int64_t *__restrict__ inst_toff,
+                           int32_t n_inst) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < N;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = upper_index(inst_toff, 0, n_inst, j);
+        sa[j] = (uint32_t)((int64_t)sa[j] - __ldg(inst_toff + i));
+    }
+}
+
+// Device copies of the instance offsets (text and fragment), with checks.
+int make_instances(dnasa_ctx *ctx, const int64_t *toff, int64_t n_reads, int64_t N,
+                   const int64_t *inst_toff_host, int32_t n_inst, DevBuf &inst_toff, DevBuf &inst_roff,
+                   int64_t *max_reads, cudaStream_t s) {
+    if (inst_toff_host[0] != 0 || inst_toff_host[n_inst] != N)
+        return fail(ctx, DNASA_INVALID_ARG, "batched: inst_off must start at 0 and end at N");
+    for (int i = 0; i < n_inst; ++i)
+        if (inst_toff_host[i + 1] <= inst_toff_host[i])
+            return fail(ctx, DNASA_INVALID_ARG, "batched: inst_off must increase strictly");
+    DNASA_TRY(dev_alloc(ctx, inst_toff, (size_t)(n_inst + 1) * 8, s));
+    DNASA_TRY(dev_alloc(ctx, inst_roff, (size_t)(n_inst + 1) * 8, s));
+    DNASA_CUDA(ctx, cudaMemcpyAsync(inst_toff.p, inst_toff_host, (size_t)(n_inst + 1) * 8,
+                                    cudaMemcpyHostToDevice, s));
+    {
+        LaunchScope ls_(ctx, PK_OTHER, s, 0.0);
+        k_inst_roff<<<ceil_div(n_inst + 1, 256), 256, 0, s>>>(toff, n_reads, (const int64_t *)inst_toff.p,
+                                                             n_inst, (int64_t *)inst_roff.p, &ctx->ctrl->err);
+    }
+    DNASA_CUDA(ctx, cudaGetLastError());
+    std::vector<int64_t> roff((size_t)n_inst + 1);
+    DNASA_CUDA(ctx, cudaMemcpyAsync(roff.data(), inst_roff.p, (size_t)(n_inst + 1) * 8,
+                                    cudaMemcpyDeviceToHost, s));
+    int rc = check_device_status(ctx, s, "batched");
+    if (rc != DNASA_OK) return fail(ctx, DNASA_INVALID_ARG, "batched: an instance does not start at a fragment");
+    *max_reads = 0;
+    for (int i = 0; i < n_inst; ++i) *max_reads = std::max(*max_reads, roff[i + 1] - roff[i]);
+    return DNASA_OK;
+}
+
 }  // namespace
 
 // Whole pipeline on a text already on the device, possibly several instances.
@@ -103,29 +161,8 @@ int assemble_impl(dnasa_ctx *ctx, const uint8_t *text, int64_t N, const int64_t 
     TextDesc t = one_instance((const uint64_t *)packed.p, (const int64_t *)toff.p, n_reads, N);
     int64_t max_reads = n_reads;
     if (n_inst > 1) {
-        // fragment offsets of the instances: the fragment index at each instance start
-        std::vector<int64_t> roff(n_inst + 1);
-        DNASA_TRY(dev_alloc(ctx, inst_toff, (size_t)(n_inst + 1) * 8, s));
-        DNASA_TRY(dev_alloc(ctx, inst_roff, (size_t)(n_inst + 1) * 8, s));
-        DNASA_CUDA(ctx, cudaMemcpyAsync(inst_toff.p, inst_toff_host, (size_t)(n_inst + 1) * 8,
-                                        cudaMemcpyHostToDevice, s));
-        std::vector<int64_t> toff_h((size_t)n_reads + 1);
-        DNASA_CUDA(ctx, cudaMemcpyAsync(toff_h.data(), toff.p, (size_t)(n_reads + 1) * 8,
-                                        cudaMemcpyDeviceToHost, s));
-        DNASA_CUDA(ctx, cudaStreamSynchronize(s));
-        max_reads = 0;
-        for (int i = 0; i <= n_inst; ++i) {
-            auto it = std::lower_bound(toff_h.begin(), toff_h.end(), inst_toff_host[i]);
-            if (it == toff_h.end() || *it != inst_toff_host[i])
-                return fail(ctx, DNASA_INVALID_ARG, "assemble_batched: an instance does not start at a fragment");
-            roff[i] = it - toff_h.begin();
-            if (i > 0) max_reads = std::max(max_reads, roff[i] - roff[i - 1]);
-            if (i > 0 && roff[i] <= roff[i - 1])
-                return fail(ctx, DNASA_INVALID_ARG, "assemble_batched: empty instance");
-        }
-        DNASA_CUDA(ctx, cudaMemcpyAsync(inst_roff.p, roff.data(), (size_t)(n_inst + 1) * 8,
-                                        cudaMemcpyHostToDevice, s));
-        DNASA_CUDA(ctx, cudaStreamSynchronize(s));
+        DNASA_TRY(make_instances(ctx, (const int64_t *)toff.p, n_reads, N, inst_toff_host, n_inst,
+                                 inst_toff, inst_roff, &max_reads, s));
         t.inst_toff = (const int64_t *)inst_toff.p;
         t.inst_roff = (const int64_t *)inst_roff.p;
         t.n_inst = n_inst;
@@ -235,6 +272,56 @@ int assemble(dnasa_ctx *ctx, const uint8_t *text, int64_t N, int32_t min_overlap
     cudaSetDevice(ctx->device);
     return assemble_impl(ctx, text, N, nullptr, 1, min_overlap, contigs, cap, contig_off, off_cap,
                          nullptr, n_contigs, needed, nullptr, (cudaStream_t)stream);
+}
+
+int sa_build_batched(dnasa_ctx *ctx, const uint64_t *packed, const int64_t *toff, int64_t n_reads,
+                     int64_t N, const int64_t *inst_off, int32_t n_inst, int32_t *sa,
+                     const dnasa_opts *opts, void *stream) {
+    if (!ctx) return DNASA_INVALID_ARG;
+    ctx->last_error.clear();
+    DNASA_TRY(check_text_args(ctx, packed, toff, n_reads, N, "sa_build_batched"));
+    if (n_inst < 1 || !inst_off) return fail(ctx, DNASA_INVALID_ARG, "sa_build_batched: n_inst >= 1 and inst_off required");
+    if (!is_device_ptr(ctx, sa)) return fail(ctx, DNASA_INVALID_ARG, "sa_build_batched: sa must be a device pointer");
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    TextDesc t = one_instance(packed, toff, n_reads, N);
+    DevBuf inst_toff, inst_roff;
+    if (n_inst > 1) {
+        int64_t max_reads;
+        DNASA_TRY(make_instances(ctx, toff, n_reads, N, inst_off, n_inst, inst_toff, inst_roff, &max_reads, s));
+        t.inst_toff = (const int64_t *)inst_toff.p;
+        t.inst_roff = (const int64_t *)inst_roff.p;
+        t.n_inst = n_inst;
+    }
+    DNASA_TRY(sa_build_u32(ctx, t, (uint32_t *)sa, opts, s));
+    if (n_inst > 1) {
+        int grid = (int)std::min<int64_t>(ceil_div(N, 256), (int64_t)ctx->num_sms * 16);
+        LaunchScope ls_(ctx, PK_OTHER, s, 8.0 * N);
+        k_localize<<<std::max(grid, 1), 256, 0, s>>>((uint32_t *)sa, N, t.inst_toff, n_inst);
+    }
+    DNASA_CUDA(ctx, cudaGetLastError());
+    return DNASA_OK;
+}
+
+int assemble_batched(dnasa_ctx *ctx, const uint8_t *texts, const int64_t *inst_off, int32_t n_inst,
+                     int32_t min_overlap, const dnasa_opts *opts, uint8_t *contigs, int64_t cap,
+                     int64_t *contig_off, int64_t off_cap, int64_t *inst_contig_off,
+                     int64_t *n_contigs, int64_t *needed, void *stream) {
+    if (!ctx) return DNASA_INVALID_ARG;
+    ctx->last_error.clear();
+    if (n_inst < 1 || !inst_off) return fail(ctx, DNASA_INVALID_ARG, "assemble_batched: n_inst >= 1 and inst_off required");
+    const int64_t N = inst_off[n_inst];
+    if (N <= 0 || N >= (int64_t(1) << 31) || min_overlap < 1 || !n_contigs || !needed || cap < 0 ||
+        off_cap < 1)
+        return fail(ctx, DNASA_INVALID_ARG, "assemble_batched: bad size, min_overlap or null output");
+    if (!is_device_ptr(ctx, texts) || !is_device_ptr(ctx, contig_off) ||
+        (cap > 0 && !is_device_ptr(ctx, contigs)) ||
+        (inst_contig_off && !is_device_ptr(ctx, inst_contig_off)))
+        return fail(ctx, DNASA_INVALID_ARG, "assemble_batched: texts, contigs, contig_off and "
+                                            "inst_contig_off must be device pointers");
+    cudaSetDevice(ctx->device);
+    return assemble_impl(ctx, texts, N, inst_off, n_inst, min_overlap, contigs, cap, contig_off,
+                         off_cap, inst_contig_off, n_contigs, needed, opts, (cudaStream_t)stream);
 }
 
 }  // extern "C"
