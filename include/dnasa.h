@@ -270,6 +270,54 @@ int assemble_batched(dnasa_ctx *ctx, const uint8_t *texts, const int64_t *inst_o
                      int64_t *contig_off, int64_t off_cap, int64_t *inst_contig_off,
                      int64_t *n_contigs, int64_t *needed, void *stream);
 
+/* ---- S12: served -- continuous batching of arriving assembly jobs ------------ */
+
+/* One assembly job: a '$'-terminated fragment text in HOST memory (copied at
+ * submit, so the caller may free it afterwards). */
+typedef struct {
+    const uint8_t *text;
+    int64_t N;
+    int32_t min_overlap;
+    int32_t reserved;
+} dnasa_job;
+
+/* A finished job.  contigs / contig_off point into server-owned host memory that
+ * stays valid until the next dnasa_server_poll or dnasa_server_destroy: contig c
+ * is contigs[contig_off[c] .. contig_off[c+1]).  Times are milliseconds since
+ * the server was created: submitted, batch started on a slot, result ready. */
+typedef struct {
+    uint64_t id;
+    int32_t status;            /* dnasa_status of the job's batch */
+    int32_t reserved;
+    int64_t n_contigs;
+    int64_t bytes;
+    const uint8_t *contigs;
+    const int64_t *contig_off;
+    double t_submit_ms, t_start_ms, t_done_ms;
+} dnasa_result;
+
+typedef struct dnasa_server dnasa_server;
+
+/* Starts a server on `device` with `slots` workers (own context and stream each,
+ * 1..16) that admit queued jobs, in arrival order, as batches of at most
+ * max_batch jobs of equal min_overlap, while their estimated device memory
+ * (about 80 bytes per text symbol) fits in hbm_budget (0 = 90 % of the free
+ * memory at creation) less what the batches already running hold.  A job larger
+ * than the whole budget runs alone once nothing else runs.  Batches of different
+ * slots overlap on the GPU.  Each result equals that job assembled alone. */
+int dnasa_server_create(int device, size_t hbm_budget, int32_t slots, int32_t max_batch,
+                        dnasa_server **out);
+/* Queues a job (thread-safe; returns at once). */
+int dnasa_server_submit(dnasa_server *srv, const dnasa_job *job, uint64_t id);
+/* Moves up to max_results finished jobs into out (host array), waiting up to
+ * wait_ms for the first one; *n_out = how many were written. */
+int dnasa_server_poll(dnasa_server *srv, dnasa_result *out, int32_t max_results, int32_t wait_ms,
+                      int32_t *n_out);
+/* Jobs queued or running. */
+int dnasa_server_pending(dnasa_server *srv);
+/* Finishes every queued job, then stops the workers and frees everything. */
+void dnasa_server_destroy(dnasa_server *srv);
+
 #ifdef __cplusplus
 }
 #endif

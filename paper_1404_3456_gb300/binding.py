@@ -50,6 +50,19 @@ class ProfEntry(ctypes.Structure):
 PROF_KINDS = ["onesweep", "hist", "rerank", "gather", "init_keys", "finish", "lcp", "overlap",
               "layout", "pack", "other"]
 
+class Job(ctypes.Structure):
+    _fields_ = [("text", ctypes.c_void_p), ("N", ctypes.c_int64), ("min_overlap", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint64), ("status", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("n_contigs", ctypes.c_int64), ("bytes", ctypes.c_int64),
+                ("contigs", ctypes.POINTER(ctypes.c_uint8)), ("contig_off", ctypes.POINTER(ctypes.c_int64)),
+                ("t_submit_ms", ctypes.c_double), ("t_start_ms", ctypes.c_double),
+                ("t_done_ms", ctypes.c_double)]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -74,6 +87,11 @@ _SIGS = {
                               ctypes.POINTER(_I64), _P, _P]),
     "assemble": (_INT, [_P, _P, _I64, _I32, _P, _I64, _P, _I64, ctypes.POINTER(_I64),
                         ctypes.POINTER(_I64), _P]),
+    "dnasa_server_create": (_INT, [_INT, ctypes.c_size_t, _I32, _I32, ctypes.POINTER(_P)]),
+    "dnasa_server_submit": (_INT, [_P, ctypes.POINTER(Job), ctypes.c_uint64]),
+    "dnasa_server_poll": (_INT, [_P, ctypes.POINTER(Result), _I32, _I32, ctypes.POINTER(_I32)]),
+    "dnasa_server_pending": (_INT, [_P]),
+    "dnasa_server_destroy": (None, [_P]),
     "sa_build_batched": (_INT, [_P, _P, _P, _I64, _I64, _P, _I32, _P, ctypes.POINTER(Opts), _P]),
     "assemble_batched": (_INT, [_P, _P, _P, _I32, _I32, ctypes.POINTER(Opts), _P, _I64, _P, _I64,
                                 _P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), _P]),
@@ -324,4 +342,56 @@ def assemble_texts_batched(ctx: Context, texts_np, min_overlap: int, opts=None, 
     o = off[: nc + 1].cpu().tolist()
     io = ioff.cpu().tolist()
     return [[buf[o[c]: o[c + 1]] for c in range(io[i], io[i + 1])] for i in range(len(texts_np))]
+
+
+class Server:
+    """Continuous-batching assembly server (dnasa_server_* in the C ABI)."""
+
+    def __init__(self, device: int = 0, hbm_budget: int = 0, slots: int = 2, max_batch: int = 64):
+        torch.cuda.init()
+        h = ctypes.c_void_p()
+        rc = lib().dnasa_server_create(device, hbm_budget, slots, max_batch, ctypes.byref(h))
+        if rc != 0:
+            raise DnasaError(rc, "dnasa_server_create failed")
+        self.handle = h
+
+    def submit(self, text, min_overlap: int, job_id: int):
+        """text: numpy uint8 array (host); copied by the server."""
+        import numpy as np
+
+        t = np.ascontiguousarray(text, dtype=np.uint8)
+        job = Job(t.ctypes.data_as(ctypes.c_void_p), t.size, min_overlap, 0)
+        rc = lib().dnasa_server_submit(self.handle, ctypes.byref(job), job_id)
+        if rc != 0:
+            raise DnasaError(rc, "dnasa_server_submit failed")
+
+    def poll(self, max_results: int = 256, wait_ms: int = 0):
+        """Finished jobs: list of dicts (id, status, contigs [bytes...], times in ms)."""
+        arr = (Result * max(max_results, 1))()
+        n = ctypes.c_int32(0)
+        rc = lib().dnasa_server_poll(self.handle, arr, max_results, wait_ms, ctypes.byref(n))
+        if rc != 0:
+            raise DnasaError(rc, "dnasa_server_poll failed")
+        out = []
+        for r in arr[: n.value]:
+            buf = ctypes.string_at(r.contigs, r.bytes) if r.bytes else b""
+            offs = [r.contig_off[i] for i in range(r.n_contigs + 1)] if r.n_contigs else [0]
+            out.append(dict(id=r.id, status=r.status,
+                            contigs=[buf[offs[i]: offs[i + 1]] for i in range(r.n_contigs)],
+                            t_submit_ms=r.t_submit_ms, t_start_ms=r.t_start_ms, t_done_ms=r.t_done_ms))
+        return out
+
+    def pending(self) -> int:
+        return int(lib().dnasa_server_pending(self.handle))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().dnasa_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 

@@ -321,13 +321,10 @@ cudaError_t launch_pass(int tiles, cudaStream_t s, const K *kin, const uint32_t 
                         int shift, uint32_t epoch, uint32_t *err) {
     size_t smem = onesweep_smem<K, ITEMS, HAS_VALS>();
     auto kern = k_onesweep<K, ITEMS, HAS_VALS, LBW>;
-    static bool configured = false;  // per instantiation; same value on every device
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
+    // once per instantiation (thread-safe static initialisation)
+    static const cudaError_t configured =
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (configured != cudaSuccess) return configured;
     kern<<<tiles, kThreads, smem, s>>>(kin, vin, kout, vout, bucket, status, tile_ctr, n_host,
                                        d_n, shift, epoch, err);
     return cudaGetLastError();

@@ -526,14 +526,15 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
     RadixScratch rs = radix_scratch_take(a, N, 64, tile_items);
     if (!rs.hist || !rr_status) return fail(ctx, DNASA_OOM, "sa_build workspace");
 
-    static bool smem_set = false;
-    if (!smem_set) {
-        DNASA_CUDA(ctx, cudaFuncSetAttribute(k_rerank<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)sizeof(RerankSmem)));
-        DNASA_CUDA(ctx, cudaFuncSetAttribute(k_rerank<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)sizeof(RerankSmem)));
-        smem_set = true;
-    }
+    // once per process (thread-safe static initialisation)
+    static const cudaError_t smem_set = [] {
+        cudaError_t e = cudaFuncSetAttribute(k_rerank<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)sizeof(RerankSmem));
+        if (e != cudaSuccess) return e;
+        return cudaFuncSetAttribute(k_rerank<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)sizeof(RerankSmem));
+    }();
+    DNASA_CUDA(ctx, smem_set);
     DevCtrl *c = ctx->ctrl;
     unsigned long long *cnt = c->count;
     dnasa_trace &tr = ctx->trace;

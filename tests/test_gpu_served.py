@@ -1,0 +1,83 @@
+"""S12 served: jobs submitted while others run are batched and overlapped; each
+result must be, byte for byte, the job assembled alone (tolerance zero)."""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+from paper_1404_3456_gb300 import synth  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+def B():
+    from paper_1404_3456_gb300 import binding
+
+    return binding
+
+
+def jobs(n, seed=3):
+    out = []
+    for i in range(n):
+        j = synth.served_job(seed, i, g_lo=5_000, g_hi=60_000)
+        out.append(j)
+    return out
+
+
+def test_server_results_equal_alone():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    js = jobs(24)
+    ctx = B().Context(0)
+    alone = [B().assemble_text(ctx, torch.from_numpy(j["text"]).cuda(), j["min_overlap"]) for j in js]
+    ctx.close()
+    srv = B().Server(0, slots=2, max_batch=8)
+    got = {}
+    # submit from another thread at staggered times, so that jobs arrive while
+    # earlier batches are on the GPU
+    def feed():
+        for i, j in enumerate(js):
+            srv.submit(j["text"], j["min_overlap"], i)
+            time.sleep(0.002 * (i % 3))
+    th = threading.Thread(target=feed)
+    th.start()
+    deadline = time.time() + 120
+    while len(got) < len(js) and time.time() < deadline:
+        for r in srv.poll(64, wait_ms=200):
+            assert r["status"] == 0
+            got[r["id"]] = r
+    th.join()
+    srv.close()
+    assert len(got) == len(js)
+    for i in range(len(js)):
+        assert got[i]["contigs"] == alone[i], i
+        assert got[i]["t_submit_ms"] <= got[i]["t_start_ms"] <= got[i]["t_done_ms"]
+    # and against the oracle for a few
+    for i in (0, 5, 11):
+        buf, off = oracle.assemble(js[i]["text"], js[i]["min_overlap"])
+        assert got[i]["contigs"] == oracle.contigs_as_list(buf, off)
+
+
+def test_server_admission_by_budget():
+    """A budget that fits one job at a time still finishes every job (one by one)."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    js = jobs(5, seed=4)
+    srv = B().Server(0, hbm_budget=1, slots=2, max_batch=8)   # nothing fits: each runs alone
+    for i, j in enumerate(js):
+        srv.submit(j["text"], j["min_overlap"], i)
+    got = {}
+    deadline = time.time() + 60
+    while len(got) < len(js) and time.time() < deadline:
+        for r in srv.poll(64, wait_ms=200):
+            got[r["id"]] = r
+    srv.close()
+    assert sorted(got) == list(range(5))
+    # alone in the GPU: no two jobs' [start, done] windows overlap
+    spans = sorted((r["t_start_ms"], r["t_done_ms"]) for r in got.values())
+    for (a0, a1), (b0, b1) in zip(spans, spans[1:]):
+        assert b0 >= a1 - 1e-6
