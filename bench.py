@@ -55,6 +55,15 @@ def parse():
     ap.add_argument("--genome", type=int, default=G, help="genome length (default 64,000,000)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default="sa64m", choices=["sa64m", "batched", "served"])
+    ap.add_argument("--instances", type=int, default=4096, help="batched: fragment sets per batch")
+    ap.add_argument("--solo-sample", type=int, default=256,
+                    help="batched: instances timed one job per launch")
+    ap.add_argument("--jobs", type=int, default=48, help="served: distinct jobs in the trace")
+    ap.add_argument("--lambdas", default="0.5,0.9,1.25",
+                    help="served: arrival rates as multiples of one-job-per-launch capacity")
+    ap.add_argument("--slots", type=int, default=2)
+    ap.add_argument("--max-batch", type=int, default=16)
     return ap.parse_args()
 
 
@@ -172,10 +181,231 @@ def run_reference(args):
     return 0
 
 
+def pctl(xs, q):
+    xs = sorted(xs)
+    if not xs:
+        return None
+    k = min(len(xs) - 1, max(0, int(round(q / 100.0 * (len(xs) - 1)))))
+    return xs[k]
+
+
+def roofline_of(prof, peak, peak_src):
+    if not prof:
+        return None, {}
+    name, d = max(prof.items(), key=lambda kv: kv[1]["ms"])
+    achieved = d["bytes"] / (d["ms"] / 1000.0) / 1e9 if d["ms"] > 0 else 0.0
+    total = sum(x["ms"] for x in prof.values())
+    kernels = {k: {"launches": v["launches"], "ms": v["ms"], "share": v["ms"] / total}
+               for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])}
+    return ({"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
+             "frac": achieved / peak, "peak_source": peak_src, "traffic": None,
+             "launches": d["launches"]}, kernels)
+
+
+def run_batched(args):
+    """Batched workload: independent fragment sets (genome log-uniform 2-200 kbp,
+    reads U{100..1000} at 8x, min overlap 31) assembled by one assemble_batched
+    call per step, against one assemble() call per instance."""
+    import torch
+
+    import oracle
+    from paper_1404_3456_gb300 import binding, synth
+
+    rank, local_rank, world = dist_env()
+    torch.cuda.set_device(local_rank)
+    insts = [synth.batched_instance(args.seed + 1000 * rank, i) for i in range(args.instances)]
+    texts = [x["text"] for x in insts]
+    inst_off = np.concatenate([[0], np.cumsum([t.size for t in texts])]).astype(np.int64)
+    N = int(inst_off[-1])
+    ctx = binding.Context(local_rank)
+    h_text = torch.from_numpy(np.concatenate(texts)).pin_memory()
+    d_text = h_text.cuda()
+    contigs = torch.empty(N, dtype=torch.uint8, device="cuda")
+    off = torch.empty(N // 2 + 2, dtype=torch.int64, device="cuda")
+    ioff = torch.empty(len(texts) + 1, dtype=torch.int64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step(t=d_text):
+        return binding.assemble_batched(ctx, t, inst_off, 31, contigs, off, ioff)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    l0 = ctx.launch_count()
+    ctx.profile(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        nc, nb = step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    launches = ctx.launch_count() - l0
+    ms = e0.elapsed_time(e1) / args.steps
+    # end to end: text from pinned host memory, contigs and offsets back
+    h_contigs = torch.empty(N, dtype=torch.uint8).pin_memory()
+    x0, x1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    d2 = torch.empty_like(d_text)
+    x0.record(stream)
+    for _ in range(args.steps):
+        d2.copy_(h_text, non_blocking=True)
+        nc, nb = step(d2)
+        h_contigs[:nb].copy_(contigs[:nb], non_blocking=True)
+        ho = off[: nc + 1].cpu()
+    x1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = x0.elapsed_time(x1) / args.steps
+    # one job per launch on the first M instances, and the batch of the same M
+    M = min(args.solo_sample, len(texts))
+    d_solo = [torch.from_numpy(t).cuda() for t in texts[:M]]
+    for t in d_solo[:4]:
+        binding.assemble_text(ctx, t, 31)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for t in d_solo:
+        binding.assemble_text(ctx, t, 31)
+    torch.cuda.synchronize()
+    solo_s = time.perf_counter() - t0
+    sub_off = inst_off[: M + 1]
+    d_sub = d_text[: int(sub_off[-1])]
+    binding.assemble_batched(ctx, d_sub, sub_off, 31, contigs, off, ioff[: M + 1])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    binding.assemble_batched(ctx, d_sub, sub_off, 31, contigs, off, ioff[: M + 1])
+    torch.cuda.synchronize()
+    sub_s = time.perf_counter() - t0
+    cpu = None
+    if not args.no_cpu_baseline:
+        sample = texts[:4]
+        t0 = time.perf_counter()
+        for t in sample:
+            oracle.assemble(t, 31)
+        dt = time.perf_counter() - t0
+        cpu = {"value": len(sample) / dt, "unit": "assemblies/s", "cores": 1, "kind": "oracle",
+               "sample": f"oracle assemble of the first {len(sample)} instances "
+                         f"({sum(t.size for t in sample):,} symbols), {dt:.1f} s"}
+    peak, src = measured_peak()
+    roof, kernels = roofline_of(prof, peak, src)
+    value = len(texts) * world / (ms / 1000.0)
+    line = {
+        "metric": "batched assemblies/s (assemble_batched, 4096 fragment sets)", "value": value,
+        "unit": "assemblies/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u8/int32", "data": "synthetic",
+        "config": {"workload": f"batched: {len(texts)} instances, {N:,} symbols, genome log-uniform "
+                               "2-200 kbp, reads U{100..1000} at 8x, min overlap 31",
+                   "msuffix_per_s": N * world / (ms / 1000.0) / 1e6,
+                   "one_job_per_launch": {"instances": M, "s": solo_s, "assemblies_per_s": M / solo_s},
+                   "batched_same_instances": {"instances": M, "s": sub_s, "assemblies_per_s": M / sub_s}},
+        "roofline": roof, "cpu_baseline": cpu,
+        "e2e": {"value": len(texts) / (e2e_ms / 1000.0), "unit": "assemblies/s",
+                "h2d_bytes_per_step": N, "d2h_bytes_per_step": int(nb) + 8 * (int(nc) + 1),
+                "ms_per_step": e2e_ms},
+        "gpu_launches": launches, "kernels": kernels,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_served(args):
+    """Served workload: jobs with genome log-uniform 5 kbp - 5 Mbp (2 % tandem
+    arrays), 150 bp reads at 10x, min overlap 41, arriving as a Poisson process at
+    several multiples of the one-job-per-launch capacity.  The server (continuous
+    batching) and a FIFO one-job-per-launch loop see the identical trace."""
+    import threading
+
+    import torch
+
+    from paper_1404_3456_gb300 import binding, synth
+
+    rank, local_rank, world = dist_env()
+    torch.cuda.set_device(local_rank)
+    jobs = [synth.served_job(args.seed + 1000 * rank, i) for i in range(args.jobs)]
+    ctx = binding.Context(local_rank)
+    pinned = [torch.from_numpy(j["text"]).pin_memory() for j in jobs]
+
+    def solo(i):  # one job per launch: upload, assemble, contigs back
+        t = pinned[i].cuda(non_blocking=True)
+        return binding.assemble_text(ctx, t, jobs[i]["min_overlap"])
+
+    for i in range(min(3, len(jobs))):
+        solo(i)
+    t0 = time.perf_counter()
+    for i in range(len(jobs)):
+        solo(i)
+    cap_s = time.perf_counter() - t0
+    capacity = len(jobs) / cap_s
+    rng = np.random.default_rng(args.seed)
+    results = []
+    srv = binding.Server(local_rank, slots=args.slots, max_batch=args.max_batch)
+    for f in [float(x) for x in args.lambdas.split(",")]:
+        lam = f * capacity
+        arrivals = np.cumsum(rng.exponential(1.0 / lam, size=len(jobs)))
+        # FIFO one job per launch on the trace
+        lat = []
+        t0 = time.perf_counter()
+        for i, a in enumerate(arrivals):
+            now = time.perf_counter() - t0
+            if now < a:
+                time.sleep(a - now)
+            solo(i)
+            lat.append(1000.0 * (time.perf_counter() - t0 - a))
+        fifo_span = time.perf_counter() - t0 - arrivals[0]
+        # served, same trace
+        done = {}
+        t0 = time.perf_counter()
+
+        def feed():
+            for i, a in enumerate(arrivals):
+                now = time.perf_counter() - t0
+                if now < a:
+                    time.sleep(a - now)
+                srv.submit(jobs[i]["text"], jobs[i]["min_overlap"], i)
+        th = threading.Thread(target=feed)
+        th.start()
+        while len(done) < len(jobs):
+            for r in srv.poll(256, wait_ms=50):
+                done[r["id"]] = (time.perf_counter() - t0, r)
+        th.join()
+        s_lat = [1000.0 * (done[i][0] - arrivals[i]) for i in range(len(jobs))]
+        s_span = max(v[0] for v in done.values()) - arrivals[0]
+        results.append({"lambda_x_capacity": f, "arrival_rate_jobs_per_s": lam,
+                        "served": {"jobs_per_s": len(jobs) / s_span, "p50_ms": pctl(s_lat, 50),
+                                   "p99_ms": pctl(s_lat, 99)},
+                        "one_job_per_launch": {"jobs_per_s": len(jobs) / fifo_span,
+                                               "p50_ms": pctl(lat, 50), "p99_ms": pctl(lat, 99)}})
+    srv.close()
+    top = results[-1]
+    line = {
+        "metric": "served jobs/s and p99 latency vs one-job-per-launch (continuous batching)",
+        "value": top["served"]["jobs_per_s"], "unit": "jobs/s", "n_gpus": world,
+        "steps": len(jobs), "warmup": 3, "ms_per_step": 1000.0 / top["served"]["jobs_per_s"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8/int32",
+        "data": "synthetic",
+        "config": {"workload": f"served: {len(jobs)} jobs (genome log-uniform 5 kbp-5 Mbp, 2% tandem, "
+                               "150 bp reads at 10x, min overlap 41), Poisson arrivals",
+                   "one_job_per_launch_capacity_jobs_per_s": capacity,
+                   "mean_job_symbols": float(np.mean([j["text"].size for j in jobs])),
+                   "slots": args.slots, "max_batch": args.max_batch, "sweep": results},
+        "e2e": {"value": top["served"]["jobs_per_s"], "unit": "jobs/s",
+                "h2d_bytes_per_step": float(np.mean([j["text"].size for j in jobs])),
+                "d2h_bytes_per_step": None},
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args)
+    if args.workload == "served":
+        return run_served(args)
     import torch
 
     rank, local_rank, world = dist_env()

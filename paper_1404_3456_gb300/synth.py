@@ -141,19 +141,32 @@ def tiny(seed: int, G: int = 10_000, read_len: int = 400, n_random: int = 200,
 
 def shotgun(rng, genome: np.ndarray, coverage: float, len_lo: int, len_hi: int):
     """Error-free reads of length U{len_lo..len_hi} at uniform starts until the
-    read bases reach coverage x |genome|."""
+    read bases reach coverage x |genome|.  Returns (reads, starts)."""
     G = genome.size
     target = coverage * G
-    reads, starts = [], []
-    total = 0
-    while total < target:
-        n = int(rng.integers(len_lo, len_hi + 1))
-        n = min(n, G)
-        s = int(rng.integers(0, G - n + 1))
-        reads.append(genome[s: s + n])
-        starts.append(s)
-        total += n
-    return reads, np.array(starts, dtype=np.int64)
+    mean = (len_lo + len_hi) / 2.0
+    lens = np.zeros(0, dtype=np.int64)
+    while lens.sum() < target:
+        more = rng.integers(len_lo, len_hi + 1, size=int(target / mean * 1.1) + 16)
+        lens = np.concatenate([lens, np.minimum(more, G)])
+    cut = int(np.searchsorted(np.cumsum(lens), target)) + 1
+    lens = lens[:cut]
+    starts = rng.integers(0, G - lens + 1)
+    reads = [genome[s: s + n] for s, n in zip(starts, lens)]
+    return reads, starts.astype(np.int64)
+
+
+def shotgun_fixed_text(rng, genome: np.ndarray, coverage: float, read_len: int):
+    """Reads of one length at uniform starts until coverage x |genome| bases, as a
+    '$'-joined text (vectorised).  Returns (text, starts)."""
+    G = genome.size
+    L = min(read_len, G)
+    n = int(np.ceil(coverage * G / L))
+    starts = rng.integers(0, G - L + 1, size=n)
+    text = np.empty((n, L + 1), dtype=np.uint8)
+    text[:, :L] = genome[starts[:, None] + np.arange(L)[None, :]]
+    text[:, L] = SEP
+    return text.ravel(), starts.astype(np.int64)
 
 
 def log_uniform(rng, lo: float, hi: float) -> int:
@@ -180,9 +193,8 @@ def served_job(seed: int, index: int, g_lo: int = 5_000, g_hi: int = 5_000_000,
     rng = rng_for(seed * 1_000_003 + index, 4)
     G = log_uniform(rng, g_lo, g_hi)
     genome = genome_with_repeats(rng, G, 0.02, (2, 50), (10, 200))
-    reads, starts = shotgun(rng, genome, coverage, read_len, read_len)
-    return dict(genome=genome, reads=reads, starts=starts, text=join_reads(reads),
-                min_overlap=min_overlap)
+    text, starts = shotgun_fixed_text(rng, genome, coverage, read_len)
+    return dict(genome=genome, starts=starts, text=text, min_overlap=min_overlap)
 
 
 def sa64m_genome(seed: int, G: int = 64_000_000) -> np.ndarray:
