@@ -43,6 +43,7 @@ UNIT = "Msuffix/s"
 SAMPLE_CPU = 16_000_000   # oracle sample for cpu_baseline (~10-20 s single-threaded)
 SAMPLE_REF = 4_000_000    # oracle sample per --impl reference step (~3 s)
 G = 64_000_000
+TUNE_CACHE = os.path.join(ROOT, "paper_1404_3456_gb300", "_build", "tune_cache.tsv")
 
 
 def parse():
@@ -55,13 +56,14 @@ def parse():
     ap.add_argument("--genome", type=int, default=G, help="genome length (default 64,000,000)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="sa64m", choices=["sa64m", "batched", "served"])
+    ap.add_argument("--workload", default="sa64m", choices=["sa64m", "large", "batched", "served"])
     ap.add_argument("--instances", type=int, default=4096, help="batched: fragment sets per batch")
     ap.add_argument("--solo-sample", type=int, default=256,
                     help="batched: instances timed one job per launch")
     ap.add_argument("--jobs", type=int, default=48, help="served: distinct jobs in the trace")
     ap.add_argument("--lambdas", default="0.5,0.9,1.25",
                     help="served: arrival rates as multiples of one-job-per-launch capacity")
+    ap.add_argument("--no-tune", action="store_true", help="skip the build-option autotuner")
     ap.add_argument("--slots", type=int, default=2)
     ap.add_argument("--max-batch", type=int, default=16)
     return ap.parse_args()
@@ -224,9 +226,16 @@ def run_batched(args):
     off = torch.empty(N // 2 + 2, dtype=torch.int64, device="cuda")
     ioff = torch.empty(len(texts) + 1, dtype=torch.int64, device="cuda")
     stream = torch.cuda.current_stream()
+    opts, tuned = None, None
+    if not args.no_tune:
+        packed, toff, nr = binding.pack_text(ctx, d_text)
+        opts, tms = binding.dnasa_autotune(ctx, packed, toff, nr, N, inst_off, cache_path=TUNE_CACHE)
+        tuned = {"tile_items": opts.tile_items, "finish_threshold": opts.finish_threshold,
+                 "lookback": opts.lookback, "sa_ms": tms}
+        del packed, toff
 
     def step(t=d_text):
-        return binding.assemble_batched(ctx, t, inst_off, 31, contigs, off, ioff)
+        return binding.assemble_batched(ctx, t, inst_off, 31, contigs, off, ioff, opts)
 
     for _ in range(args.warmup):
         step()
@@ -269,10 +278,16 @@ def run_batched(args):
     solo_s = time.perf_counter() - t0
     sub_off = inst_off[: M + 1]
     d_sub = d_text[: int(sub_off[-1])]
-    binding.assemble_batched(ctx, d_sub, sub_off, 31, contigs, off, ioff[: M + 1])
+    sub_opts = None
+    if not args.no_tune:   # the switch point depends on N: tune the subset on its own
+        packed, toff, nr = binding.pack_text(ctx, d_sub)
+        sub_opts, _ = binding.dnasa_autotune(ctx, packed, toff, nr, int(sub_off[-1]), sub_off,
+                                             cache_path=TUNE_CACHE)
+        del packed, toff
+    binding.assemble_batched(ctx, d_sub, sub_off, 31, contigs, off, ioff[: M + 1], sub_opts)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    binding.assemble_batched(ctx, d_sub, sub_off, 31, contigs, off, ioff[: M + 1])
+    binding.assemble_batched(ctx, d_sub, sub_off, 31, contigs, off, ioff[: M + 1], sub_opts)
     torch.cuda.synchronize()
     sub_s = time.perf_counter() - t0
     cpu = None
@@ -297,7 +312,8 @@ def run_batched(args):
                                "2-200 kbp, reads U{100..1000} at 8x, min overlap 31",
                    "msuffix_per_s": N * world / (ms / 1000.0) / 1e6,
                    "one_job_per_launch": {"instances": M, "s": solo_s, "assemblies_per_s": M / solo_s},
-                   "batched_same_instances": {"instances": M, "s": sub_s, "assemblies_per_s": M / sub_s}},
+                   "batched_same_instances": {"instances": M, "s": sub_s, "assemblies_per_s": M / sub_s},
+                   "autotuned": tuned},
         "roofline": roof, "cpu_baseline": cpu,
         "e2e": {"value": len(texts) / (e2e_ms / 1000.0), "unit": "assemblies/s",
                 "h2d_bytes_per_step": N, "d2h_bytes_per_step": int(nb) + 8 * (int(nc) + 1),
@@ -418,18 +434,31 @@ def main():
     from paper_1404_3456_gb300 import binding
 
     dev = torch.device("cuda", local_rank)
-    text_np = genome_text(args.seed, args.genome)
+    large = args.workload == "large"
+    if large:   # 1.5 Gbp, int64 SA (85 % i.i.d., 10 % tandem, 5 % copies of a 6 kbp element)
+        from paper_1404_3456_gb300 import synth
+
+        text_np = synth.genome_text(synth.large_genome(args.seed))
+        args.no_e2e = True
+    else:
+        text_np = genome_text(args.seed, args.genome)
     N = int(text_np.size)
+    idx_dtype = torch.int64 if large else torch.int32
     ctx = binding.Context(local_rank)
     stream = torch.cuda.current_stream()
     text = torch.from_numpy(text_np).to(dev)
     packed, toff, nr = binding.pack_text(ctx, text)
     del text
-    sa = torch.empty(N, dtype=torch.int32, device=dev)
+    sa = torch.empty(N, dtype=idx_dtype, device=dev)
     lcp = torch.empty(N, dtype=torch.int32, device=dev)
+    opts, tuned = None, None
+    if not args.no_tune:
+        opts, tms = binding.dnasa_autotune(ctx, packed, toff, nr, N, cache_path=TUNE_CACHE)
+        tuned = {"tile_items": opts.tile_items, "finish_threshold": opts.finish_threshold,
+                 "lookback": opts.lookback, "sa_ms": tms}
 
     def step():
-        binding.sa_build(ctx, packed, toff, nr, N, sa)
+        binding.sa_build(ctx, packed, toff, nr, N, sa, opts)
         binding.lcp_build(ctx, packed, toff, nr, N, sa, lcp)
 
     for _ in range(args.warmup):
@@ -468,7 +497,7 @@ def main():
     s0 = torch.cuda.Event(enable_timing=True)
     s1 = torch.cuda.Event(enable_timing=True)
     s0.record(stream)
-    binding.sa_build(ctx, packed, toff, nr, N, sa)
+    binding.sa_build(ctx, packed, toff, nr, N, sa, opts)
     s1.record(stream)
     torch.cuda.synchronize()
     sa_only_ms = s0.elapsed_time(s1)
@@ -486,7 +515,7 @@ def main():
         def e2e_step():
             d_packed.copy_(h_packed, non_blocking=True)
             d_toff.copy_(h_toff, non_blocking=True)
-            binding.sa_build(ctx, d_packed, d_toff, nr, N, sa)
+            binding.sa_build(ctx, d_packed, d_toff, nr, N, sa, opts)
             binding.lcp_build(ctx, d_packed, d_toff, nr, N, sa, lcp)
             h_sa.copy_(sa, non_blocking=True)
             h_lcp.copy_(lcp, non_blocking=True)
@@ -547,7 +576,12 @@ def main():
                  for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])}
     cpu = None
     if not args.no_cpu_baseline:
-        sample = genome_text(args.seed, SAMPLE_CPU)
+        if large:
+            from paper_1404_3456_gb300 import synth
+
+            sample = synth.genome_text(text_np[:SAMPLE_CPU].copy())
+        else:
+            sample = genome_text(args.seed, SAMPLE_CPU)
         rate, dt = cpu_oracle_rate(sample)
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"oracle SA + Kasai LCP of the first {SAMPLE_CPU:,} bp of the same "
@@ -556,12 +590,15 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u8/int32", "data": "synthetic",
-        "config": {"workload": f"sa64m: sa_build + lcp_build of a {args.genome:,} bp genome "
-                               f"(N = {N:,} suffixes), int32 SA and LCP",
-                   "genome_bp": args.genome, "seed": args.seed, "parallelism": f"replicas{world}",
+        "config": {"workload": (f"large: sa_build + lcp_build of a {N - 1:,} bp genome, int64 SA, "
+                                "int32 LCP" if large else
+                                f"sa64m: sa_build + lcp_build of a {args.genome:,} bp genome "
+                                f"(N = {N:,} suffixes), int32 SA and LCP"),
+                   "genome_bp": N - 1, "seed": args.seed, "parallelism": f"replicas{world}",
                    "l2": "working set >> L2 (no flush needed)",
                    "rounds": trace["rounds"], "finished_direct": trace["finished_direct"],
-                   "active_per_round": trace["active"], "sa_only_ms": sa_only_ms},
+                   "active_per_round": trace["active"], "sa_only_ms": sa_only_ms,
+                   "autotuned": tuned},
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": ({"value": N * world / (e2e["ms"] / 1000.0) / 1e6, "unit": UNIT,

@@ -153,6 +153,13 @@ uint64_t dnasa_launch_count(dnasa_ctx *ctx);
 int dnasa_sort_pairs(dnasa_ctx *ctx, uint64_t *keys, uint32_t *vals, int64_t n, int key_bits,
                      int tile_items, int lookback, void *stream);
 
+/* Failure-path self-test (no counterpart in the paper): runs one digit pass in
+ * which the only tile waits on a predecessor that never publishes its counts.
+ * The wait is bounded; the pass writes nothing and the call returns
+ * DNASA_DEVICE_TIMEOUT, after which the context works normally.  Hangs and
+ * faults nothing.  Synchronizes the stream. */
+int dnasa_selftest_timeout(dnasa_ctx *ctx, void *stream);
+
 /* ---- allocation-free radix sort ------------------------------------------------ */
 
 /* Largest n dnasa_sort_pairs_noalloc accepts. */
@@ -205,7 +212,9 @@ int sa_build(dnasa_ctx *ctx, const uint64_t *packed, const int64_t *toff, int64_
 
 /* lcp[0] = 0; lcp[j] = number of equal bases at the start of suffixes sa[j-1]
  * and sa[j], stopping at the first '$' of either (a '$' never matches).
- *   lcp  device, N int32.  Enqueues only (no synchronization). */
+ *   lcp  device, N int32.  Synchronizes the stream once (to size the pass over
+ *   pairs longer than 64 bases, which walks runs of consecutive text positions
+ *   and starts each comparison from the previous LCP minus one, after Kasai). */
 int lcp_build(dnasa_ctx *ctx, const uint64_t *packed, const int64_t *toff, int64_t n_reads,
               int64_t N, const void *sa, int idx_width, int32_t *lcp, void *stream);
 
@@ -269,6 +278,19 @@ int assemble_batched(dnasa_ctx *ctx, const uint8_t *texts, const int64_t *inst_o
                      int32_t min_overlap, const dnasa_opts *opts, uint8_t *contigs, int64_t cap,
                      int64_t *contig_off, int64_t off_cap, int64_t *inst_contig_off,
                      int64_t *n_contigs, int64_t *needed, void *stream);
+
+/* Autotuner of the build options: times sa_build (batched when n_inst > 1) on
+ * this text for every tile size (2048, 3840, 5120) and doubling-to-direct
+ * switch (never, N/64, N/8, as soon as every group fits the finisher), and
+ * writes the fastest to *best (host) and its time to *best_ms (host, may be
+ * NULL).  The radix digit is 8 bits: the only width the kernels implement.
+ * With cache_path (may be NULL), a line "key<TAB>tile<TAB>switch<TAB>lookback
+ * <TAB>ms" keyed by GPU name, bits of N and bits of n_inst is looked up first
+ * and appended after tuning.  inst_off as for sa_build_batched (host).
+ * Synchronizes the stream. */
+int dnasa_autotune(dnasa_ctx *ctx, const uint64_t *packed, const int64_t *toff, int64_t n_reads,
+                   int64_t N, const int64_t *inst_off, int32_t n_inst, const char *cache_path,
+                   dnasa_opts *best, double *best_ms, void *stream);
 
 /* ---- S12: served -- continuous batching of arriving assembly jobs ------------ */
 

@@ -73,6 +73,8 @@ def _load():
             lib.oracle_lcp_direct.restype = ctypes.c_int
             lib.oracle_sa_check.argtypes = [P, I64, P]
             lib.oracle_sa_check.restype = I64
+            lib.oracle_check_pairs.argtypes = [P, I64, P, P, P, I64]
+            lib.oracle_check_pairs.restype = I64
             lib.oracle_split_sort_u64.argtypes = [P, P, I64, ctypes.c_int, ctypes.c_int]
             lib.oracle_split_sort_u64.restype = ctypes.c_int
             for name in ("oracle_overlaps_brute", "oracle_overlaps_sorted"):
@@ -143,6 +145,22 @@ def sa_check(text, sa) -> int:
     if sa.size != t.size:
         return 1
     return int(_load().oracle_sa_check(_ptr(t), t.size, _ptr(sa)))
+
+
+def check_pairs(text, sa, lcp, idx) -> int:
+    """Violations among the sampled SA neighbours (j-1, j), j in idx: order, and
+    LCP when lcp is not None.  For arrays too large to check in full."""
+    t = _text(text)
+    sa = np.ascontiguousarray(sa, dtype=np.int64)
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    lp = None
+    if lcp is not None:
+        lcp = np.ascontiguousarray(lcp, dtype=np.int32)
+        lp = _ptr(lcp)
+    n = _load().oracle_check_pairs(_ptr(t), t.size, _ptr(sa), lp, _ptr(idx), idx.size)
+    if n < 0:
+        raise RuntimeError("oracle_check_pairs: bad arguments")
+    return int(n)
 
 
 def split_sort(keys, vals, lo_bit: int, hi_bit: int):

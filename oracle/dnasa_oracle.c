@@ -24,6 +24,7 @@
  *   oracle_lcp_kasai        LCP of adjacent SA entries, Kasai et al. 2001
  *   oracle_lcp_direct       the same, measured pair by pair (a pin for Kasai)
  *   oracle_sa_check         Burkhardt & Kaerkkaeinen (CPM 2003) linear SA checker
+ *   oracle_check_pairs      sampled SA neighbours (order and LCP) checked one by one
  *   oracle_split_sort_u64   Sec. IV / Algorithm 1: LSD radix sort made of 1-bit
  *                           stable "split" passes (flag, exclusive scan, scatter)
  *   oracle_overlaps_brute   Sec. III "fir" relation generalised to suffix-prefix
@@ -163,6 +164,25 @@ int64_t oracle_sa_check(const uint8_t *T, int64_t N, const int64_t *sa)
         else if (!(isa[p + 1] < isa[q + 1])) bad = 2 + j;
     }
     free(isa);
+    return bad;
+}
+
+/* Checks sampled neighbours of a (possibly huge) suffix array one by one: for
+ * each j in idx[0..m), suffix sa[j-1] must be smaller than suffix sa[j] and, if
+ * lcp is non-NULL, lcp[j] must be their common prefix.  Returns the number of
+ * violations (0 = all sampled pairs correct). */
+int64_t oracle_check_pairs(const uint8_t *T, int64_t N, const int64_t *sa, const int32_t *lcp,
+                           const int64_t *idx, int64_t m)
+{
+    if (!text_ok(T, N) || !sa || !idx || m < 0) return -1;
+    int64_t bad = 0;
+    for (int64_t i = 0; i < m; ++i) {
+        int64_t j = idx[i];
+        if (j < 1 || j >= N) { ++bad; continue; }
+        int64_t p = sa[j - 1], q = sa[j];
+        if (p < 0 || p >= N || q < 0 || q >= N || suffix_cmp(T, p, q) >= 0) { ++bad; continue; }
+        if (lcp && lcp[j] != (int32_t)common_prefix(T, p, q)) ++bad;
+    }
     return bad;
 }
 

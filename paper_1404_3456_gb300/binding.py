@@ -79,6 +79,7 @@ _SIGS = {
     "dnasa_profile_read": (_INT, [_P, ctypes.POINTER(ProfEntry), _INT, ctypes.POINTER(_INT)]),
     "dnasa_launch_count": (ctypes.c_uint64, [_P]),
     "dnasa_sort_pairs": (_INT, [_P, _P, _P, _I64, _INT, _INT, _INT, _P]),
+    "dnasa_selftest_timeout": (_INT, [_P, _P]),
     "dnasa_sort_pairs_noalloc": (_INT, [_P, _P, _I64, _INT, _P]),
     "dnasa_pack": (_INT, [_P, _P, _I64, _P, _P, _I64, ctypes.POINTER(_I64), _P]),
     "sa_build": (_INT, [_P, _P, _P, _I64, _I64, _P, _INT, ctypes.POINTER(Opts), _P]),
@@ -87,6 +88,8 @@ _SIGS = {
                               ctypes.POINTER(_I64), _P, _P]),
     "assemble": (_INT, [_P, _P, _I64, _I32, _P, _I64, _P, _I64, ctypes.POINTER(_I64),
                         ctypes.POINTER(_I64), _P]),
+    "dnasa_autotune": (_INT, [_P, _P, _P, _I64, _I64, _P, _I32, ctypes.c_char_p, ctypes.POINTER(Opts),
+                              ctypes.POINTER(ctypes.c_double), _P]),
     "dnasa_server_create": (_INT, [_INT, ctypes.c_size_t, _I32, _I32, ctypes.POINTER(_P)]),
     "dnasa_server_submit": (_INT, [_P, ctypes.POINTER(Job), ctypes.c_uint64]),
     "dnasa_server_poll": (_INT, [_P, ctypes.POINTER(Result), _I32, _I32, ctypes.POINTER(_I32)]),
@@ -203,6 +206,11 @@ def dnasa_sort_pairs(ctx: Context, keys, vals=None, key_bits: int = 64, tile_ite
     """Stable radix sort in place: keys int64 (bit pattern of uint64), vals int32/uint32."""
     ctx.check(lib().dnasa_sort_pairs(ctx.handle, _ptr(keys), _ptr(vals) if vals is not None else None,
                                      keys.numel(), key_bits, tile_items, lookback, _stream(stream)))
+
+
+def dnasa_selftest_timeout(ctx: Context, stream=None) -> int:
+    """Returns the status of the bounded-wait self-test (DEVICE_TIMEOUT expected)."""
+    return int(lib().dnasa_selftest_timeout(ctx.handle, _stream(stream)))
 
 
 NOALLOC_MAX_ITEMS = 1 << 20   # DNASA_NOALLOC_MAX_ITEMS in dnasa.h
@@ -394,4 +402,20 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def dnasa_autotune(ctx: Context, packed, toff, n_reads: int, N: int, inst_off=None,
+                   cache_path: str | None = None, stream=None):
+    """Fastest build options for this text (and instance split); returns (Opts, ms)."""
+    best = Opts()
+    ms = ctypes.c_double(0.0)
+    if inst_off is None:
+        arr, p, n_inst = None, None, 1
+    else:
+        arr, p = _host_i64(inst_off)
+        n_inst = arr.size - 1
+    ctx.check(lib().dnasa_autotune(ctx.handle, _ptr(packed), _ptr(toff), n_reads, N, p, n_inst,
+                                   cache_path.encode() if cache_path else None, ctypes.byref(best),
+                                   ctypes.byref(ms), _stream(stream)))
+    return best, ms.value
 

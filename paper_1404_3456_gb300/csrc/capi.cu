@@ -4,6 +4,9 @@
 // stream-ordered allocator; each step's scratch comes from the context
 // workspace.
 #include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <string>
 
 #include "common.cuh"
 
@@ -324,4 +327,97 @@ int assemble_batched(dnasa_ctx *ctx, const uint8_t *texts, const int64_t *inst_o
                          off_cap, inst_contig_off, n_contigs, needed, opts, (cudaStream_t)stream);
 }
 
+int dnasa_autotune(dnasa_ctx *ctx, const uint64_t *packed, const int64_t *toff, int64_t n_reads,
+                   int64_t N, const int64_t *inst_off, int32_t n_inst, const char *cache_path,
+                   dnasa_opts *best, double *best_ms, void *stream) {
+    if (!ctx || !best) return DNASA_INVALID_ARG;
+    ctx->last_error.clear();
+    DNASA_TRY(check_text_args(ctx, packed, toff, n_reads, N, "dnasa_autotune"));
+    if (n_inst < 1 || (n_inst > 1 && !inst_off))
+        return fail(ctx, DNASA_INVALID_ARG, "dnasa_autotune: n_inst >= 1 (and inst_off when > 1)");
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaDeviceProp prop;
+    DNASA_CUDA(ctx, cudaGetDeviceProperties(&prop, ctx->device));
+    char key[320];
+    snprintf(key, sizeof key, "%s|n%d|i%d", prop.name, bits_for((uint64_t)N),
+             bits_for((uint64_t)n_inst));
+    if (cache_path) {   // one line per key: key \t tile \t finish \t lookback \t ms
+        FILE *f = fopen(cache_path, "r");
+        if (f) {
+            char line[512];
+            while (fgets(line, sizeof line, f)) {
+                char *tab = strchr(line, '\t');
+                if (!tab || (size_t)(tab - line) != strlen(key) || strncmp(line, key, strlen(key))) continue;
+                int tile, lb;
+                long long fin;
+                double ms;
+                if (sscanf(tab + 1, "%d\t%lld\t%d\t%lf", &tile, &fin, &lb, &ms) == 4) {
+                    *best = dnasa_opts{};
+                    best->tile_items = tile;
+                    best->finish_threshold = fin;
+                    best->lookback = lb;
+                    if (best_ms) *best_ms = ms;
+                    fclose(f);
+                    return DNASA_OK;
+                }
+            }
+            fclose(f);
+        }
+    }
+    TextDesc t = one_instance(packed, toff, n_reads, N);
+    DevBuf inst_toff, inst_roff, sa;
+    if (n_inst > 1) {
+        int64_t max_reads;
+        DNASA_TRY(make_instances(ctx, toff, n_reads, N, inst_off, n_inst, inst_toff, inst_roff, &max_reads, s));
+        t.inst_toff = (const int64_t *)inst_toff.p;
+        t.inst_roff = (const int64_t *)inst_roff.p;
+        t.n_inst = n_inst;
+    }
+    DNASA_TRY(dev_alloc(ctx, sa, (size_t)N * 4, s));
+    cudaEvent_t e0, e1;
+    DNASA_CUDA(ctx, cudaEventCreate(&e0));
+    DNASA_CUDA(ctx, cudaEventCreate(&e1));
+    dnasa_opts warm{};
+    int rc = sa_build_u32(ctx, t, (uint32_t *)sa.p, &warm, s);   // also sizes the workspace
+    double bms = 1e30;
+    dnasa_opts bopt{};
+    const int tiles[3] = {2048, 3840, 5120};
+    const int64_t fins[4] = {-1, std::max<int64_t>(N / 64, 1), std::max<int64_t>(N / 8, 1), N};
+    for (int ti = 0; ti < 3 && rc == DNASA_OK; ++ti) {
+        for (int fi = 0; fi < 4 && rc == DNASA_OK; ++fi) {
+            dnasa_opts o{};
+            o.tile_items = tiles[ti];
+            o.finish_threshold = fins[fi];
+            o.lookback = 8;
+            cudaEventRecord(e0, s);
+            rc = sa_build_u32(ctx, t, (uint32_t *)sa.p, &o, s);
+            cudaEventRecord(e1, s);
+            if (rc != DNASA_OK) break;
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < bms) {
+                bms = ms;
+                bopt = o;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    DNASA_TRY(rc);
+    *best = bopt;
+    if (best_ms) *best_ms = bms;
+    if (cache_path) {
+        FILE *f = fopen(cache_path, "a");
+        if (f) {
+            fprintf(f, "%s\t%d\t%lld\t%d\t%.4f\n", key, bopt.tile_items,
+                    (long long)bopt.finish_threshold, bopt.lookback, bms);
+            fclose(f);
+        }
+    }
+    return DNASA_OK;
+}
+
 }  // extern "C"
+

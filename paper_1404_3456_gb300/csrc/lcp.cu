@@ -43,7 +43,8 @@ __device__ __forceinline__ PairInfo pair_info(const TextDesc &t, const uint32_t 
 // One thread per adjacent pair: the first 64 bases.  Pairs still equal there
 // (repeats) are queued for k_lcp_long.
 __global__ void __launch_bounds__(256) k_lcp(TextDesc t, const uint32_t *__restrict__ sa,
-                                             int32_t *__restrict__ lcp, uint32_t *__restrict__ longq,
+                                             int32_t *__restrict__ lcp, uint32_t *__restrict__ qpos,
+                                             uint32_t *__restrict__ qj,
                                              unsigned long long *__restrict__ nlong) {
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -73,37 +74,54 @@ __global__ void __launch_bounds__(256) k_lcp(TextDesc t, const uint32_t *__restr
             unsigned long long qb = 0;
             if (lane == 0) qb = atomicAdd(nlong, (unsigned long long)__popc(qm));
             qb = __shfl_sync(0xffffffffu, qb, 0);
-            if (queue) longq[qb + __popc(qm & lanemask_lt())] = (uint32_t)j;
+            if (queue) {
+                unsigned long long at = qb + __popc(qm & lanemask_lt());
+                qpos[at] = sa[j];
+                qj[at] = (uint32_t)j;
+            }
         }
     }
 }
 
-// One thread per queued pair (the LCP is over 64 bases: repeats): four words
-// (128 bases) per round trip, their eight loads issued together.
-__global__ void __launch_bounds__(256) k_lcp_long(TextDesc t, const uint32_t *__restrict__ sa,
-                                                  int32_t *__restrict__ lcp,
-                                                  const uint32_t *__restrict__ longq,
-                                                  const unsigned long long *__restrict__ nlong) {
-    const int64_t nq = (int64_t)*nlong;
-    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nq;
-         w += (int64_t)gridDim.x * blockDim.x) {
-        int64_t j = longq[w];
-        PairInfo pi = pair_info(t, sa, j);
-        int64_t res = pi.m;
-        for (int64_t h = kShortBases; h < pi.m; h += 4 * 32) {
-            uint64_t d[4];
+// The queued pairs (LCP over 64 bases: repeats), sorted by the text position p
+// of their lower suffix.  Kasai's bound: the LCP of suffix p+1 with its SA
+// predecessor is at least that of p minus one, so along a run of consecutive
+// positions each comparison starts where the previous one ended instead of at
+// base 64.  One thread walks kChain consecutive entries, four words (128 bases)
+// per round trip.
+constexpr int kChain = 128;
+
+__global__ void __launch_bounds__(256) k_lcp_chain(TextDesc t, const uint32_t *__restrict__ sa,
+                                                   int32_t *__restrict__ lcp,
+                                                   const uint32_t *__restrict__ qpos,
+                                                   const uint32_t *__restrict__ qj, int64_t nq) {
+    const int64_t chunks = (nq + kChain - 1) / kChain;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < chunks;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        int64_t prev_p = -2, prev_h = 0;
+        const int64_t e1 = min((c + 1) * kChain, nq);
+        for (int64_t e = c * kChain; e < e1; ++e) {
+            const int64_t p = qpos[e], j = qj[e];
+            PairInfo pi = pair_info(t, sa, j);
+            int64_t h = (p == prev_p + 1 && prev_h - 1 > kShortBases) ? prev_h - 1 : kShortBases;
+            int64_t res = pi.m;
+            for (; h < pi.m; h += 4 * 32) {
+                uint64_t d[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                int64_t o = h + 32 * u;   // past the shorter suffix's end: a "mismatch" at o
-                d[u] = o < pi.m ? bases32(t.packed, pi.bp + o) ^ bases32(t.packed, pi.bq + o) : ~0ull;
+                for (int u = 0; u < 4; ++u) {
+                    int64_t o = h + 32 * u;   // past the shorter suffix's end: a "mismatch" at o
+                    d[u] = o < pi.m ? bases32(t.packed, pi.bp + o) ^ bases32(t.packed, pi.bq + o) : ~0ull;
+                }
+                int64_t at = -1;
+#pragma unroll
+                for (int u = 3; u >= 0; --u)
+                    if (d[u]) at = h + 32 * u + (__clzll((long long)d[u]) >> 1);
+                if (at >= 0) { res = min(at, pi.m); break; }
             }
-            int64_t at = -1;
-#pragma unroll
-            for (int u = 3; u >= 0; --u)
-                if (d[u]) at = h + 32 * u + (__clzll((long long)d[u]) >> 1);
-            if (at >= 0) { res = min(at, pi.m); break; }
+            lcp[j] = (int32_t)res;
+            prev_p = p;
+            prev_h = res;
         }
-        lcp[j] = (int32_t)res;
     }
 }
 
@@ -111,19 +129,34 @@ __global__ void __launch_bounds__(256) k_lcp_long(TextDesc t, const uint32_t *__
 
 int lcp_build_impl(dnasa_ctx *ctx, const TextDesc &t, const uint32_t *sa32, int32_t *lcp,
                    cudaStream_t s) {
-    DNASA_TRY(ws_reserve(ctx, ((size_t)t.N * 4 + 255) / 256 * 256 + 4096, s));
+    const int tile = radix_tile_default();
+    const int key_bits = bits_for((uint64_t)(t.N - 1));
+    const size_t q = ((size_t)t.N * 4 + 255) / 256 * 256;
+    DNASA_TRY(ws_reserve(ctx, 4 * q + radix_scratch_bytes(t.N, key_bits, tile) + 8192, s));
     Arena a = ws_arena(ctx);
-    uint32_t *longq = a.take<uint32_t>((size_t)t.N);
+    uint32_t *qk[2] = {a.take<uint32_t>((size_t)t.N), a.take<uint32_t>((size_t)t.N)};
+    uint32_t *qv[2] = {a.take<uint32_t>((size_t)t.N), a.take<uint32_t>((size_t)t.N)};
+    RadixScratch rs = radix_scratch_take(a, t.N, key_bits, tile);
+    if (!rs.hist) return fail(ctx, DNASA_OOM, "lcp_build workspace");
     unsigned long long *nlong = ctx->ctrl->count + CNT_TMP;
     DNASA_CUDA(ctx, cudaMemsetAsync(nlong, 0, 8, s));
     int grid = (int)std::min<int64_t>(ceil_div(t.N, 256), (int64_t)ctx->num_sms * 16);
     {
         LaunchScope ls_(ctx, PK_LCP, s, 8.5 * t.N);
-        k_lcp<<<std::max(grid, 1), 256, 0, s>>>(t, sa32, lcp, longq, nlong);
+        k_lcp<<<std::max(grid, 1), 256, 0, s>>>(t, sa32, lcp, qk[0], qv[0], nlong);
     }
+    DNASA_CUDA(ctx, cudaGetLastError());
+    DNASA_CUDA(ctx, cudaMemcpyAsync(ctx->pinned, nlong, 8, cudaMemcpyDeviceToHost, s));
+    DNASA_TRY(check_device_status(ctx, s, "lcp_build"));
+    const int64_t nq = (int64_t)ctx->pinned[0];
+    if (nq == 0) return DNASA_OK;
+    int which = 0;
+    DNASA_TRY(radix_sort_pairs<uint32_t>(ctx, rs, qk, qv, nq, nullptr, key_bits, false, tile, &which, s));
     {
-        LaunchScope ls_(ctx, PK_LCP, s, 0.0);
-        k_lcp_long<<<ctx->num_sms * 16, 256, 0, s>>>(t, sa32, lcp, longq, nlong);
+        LaunchScope ls_(ctx, PK_LCP, s, 16.0 * nq);
+        int g2 = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(ceil_div(nq, kChain), 128),
+                                                           (int64_t)ctx->num_sms * 32));
+        k_lcp_chain<<<g2, 128, 0, s>>>(t, sa32, lcp, qk[which], qv[which], nq);
     }
     DNASA_CUDA(ctx, cudaGetLastError());
     return DNASA_OK;

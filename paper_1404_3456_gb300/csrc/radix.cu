@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(kThreads) k_onesweep(
     const K *__restrict__ kin, const uint32_t *__restrict__ vin, K *__restrict__ kout,
     uint32_t *__restrict__ vout, const uint32_t *__restrict__ bucket, unsigned long long *status,
     uint32_t *tile_ctr, int64_t n_host, const unsigned long long *__restrict__ d_n, int shift,
-    uint32_t epoch, uint32_t *err) {
+    uint32_t epoch, uint32_t *err, uint32_t spin_limit) {
     constexpr int TILE = kThreads * ITEMS;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     K *s_keys = reinterpret_cast<K *>(smem_raw);
@@ -278,7 +278,7 @@ __global__ void __launch_bounds__(kThreads) k_onesweep(
                 if (done) break;
                 if (k == LBW) { t -= LBW; continue; }
                 t -= k;                                            // wait on tile t
-                if (++spins > kSpinLimit || ((spins & 1023) == 0 && ld_relaxed_u32(err) != 0)) {
+                if (++spins > spin_limit || ((spins & 1023) == 0 && ld_relaxed_u32(err) != 0)) {
                     gave_up = true;
                     break;
                 }
@@ -318,7 +318,7 @@ template <typename K, int ITEMS, bool HAS_VALS, int LBW>
 cudaError_t launch_pass(int tiles, cudaStream_t s, const K *kin, const uint32_t *vin, K *kout,
                         uint32_t *vout, const uint32_t *bucket, unsigned long long *status,
                         uint32_t *tile_ctr, int64_t n_host, const unsigned long long *d_n,
-                        int shift, uint32_t epoch, uint32_t *err) {
+                        int shift, uint32_t epoch, uint32_t *err, uint32_t spin_limit = kSpinLimit) {
     size_t smem = onesweep_smem<K, ITEMS, HAS_VALS>();
     auto kern = k_onesweep<K, ITEMS, HAS_VALS, LBW>;
     // once per instantiation (thread-safe static initialisation)
@@ -326,7 +326,7 @@ cudaError_t launch_pass(int tiles, cudaStream_t s, const K *kin, const uint32_t 
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (configured != cudaSuccess) return configured;
     kern<<<tiles, kThreads, smem, s>>>(kin, vin, kout, vout, bucket, status, tile_ctr, n_host,
-                                       d_n, shift, epoch, err);
+                                       d_n, shift, epoch, err, spin_limit);
     return cudaGetLastError();
 }
 
@@ -500,6 +500,38 @@ extern "C" int dnasa_sort_pairs(dnasa_ctx *ctx, uint64_t *keys, uint32_t *vals, 
             DNASA_CUDA(ctx, cudaMemcpyAsync(vals, valt, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
     }
     return DNASA_OK;
+}
+
+// Failure-path self-test: a pass whose only CTA takes tile 1 and looks back at a
+// tile 0 that nothing ever publishes.  Its bounded spin gives up, it records
+// DERR_TIMEOUT, writes nothing, and the call reports DNASA_DEVICE_TIMEOUT; the
+// context stays usable.  Nothing hangs: the bound is a few thousand probes.
+extern "C" int dnasa_selftest_timeout(dnasa_ctx *ctx, void *stream) {
+    if (!ctx) return DNASA_INVALID_ARG;
+    ctx->last_error.clear();
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    constexpr int kItems = 15, kTile = kThreads * kItems;
+    const int64_t n = 2 * kTile;
+    DNASA_TRY(ws_reserve(ctx, (size_t)n * 24 + 8 * kRadix + 4096, s));
+    Arena a = ws_arena(ctx);
+    unsigned long long *k0 = a.take<unsigned long long>((size_t)n), *k1 = a.take<unsigned long long>((size_t)n);
+    uint32_t *v0 = a.take<uint32_t>((size_t)n), *v1 = a.take<uint32_t>((size_t)n);
+    uint32_t *bucket = a.take<uint32_t>(kRadix);
+    if (!bucket) return fail(ctx, DNASA_OOM, "selftest workspace");
+    DNASA_CUDA(ctx, cudaMemsetAsync(k0, 0, (size_t)n * 8, s));
+    DNASA_CUDA(ctx, cudaMemsetAsync(v0, 0, (size_t)n * 4, s));
+    DNASA_CUDA(ctx, cudaMemsetAsync(bucket, 0, kRadix * 4, s));
+    unsigned long long *status;
+    uint32_t epoch;
+    DNASA_TRY(lb_prepare(ctx, (size_t)2 * kRadix, s, &status, &epoch));
+    const uint32_t one = 1;   // the only CTA will draw tile 1: tile 0 never runs
+    DNASA_CUDA(ctx, cudaMemcpyAsync(ctx->ctrl->tile_ctr, &one, 4, cudaMemcpyHostToDevice, s));
+    cudaError_t e = launch_pass<unsigned long long, kItems, true, 8>(
+        1, s, k0, v0, k1, v1, bucket, status, ctx->ctrl->tile_ctr, n, nullptr, 0, epoch,
+        &ctx->ctrl->err, 4096u);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "selftest pass");
+    return check_device_status(ctx, s, "dnasa_selftest_timeout");
 }
 
 // ------------------------------------------------------------------ allocation-free sort

@@ -75,3 +75,21 @@ def test_batched_rejects_bad_offsets(ctx):
     with pytest.raises(B().DnasaError) as e:   # 3 is not a fragment start
         B().assemble_batched(ctx, joined, [0, 3, 9], 2, contigs, off)
     assert e.value.status == B().INVALID_ARG
+
+
+def test_autotune_picks_valid_options(ctx, tmp_path):
+    texts = small_batch(3, 12)
+    inst_off = np.concatenate([[0], np.cumsum([t.size for t in texts])]).astype(np.int64)
+    joined = torch.from_numpy(np.concatenate(texts)).cuda()
+    packed, toff, nr = B().pack_text(ctx, joined)
+    cache = str(tmp_path / "tune.tsv")
+    opts, ms = B().dnasa_autotune(ctx, packed, toff, nr, int(inst_off[-1]), inst_off, cache_path=cache)
+    assert opts.tile_items in (2048, 3840, 5120) and ms > 0
+    again, ms2 = B().dnasa_autotune(ctx, packed, toff, nr, int(inst_off[-1]), inst_off, cache_path=cache)
+    assert (again.tile_items, again.finish_threshold) == (opts.tile_items, opts.finish_threshold)
+    sa = torch.empty(int(inst_off[-1]), dtype=torch.int32, device="cuda")
+    B().sa_build_batched(ctx, packed, toff, nr, int(inst_off[-1]), inst_off, sa, opts)
+    got = sa.cpu().numpy()
+    for i in (0, 5, 11):
+        t = texts[i]
+        assert np.array_equal(got[inst_off[i]: inst_off[i + 1]].astype(np.int64), oracle.suffix_array(t))

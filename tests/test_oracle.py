@@ -169,6 +169,23 @@ def test_checker_rejects_perturbations():
     assert oracle.sa_check(text, np.roll(sa, 1)) != 0
 
 
+def test_check_pairs_finds_planted_errors():
+    """The sampled checker accepts the true SA and LCP and flags a planted swap
+    and a planted LCP error (mistakes planted in oracle data, on the CPU)."""
+    rng = np.random.default_rng(5)
+    text, _ = random_reads_text(rng, 10, 5, 80, periodic=True)
+    sa = oracle.suffix_array(text)
+    lcp = oracle.lcp_kasai(text, sa)
+    idx = np.arange(1, len(sa))
+    assert oracle.check_pairs(text, sa, lcp, idx) == 0
+    bad = sa.copy()
+    bad[10], bad[11] = bad[11], bad[10]
+    assert oracle.check_pairs(text, bad, None, idx) >= 1
+    badl = lcp.copy()
+    badl[7] += 1
+    assert oracle.check_pairs(text, sa, badl, idx) == 1
+
+
 # ---------------------------------------------------------------- Algorithm 1
 
 
