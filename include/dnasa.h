@@ -72,6 +72,9 @@ typedef struct {
     int32_t max_rounds;        /* safety bound on doubling rounds (default 63) */
     int32_t lookback;          /* look-back loads in flight per digit in a onesweep pass:
                                   8 (default) or 1 */
+    int32_t seg_max;           /* largest group a doubling round sorts on chip (8..2048,
+                                  default 256); larger groups go through radix passes */
+    int32_t reserved;
 } dnasa_opts;
 
 /* One suffix-prefix overlap: the last L bases of fragment j equal the first L
@@ -120,7 +123,8 @@ enum {
     DNASA_PROF_LAYOUT = 8,
     DNASA_PROF_PACK = 9,
     DNASA_PROF_OTHER = 10,
-    DNASA_PROF_KINDS = 11
+    DNASA_PROF_SEGSORT = 11,  /* in-group sorting of a doubling round */
+    DNASA_PROF_KINDS = 12
 };
 
 /* Per kernel class: launches, summed device time (CUDA events recorded on the
@@ -280,12 +284,13 @@ int assemble_batched(dnasa_ctx *ctx, const uint8_t *texts, const int64_t *inst_o
                      int64_t *n_contigs, int64_t *needed, void *stream);
 
 /* Autotuner of the build options: times sa_build (batched when n_inst > 1) on
- * this text for every tile size (2048, 3840, 5120) and doubling-to-direct
- * switch (never, N/64, N/8, as soon as every group fits the finisher), and
+ * this text for every tile size (2048, 3840, 5120), doubling-to-direct switch
+ * (never, N/64, N/8, as soon as every group fits the finisher) and on-chip group
+ * limit (32, 256, 2048), and
  * writes the fastest to *best (host) and its time to *best_ms (host, may be
  * NULL).  The radix digit is 8 bits: the only width the kernels implement.
  * With cache_path (may be NULL), a line "key<TAB>tile<TAB>switch<TAB>lookback
- * <TAB>ms" keyed by GPU name, bits of N and bits of n_inst is looked up first
+ * <TAB>seg_max<TAB>ms" keyed by GPU name, bits of N and bits of n_inst is looked up first
  * and appended after tuning.  inst_off as for sa_build_batched (host).
  * Synchronizes the stream. */
 int dnasa_autotune(dnasa_ctx *ctx, const uint64_t *packed, const int64_t *toff, int64_t n_reads,

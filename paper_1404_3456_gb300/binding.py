@@ -33,7 +33,7 @@ class DnasaError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("digit_bits", ctypes.c_int32), ("tile_items", ctypes.c_int32),
                 ("finish_threshold", ctypes.c_int64), ("max_rounds", ctypes.c_int32),
-                ("lookback", ctypes.c_int32)]
+                ("lookback", ctypes.c_int32), ("seg_max", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class Trace(ctypes.Structure):
@@ -48,7 +48,7 @@ class ProfEntry(ctypes.Structure):
 
 
 PROF_KINDS = ["onesweep", "hist", "rerank", "gather", "init_keys", "finish", "lcp", "overlap",
-              "layout", "pack", "other"]
+              "layout", "pack", "other", "segsort"]
 
 class Job(ctypes.Structure):
     _fields_ = [("text", ctypes.c_void_p), ("N", ctypes.c_int64), ("min_overlap", ctypes.c_int32),
@@ -190,8 +190,8 @@ class Context:
             pass
 
 
-def make_opts(digit_bits=0, tile_items=0, finish_threshold=0, max_rounds=0, lookback=0):
-    return Opts(digit_bits, tile_items, finish_threshold, max_rounds, lookback)
+def make_opts(digit_bits=0, tile_items=0, finish_threshold=0, max_rounds=0, lookback=0, seg_max=0):
+    return Opts(digit_bits, tile_items, finish_threshold, max_rounds, lookback, seg_max, 0)
 
 
 # ---------------------------------------------------------------- entry points

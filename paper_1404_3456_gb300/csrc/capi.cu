@@ -37,6 +37,7 @@ TextDesc one_instance(const uint64_t *packed, const int64_t *toff, int64_t n_rea
     t.inst_toff = nullptr;
     t.inst_roff = nullptr;
     t.n_inst = 1;
+    t.fid = nullptr;
     return t;
 }
 
@@ -155,7 +156,7 @@ int assemble_impl(dnasa_ctx *ctx, const uint8_t *text, int64_t N, const int64_t 
                   int32_t n_inst, int32_t min_overlap, uint8_t *contigs, int64_t cap,
                   int64_t *contig_off, int64_t off_cap, int64_t *inst_contig_off, int64_t *n_contigs,
                   int64_t *needed, const dnasa_opts *opts, cudaStream_t s) {
-    DevBuf packed, toff, sa, lcp, contained, edges, inst_toff, inst_roff;
+    DevBuf packed, toff, sa, lcp, contained, edges, inst_toff, inst_roff, fid, isa;
     const int64_t toff_cap = N / 2 + 2;
     DNASA_TRY(dev_alloc(ctx, packed, (size_t)dnasa_packed_words(N) * 8, s));
     DNASA_TRY(dev_alloc(ctx, toff, (size_t)toff_cap * 8, s));
@@ -173,14 +174,22 @@ int assemble_impl(dnasa_ctx *ctx, const uint8_t *text, int64_t N, const int64_t 
     DNASA_TRY(dev_alloc(ctx, sa, (size_t)N * 4, s));
     DNASA_TRY(dev_alloc(ctx, lcp, (size_t)N * 4, s));
     DNASA_TRY(dev_alloc(ctx, contained, (size_t)n_reads, s));
-    DNASA_TRY(sa_build_u32(ctx, t, (uint32_t *)sa.p, opts, s));
-    DNASA_TRY(lcp_build_impl(ctx, t, (const uint32_t *)sa.p, (int32_t *)lcp.p, s));
+    DNASA_TRY(dev_alloc(ctx, isa, (size_t)N * 4, s));
+    if (n_reads > 1) {   // fragment of every position: one load instead of a binary search
+        DNASA_TRY(dev_alloc(ctx, fid, (size_t)N * 4, s));
+        DNASA_TRY(fragment_ids(ctx, t, (uint32_t *)fid.p, s));
+        t.fid = (const uint32_t *)fid.p;
+    }
+    DNASA_TRY(sa_build_u32(ctx, t, (uint32_t *)sa.p, opts, s, (uint32_t *)isa.p));
+    DNASA_TRY(lcp_build_impl(ctx, t, (const uint32_t *)sa.p, (int32_t *)lcp.p, s,
+                             (const uint32_t *)isa.p));
     int64_t ecap = std::max<int64_t>(8 * n_reads, 1024), ne = 0;
     for (int attempt = 0; attempt < 2; ++attempt) {
         if (edges.p) { cudaFreeAsync(edges.p, s); edges.p = nullptr; }
         DNASA_TRY(dev_alloc(ctx, edges, (size_t)ecap * sizeof(dnasa_edge), s));
         int rc = overlap_impl(ctx, t, (const uint32_t *)sa.p, (const int32_t *)lcp.p, min_overlap,
-                              (dnasa_edge *)edges.p, ecap, &ne, (uint8_t *)contained.p, s);
+                              (dnasa_edge *)edges.p, ecap, &ne, (uint8_t *)contained.p, s,
+                              (const uint32_t *)isa.p);
         if (rc == DNASA_CAPACITY && attempt == 0) { ecap = ne + 16; continue; }
         DNASA_TRY(rc);
         break;
@@ -211,6 +220,8 @@ int sa_build(dnasa_ctx *ctx, const uint64_t *packed, const int64_t *toff, int64_
         return fail(ctx, DNASA_INVALID_ARG, "sa_build: digit_bits must be 0 or 8");
     if (opts && opts->lookback != 0 && opts->lookback != 1 && opts->lookback != 8)
         return fail(ctx, DNASA_INVALID_ARG, "sa_build: lookback must be 0, 1 or 8");
+    if (opts && opts->seg_max != 0 && (opts->seg_max < 8 || opts->seg_max > 2048))
+        return fail(ctx, DNASA_INVALID_ARG, "sa_build: seg_max must be 0 or in [8, 2048]");
     cudaSetDevice(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
     TextDesc t = one_instance(packed, toff, n_reads, N);
@@ -349,14 +360,15 @@ int dnasa_autotune(dnasa_ctx *ctx, const uint64_t *packed, const int64_t *toff, 
             while (fgets(line, sizeof line, f)) {
                 char *tab = strchr(line, '\t');
                 if (!tab || (size_t)(tab - line) != strlen(key) || strncmp(line, key, strlen(key))) continue;
-                int tile, lb;
+                int tile, lb, sm;
                 long long fin;
                 double ms;
-                if (sscanf(tab + 1, "%d\t%lld\t%d\t%lf", &tile, &fin, &lb, &ms) == 4) {
+                if (sscanf(tab + 1, "%d\t%lld\t%d\t%d\t%lf", &tile, &fin, &lb, &sm, &ms) == 5) {
                     *best = dnasa_opts{};
                     best->tile_items = tile;
                     best->finish_threshold = fin;
                     best->lookback = lb;
+                    best->seg_max = sm;
                     if (best_ms) *best_ms = ms;
                     fclose(f);
                     return DNASA_OK;
@@ -384,11 +396,13 @@ int dnasa_autotune(dnasa_ctx *ctx, const uint64_t *packed, const int64_t *toff, 
     dnasa_opts bopt{};
     const int tiles[3] = {2048, 3840, 5120};
     const int64_t fins[4] = {-1, std::max<int64_t>(N / 64, 1), std::max<int64_t>(N / 8, 1), N};
+    const int segs[3] = {32, 256, 2048};
     for (int ti = 0; ti < 3 && rc == DNASA_OK; ++ti) {
-        for (int fi = 0; fi < 4 && rc == DNASA_OK; ++fi) {
+        for (int fi = 0; fi < 4 * 3 && rc == DNASA_OK; ++fi) {
             dnasa_opts o{};
             o.tile_items = tiles[ti];
-            o.finish_threshold = fins[fi];
+            o.finish_threshold = fins[fi % 4];
+            o.seg_max = segs[fi / 4];
             o.lookback = 8;
             cudaEventRecord(e0, s);
             rc = sa_build_u32(ctx, t, (uint32_t *)sa.p, &o, s);
@@ -411,8 +425,8 @@ int dnasa_autotune(dnasa_ctx *ctx, const uint64_t *packed, const int64_t *toff, 
     if (cache_path) {
         FILE *f = fopen(cache_path, "a");
         if (f) {
-            fprintf(f, "%s\t%d\t%lld\t%d\t%.4f\n", key, bopt.tile_items,
-                    (long long)bopt.finish_threshold, bopt.lookback, bms);
+            fprintf(f, "%s\t%d\t%lld\t%d\t%d\t%.4f\n", key, bopt.tile_items,
+                    (long long)bopt.finish_threshold, bopt.lookback, bopt.seg_max, bms);
             fclose(f);
         }
     }

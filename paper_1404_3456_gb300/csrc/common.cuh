@@ -30,7 +30,7 @@ struct DevCtrl {
     unsigned long long count[16];  // general device counters (see CNT_*)
 };
 enum { CNT_ACTIVE = 0, CNT_GROUPS = 1, CNT_MAXGROUP = 2, CNT_CAND = 3, CNT_EDGES = 4,
-       CNT_DOLLARS = 5, CNT_TMP = 6 };
+       CNT_DOLLARS = 5, CNT_TMP = 6, CNT_SEG = 8 /* 8..12: group counts by size class */ };
 
 // ---------------------------------------------------------------- context
 
@@ -53,7 +53,7 @@ namespace dnasa {
 // Kernel classes the profiler aggregates (same numbering as DNASA_PROF_* in dnasa.h).
 enum ProfKind { PK_ONESWEEP = 0, PK_HIST = 1, PK_RERANK = 2, PK_GATHER = 3, PK_INIT = 4,
                 PK_FINISH = 5, PK_LCP = 6, PK_OVERLAP = 7, PK_LAYOUT = 8, PK_PACK = 9,
-                PK_OTHER = 10, PK_COUNT = 11 };
+                PK_OTHER = 10, PK_SEGSORT = 11, PK_COUNT = 12 };
 struct ProfRec {
     int kind;
     cudaEvent_t a, b;
@@ -164,17 +164,22 @@ struct TextDesc {
     const int64_t *inst_toff;  // device, n_inst + 1 text offsets of instances (nullptr: one)
     const int64_t *inst_roff;  // device, n_inst + 1 fragment offsets of instances
     int32_t n_inst;
+    const uint32_t *fid;       // device, N: fragment of each text position (nullptr: search toff)
 };
 
-// Builds the SA into sa32 (uint32, N entries, text coordinates).  Also leaves
-// rank = ISA in `isa_out` if non-null (N uint32).
+// Builds the SA into sa32 (uint32, N entries, text coordinates).  If isa_out is
+// non-null it also receives the inverse SA (the final rank array), N uint32.
 int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_opts *opts,
-                 cudaStream_t s);
+                 cudaStream_t s, uint32_t *isa_out = nullptr);
+// fid[p] = fragment holding text position p, for p in [0, N).
+int fragment_ids(dnasa_ctx *ctx, const TextDesc &t, uint32_t *fid, cudaStream_t s);
+// isa (may be null) = inverse of sa32: the LCP is then computed in text order.
 int lcp_build_impl(dnasa_ctx *ctx, const TextDesc &t, const uint32_t *sa32, int32_t *lcp,
-                   cudaStream_t s);
+                   cudaStream_t s, const uint32_t *isa = nullptr);
+// isa (may be null: rebuilt from sa32) is the inverse of sa32.
 int overlap_impl(dnasa_ctx *ctx, const TextDesc &t, const uint32_t *sa32, const int32_t *lcp,
                  int32_t min_overlap, dnasa_edge *edges, int64_t cap, int64_t *n_edges,
-                 uint8_t *contained, cudaStream_t s);
+                 uint8_t *contained, cudaStream_t s, const uint32_t *isa = nullptr);
 int widen_u32_to_i64(dnasa_ctx *ctx, const uint32_t *a, int64_t n, int64_t *b, cudaStream_t s);
 // Symbols in the initial packed key for an N-symbol text of n_inst instances
 // (and the instance bits).
@@ -209,6 +214,12 @@ __device__ __forceinline__ int64_t upper_index(const int64_t *__restrict__ off, 
 __device__ __forceinline__ int64_t read_of(const int64_t *__restrict__ toff, int64_t n_reads,
                                            int64_t p) {
     return upper_index(toff, 0, n_reads, p);
+}
+
+// Fragment holding text position p: one load from the per-position table when
+// the caller built one, otherwise a binary search of the fragment offsets.
+__device__ __forceinline__ int64_t frag_of(const TextDesc &t, int64_t p) {
+    return t.fid ? (int64_t)__ldg(t.fid + p) : read_of(t.toff, t.n_reads, p);
 }
 
 __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p) {

@@ -69,54 +69,101 @@ __device__ int32_t uf_find(int32_t *parent, int32_t x) {
     return x;
 }
 
-__global__ void k_greedy(TextDesc t, const unsigned long long *__restrict__ keys, int64_t ne,
-                         int kbl, int lb, const uint8_t *__restrict__ contained, LayoutArrays A) {
+// One CTA per instance.  The acceptance is sequential (each decision depends on
+// the ones before), so one thread makes it, but against successor /
+// predecessor / union-find arrays in shared memory (instances of up to
+// kGreedyMaxReads fragments; larger ones use the global arrays), with the
+// instance's sorted edges staged into shared memory in chunks by the whole CTA.
+constexpr int kGreedyMaxReads = 4096;
+constexpr int kGreedyChunk = 2048;
+constexpr int kGreedyThreads = 128;
+constexpr size_t kGreedySmem = (size_t)kGreedyMaxReads * 4 * 4 + (size_t)kGreedyChunk * 8;
+
+__global__ void __launch_bounds__(kGreedyThreads) k_greedy(TextDesc t,
+                                                          const unsigned long long *__restrict__ keys,
+                                                          int64_t ne, int kbl, int lb,
+                                                          const uint8_t *__restrict__ contained,
+                                                          LayoutArrays A) {
+    extern __shared__ __align__(16) unsigned char gsm[];
+    unsigned long long *ebuf = reinterpret_cast<unsigned long long *>(gsm);
+    int32_t *s_succ = reinterpret_cast<int32_t *>(ebuf + kGreedyChunk);
+    int32_t *s_pred = s_succ + kGreedyMaxReads;
+    int32_t *s_succL = s_pred + kGreedyMaxReads;
+    int32_t *s_parent = s_succL + kGreedyMaxReads;
+    __shared__ int64_t s_range[2];
     const unsigned long long lmask = (1ull << lb) - 1ull;
     const unsigned long long kmask = (1ull << kbl) - 1ull;
     const int shift = lb + 2 * kbl;
-    for (int64_t inst = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; inst < t.n_inst;
-         inst += (int64_t)gridDim.x * blockDim.x) {
-        int64_t r0 = inst_r0(t, inst);
-        int64_t r1 = t.n_inst > 1 ? __ldg(t.inst_roff + inst + 1) : t.n_reads;
-        for (int64_t r = r0; r < r1; ++r) {
-            A.succ[r] = -1; A.pred[r] = -1; A.succL[r] = 0; A.parent[r] = (int32_t)r;
-            A.out_off[r] = -1; A.skip[r] = 0; A.chead[r] = -1;
+    for (int64_t inst = blockIdx.x; inst < t.n_inst; inst += gridDim.x) {
+        const int64_t r0 = inst_r0(t, inst);
+        const int64_t r1 = t.n_inst > 1 ? __ldg(t.inst_roff + inst + 1) : t.n_reads;
+        const int64_t nr = r1 - r0;
+        const bool fast = nr <= kGreedyMaxReads;
+        int32_t *succ = fast ? s_succ : A.succ + r0;       // indexed by local fragment number
+        int32_t *pred = fast ? s_pred : A.pred + r0;
+        int32_t *succL = fast ? s_succL : A.succL + r0;
+        int32_t *parent = fast ? s_parent : A.parent + r0;
+        for (int64_t i = threadIdx.x; i < nr; i += kGreedyThreads) {
+            succ[i] = -1; pred[i] = -1; succL[i] = 0; parent[i] = (int32_t)i;
+            A.out_off[r0 + i] = -1; A.skip[r0 + i] = 0; A.chead[r0 + i] = -1;
         }
-        // edges of this instance: keys with instance field == inst
-        int64_t lo = 0, hi = ne;
-        const unsigned long long kinst = (unsigned long long)inst;
-        while (lo < hi) {
-            int64_t m = (lo + hi) >> 1;
-            if ((keys[m] >> shift) < kinst) lo = m + 1; else hi = m;
-        }
-        for (int64_t e = lo; e < ne && (keys[e] >> shift) == kinst; ++e) {
-            unsigned long long key = keys[e];
-            int32_t L = (int32_t)(lmask - ((key >> (2 * kbl)) & lmask));
-            int32_t j = (int32_t)(r0 + ((key >> kbl) & kmask));
-            int32_t k = (int32_t)(r0 + (key & kmask));
-            if (A.succ[j] != -1 || A.pred[k] != -1) continue;
-            int32_t a = uf_find(A.parent, j), b = uf_find(A.parent, k);
-            if (a == b) continue;
-            A.succ[j] = k; A.succL[j] = L; A.pred[k] = j; A.parent[a] = b;
-        }
-        int64_t bytes = 0, nc = 0;
-        for (int64_t r = r0; r < r1; ++r) {
-            if (contained[r] || A.pred[r] != -1) continue;
-            A.chead[r] = (int32_t)nc;
-            int64_t cur = r;
-            int32_t sk = 0;
-            for (;;) {
-                A.out_off[cur] = bytes;
-                A.skip[cur] = sk;
-                bytes += frag_len(t.toff, cur) - sk;
-                if (A.succ[cur] == -1) break;
-                sk = A.succL[cur];
-                cur = A.succ[cur];
+        if (threadIdx.x == 0) {   // this instance's edges: keys whose instance field == inst
+            const unsigned long long kinst = (unsigned long long)inst;
+            int64_t lo = 0, hi = ne;
+            while (lo < hi) {
+                int64_t m = (lo + hi) >> 1;
+                if ((keys[m] >> shift) < kinst) lo = m + 1; else hi = m;
             }
-            ++nc;
+            int64_t e = lo;
+            hi = ne;
+            while (e < hi) {
+                int64_t m = (e + hi) >> 1;
+                if ((keys[m] >> shift) <= kinst) e = m + 1; else hi = m;
+            }
+            s_range[0] = lo;
+            s_range[1] = e;
         }
-        A.inst_bytes[inst] = bytes;
-        A.inst_contigs[inst] = nc;
+        __syncthreads();
+        const int64_t e0 = s_range[0], e1 = s_range[1];
+        for (int64_t c0 = e0; c0 < e1; c0 += kGreedyChunk) {
+            const int len = (int)min((int64_t)kGreedyChunk, e1 - c0);
+            for (int i = threadIdx.x; i < len; i += kGreedyThreads) ebuf[i] = keys[c0 + i];
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                for (int i = 0; i < len; ++i) {
+                    const unsigned long long key = ebuf[i];
+                    const int32_t L = (int32_t)(lmask - ((key >> (2 * kbl)) & lmask));
+                    const int32_t j = (int32_t)((key >> kbl) & kmask);
+                    const int32_t k = (int32_t)(key & kmask);
+                    if (succ[j] != -1 || pred[k] != -1) continue;
+                    const int32_t a = uf_find(parent, j), b = uf_find(parent, k);
+                    if (a == b) continue;
+                    succ[j] = k; succL[j] = L; pred[k] = j; parent[a] = b;
+                }
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {   // chains in ascending head order: output offsets
+            int64_t bytes = 0, nc = 0;
+            for (int64_t r = 0; r < nr; ++r) {
+                if (contained[r0 + r] || pred[r] != -1) continue;
+                A.chead[r0 + r] = (int32_t)nc;
+                int64_t cur = r;
+                int32_t sk = 0;
+                for (;;) {
+                    A.out_off[r0 + cur] = bytes;
+                    A.skip[r0 + cur] = sk;
+                    bytes += frag_len(t.toff, r0 + cur) - sk;
+                    if (succ[cur] == -1) break;
+                    sk = succL[cur];
+                    cur = succ[cur];
+                }
+                ++nc;
+            }
+            A.inst_bytes[inst] = bytes;
+            A.inst_contigs[inst] = nc;
+        }
+        __syncthreads();
     }
 }
 
@@ -262,9 +309,14 @@ int layout_impl(dnasa_ctx *ctx, const TextDesc &t, int64_t max_reads_per_inst,
                                                            ib + lb + 2 * kbl, false, tile, &which, s));
         }
     }
+    static const cudaError_t greedy_smem =
+        cudaFuncSetAttribute(k_greedy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGreedySmem);
+    DNASA_CUDA(ctx, greedy_smem);
     {
         LaunchScope ls_(ctx, PK_LAYOUT, s, 0);
-        k_greedy<<<grid_for(ctx, t.n_inst, 64), 64, 0, s>>>(t, keys[which], nsel, kbl, lb, contained, A);
+        int g = (int)std::min<int64_t>(t.n_inst, (int64_t)ctx->num_sms * 8);
+        k_greedy<<<std::max(g, 1), kGreedyThreads, kGreedySmem, s>>>(t, keys[which], nsel, kbl, lb,
+                                                                    contained, A);
     }
     {
         LaunchScope ls_(ctx, PK_LAYOUT, s, 0);

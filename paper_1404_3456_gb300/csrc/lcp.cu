@@ -31,8 +31,8 @@ __device__ __forceinline__ bool instance_start(const TextDesc &t, int64_t j) {
 __device__ __forceinline__ PairInfo pair_info(const TextDesc &t, const uint32_t *__restrict__ sa,
                                               int64_t j) {
     int64_t p = sa[j - 1], q = sa[j];
-    int64_t rp = read_of(t.toff, t.n_reads, p);
-    int64_t rq = read_of(t.toff, t.n_reads, q);
+    int64_t rp = frag_of(t, p);
+    int64_t rq = frag_of(t, q);
     PairInfo r;
     r.m = min(__ldg(t.toff + rp + 1) - 1 - p, __ldg(t.toff + rq + 1) - 1 - q);
     r.bp = (uint64_t)(p - rp);
@@ -125,10 +125,83 @@ __global__ void __launch_bounds__(256) k_lcp_chain(TextDesc t, const uint32_t *_
     }
 }
 
+// With the inverse SA at hand: PLCP in text order (Kaerkkaeinen, Manzini &
+// Puglisi's Phi algorithm).  PLCP[p] = LCP of suffix p with its SA predecessor
+// sa[isa[p] - 1]; PLCP[p] >= PLCP[p-1] - 1, so each thread walks kPhiChunk
+// consecutive positions and starts each comparison where the previous one
+// ended.  '$' positions have PLCP 0 (among them every instance's first slot).
+constexpr int kPhiChunk = 64;
+
+__global__ void __launch_bounds__(128) k_plcp(TextDesc t, const uint32_t *__restrict__ sa,
+                                              const uint32_t *__restrict__ isa,
+                                              uint32_t *__restrict__ plcp) {
+    const int64_t chunks = (t.N + kPhiChunk - 1) / kPhiChunk;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < chunks;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p0 = c * kPhiChunk, p1 = min(p0 + kPhiChunk, t.N);
+        int64_t prev = 0;
+        int64_t rp = frag_of(t, p0);
+        for (int64_t p = p0; p < p1; ++p) {
+            while (__ldg(t.toff + rp + 1) <= p) ++rp;
+            const int64_t remp = __ldg(t.toff + rp + 1) - 1 - p;
+            const uint32_t j = isa[p];
+            int64_t h = 0;
+            if (remp > 0 && j > 0) {
+                const int64_t q = sa[j - 1];
+                const int64_t rq = frag_of(t, q);
+                const int64_t m = min(remp, __ldg(t.toff + rq + 1) - 1 - q);
+                const uint64_t bp = (uint64_t)(p - rp), bq = (uint64_t)(q - rq);
+                h = min(max(prev - 1, (int64_t)0), m);
+                for (; h < m; h += 4 * 32) {
+                    uint64_t d[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        int64_t o = h + 32 * u;
+                        d[u] = o < m ? bases32(t.packed, bp + o) ^ bases32(t.packed, bq + o) : ~0ull;
+                    }
+                    int64_t at = -1;
+#pragma unroll
+                    for (int u = 3; u >= 0; --u)
+                        if (d[u]) at = h + 32 * u + (__clzll((long long)d[u]) >> 1);
+                    if (at >= 0) { h = at; break; }
+                }
+                h = min(h, m);
+            }
+            plcp[p] = (uint32_t)h;
+            prev = h;
+        }
+    }
+}
+
+__global__ void k_lcp_gather(const uint32_t *__restrict__ sa, const uint32_t *__restrict__ plcp,
+                             int64_t N, int32_t *__restrict__ lcp) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < N;
+         j += (int64_t)gridDim.x * blockDim.x)
+        lcp[j] = (int32_t)__ldg(plcp + sa[j]);
+}
+
 }  // namespace
 
 int lcp_build_impl(dnasa_ctx *ctx, const TextDesc &t, const uint32_t *sa32, int32_t *lcp,
-                   cudaStream_t s) {
+                   cudaStream_t s, const uint32_t *isa) {
+    if (isa) {   // Phi / PLCP in text order, then one gather
+        DNASA_TRY(ws_reserve(ctx, ((size_t)t.N * 4 + 255) / 256 * 256 + 4096, s));
+        Arena a = ws_arena(ctx);
+        uint32_t *plcp = a.take<uint32_t>((size_t)t.N);
+        int chunks = ceil_div(t.N, kPhiChunk);
+        {
+            LaunchScope ls_(ctx, PK_LCP, s, 12.0 * t.N);
+            int g = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(chunks, 128), (int64_t)ctx->num_sms * 64));
+            k_plcp<<<g, 128, 0, s>>>(t, sa32, isa, plcp);
+        }
+        {
+            LaunchScope ls_(ctx, PK_LCP, s, 12.0 * t.N);
+            int g = (int)std::min<int64_t>(ceil_div(t.N, 256), (int64_t)ctx->num_sms * 16);
+            k_lcp_gather<<<std::max(g, 1), 256, 0, s>>>(sa32, plcp, t.N, lcp);
+        }
+        DNASA_CUDA(ctx, cudaGetLastError());
+        return DNASA_OK;
+    }
     const int tile = radix_tile_default();
     const int key_bits = bits_for((uint64_t)(t.N - 1));
     const size_t q = ((size_t)t.N * 4 + 255) / 256 * 256;

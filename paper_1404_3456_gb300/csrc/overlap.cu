@@ -91,7 +91,7 @@ struct QueryArgs {
 // calls emit(k) for each overlap (j, k, |X|).  Returns false when q is no query.
 template <typename F>
 __device__ __forceinline__ void query_walk(const TextDesc &t, const QueryArgs &a, int64_t q, F emit) {
-    int64_t j = read_of(t.toff, t.n_reads, q);
+    int64_t j = frag_of(t, q);
     int64_t start = __ldg(t.toff + j);
     int64_t o = q - start;
     int64_t L = __ldg(t.toff + j + 1) - 1 - q;   // bases of X = r_j[o..]
@@ -193,7 +193,7 @@ __global__ void k_contained(TextDesc t, const uint32_t *__restrict__ sa,
         } else {
             for (int64_t u = s + 1; u < is1 && lcp[u] >= len; ++u) {
                 int64_t p = sa[u];
-                int64_t rp = read_of(t.toff, t.n_reads, p);
+                int64_t rp = frag_of(t, p);
                 if (p != __ldg(t.toff + rp) || frag_len(t.toff, rp) > len) { c = 1; break; }
             }
         }
@@ -210,7 +210,7 @@ inline int grid_for(dnasa_ctx *ctx, int64_t n, int threads = 256) {
 
 int overlap_impl(dnasa_ctx *ctx, const TextDesc &t, const uint32_t *sa32, const int32_t *lcp,
                  int32_t min_overlap, dnasa_edge *edges, int64_t cap, int64_t *n_edges,
-                 uint8_t *contained, cudaStream_t s) {
+                 uint8_t *contained, cudaStream_t s, const uint32_t *isa_in) {
     const int64_t N = t.N, nr = t.n_reads;
     const int kb = bits_for((uint64_t)std::max<int64_t>(nr - 1, 1));
     const int tile = radix_tile_default();
@@ -233,7 +233,8 @@ int overlap_impl(dnasa_ctx *ctx, const TextDesc &t, const uint32_t *sa32, const 
     unsigned long long *cnt = ctx->ctrl->count;
     for (int attempt = 0; attempt < 2; ++attempt) {
         Arena a = ws_arena(ctx);
-        uint32_t *isa = a.take<uint32_t>((size_t)N);
+        uint32_t *isa_ws = a.take<uint32_t>((size_t)N);
+        const uint32_t *isa = isa_in ? isa_in : isa_ws;
         uint32_t *rk[2] = {a.take<uint32_t>((size_t)nr), a.take<uint32_t>((size_t)nr)};
         uint32_t *rv[2] = {a.take<uint32_t>((size_t)nr), a.take<uint32_t>((size_t)nr)};
         int32_t *lcpr = a.take<int32_t>((size_t)nr);
@@ -246,9 +247,9 @@ int overlap_impl(dnasa_ctx *ctx, const TextDesc &t, const uint32_t *sa32, const 
         if (!rs2.hist) return fail(ctx, DNASA_OOM, "overlap_search workspace");
 
         DNASA_CUDA(ctx, cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * 8, s));
-        {
+        if (!isa_in) {
             LaunchScope ls_(ctx, PK_OVERLAP, s, 0);
-            k_isa<<<grid_for(ctx, N), 256, 0, s>>>(sa32, N, isa);
+            k_isa<<<grid_for(ctx, N), 256, 0, s>>>(sa32, N, isa_ws);
         }
         {
             LaunchScope ls_(ctx, PK_OVERLAP, s, 0);

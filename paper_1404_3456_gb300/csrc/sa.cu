@@ -460,6 +460,277 @@ __global__ void __launch_bounds__(kFinThreads) k_finish(const uint2 *__restrict_
     }
 }
 
+// ------------------------------------------------------------------ S5: in-group sorting
+// From round 1 on, a round only has to order the members of each group by
+// rank[i+h] (all members of a group share the high key part, the head rank),
+// and members with equal keys stay together in one group that a later round
+// sorts again, so no stable order is needed.  Groups of at most 32 members are
+// sorted by one warp in registers, up to kSegMax members by one CTA in shared
+// memory (bitonic networks); only the members of larger groups go through the
+// global radix sort.  Each item is then read and written once instead of once
+// per radix pass.
+constexpr int kSegMax = 2048;
+constexpr int kSegWarpMax = 256;   // one warp, shared-memory slice
+constexpr int kSegThreads = 256;
+
+__device__ __forceinline__ bool kv_less(unsigned long long ka, uint32_t va, unsigned long long kb,
+                                        uint32_t vb) {
+    return ka < kb || (ka == kb && va < vb);
+}
+
+// Splits the group list into five lists by size (<= 8, <= 32, <= kSegWarpMax,
+// <= kSegMax, larger; nothing above seg_max is sorted on chip), one atomic per
+// warp and list.
+__global__ void __launch_bounds__(256) k_classify(const uint2 *__restrict__ groups, int64_t ng,
+                                                  int seg_max, uint2 *__restrict__ tiny,
+                                                  uint2 *__restrict__ small, uint2 *__restrict__ wmid,
+                                                  uint2 *__restrict__ mid, uint2 *__restrict__ large,
+                                                  unsigned long long *__restrict__ counts) {
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane; b < ng; b += stride) {
+        const int64_t g = b + lane;
+        uint2 gs = g < ng ? groups[g] : make_uint2(0, 0);
+        const int sz = (int)gs.y;
+        const int cls = g >= ng ? -1 : sz > seg_max ? 4 : sz <= 8 ? 0 : sz <= 32 ? 1
+                                                 : sz <= kSegWarpMax ? 2 : 3;
+        uint2 *lists[5] = {tiny, small, wmid, mid, large};
+#pragma unroll
+        for (int c = 0; c < 5; ++c) {
+            uint32_t m = __ballot_sync(0xffffffffu, cls == c);
+            if (!m) continue;
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(&counts[c], (unsigned long long)__popc(m));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (cls == c) lists[c][base + __popc(m & lanemask_lt())] = gs;
+        }
+    }
+}
+
+// Groups of at most 8 members: one thread each, insertion sort in registers.
+__global__ void __launch_bounds__(256) k_seg_thread(const uint2 *__restrict__ groups,
+                                                    const unsigned long long *__restrict__ d_ng,
+                                                    unsigned long long *__restrict__ keys,
+                                                    uint32_t *__restrict__ vals) {
+    const int64_t ng = (int64_t)*d_ng;
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ng;
+         g += (int64_t)gridDim.x * blockDim.x) {
+        const uint2 gs = groups[g];
+        const int n = (int)gs.y;   // 2..8
+        unsigned long long k[8];
+        uint32_t v[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            if (i < n) { k[i] = keys[gs.x + i]; v[i] = vals[gs.x + i]; }
+#pragma unroll
+        for (int i = 1; i < 8; ++i) {
+            if (i < n) {
+#pragma unroll
+                for (int j = i; j > 0; --j) {
+                    if (kv_less(k[j], v[j], k[j - 1], v[j - 1])) {
+                        unsigned long long tk = k[j]; k[j] = k[j - 1]; k[j - 1] = tk;
+                        uint32_t tv = v[j]; v[j] = v[j - 1]; v[j - 1] = tv;
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            if (i < n) { keys[gs.x + i] = k[i]; vals[gs.x + i] = v[i]; }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_seg_warp(const uint2 *__restrict__ groups,
+                                                  const unsigned long long *__restrict__ d_ng,
+                                                  unsigned long long *__restrict__ keys,
+                                                  uint32_t *__restrict__ vals) {
+    const int lane = threadIdx.x & 31;
+    const int64_t ng = (int64_t)*d_ng;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < ng; g += nw) {
+        const uint2 gs = groups[g];                    // 2..32 members
+        const int n = (int)gs.y;
+        int n2 = 2;
+        while (n2 < n) n2 <<= 1;                       // network only as wide as the group
+        unsigned long long k = lane < n ? keys[gs.x + lane] : ~0ull;
+        uint32_t v = lane < n ? vals[gs.x + lane] : ~0u;
+        for (int size = 2; size <= n2; size <<= 1) {
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                unsigned long long ok = __shfl_xor_sync(0xffffffffu, k, stride);
+                uint32_t ov = __shfl_xor_sync(0xffffffffu, v, stride);
+                bool keep_min = ((lane & stride) == 0) == ((lane & size) == 0);
+                bool mine_less = kv_less(k, v, ok, ov);
+                if (keep_min != mine_less) { k = ok; v = ov; }
+            }
+        }
+        if (lane < n) {
+            keys[gs.x + lane] = k;
+            vals[gs.x + lane] = v;
+        }
+    }
+}
+
+// 33..kSegWarpMax members: one warp per group, bitonic network over a private
+// shared-memory slice (warp-level synchronisation only).
+constexpr int kSegWarpsPerCta = 8;
+__global__ void __launch_bounds__(32 * kSegWarpsPerCta) k_seg_warpsm(
+    const uint2 *__restrict__ groups, const unsigned long long *__restrict__ d_ng,
+    unsigned long long *__restrict__ keys, uint32_t *__restrict__ vals) {
+    __shared__ unsigned long long sk_all[kSegWarpsPerCta][kSegWarpMax];
+    __shared__ uint32_t sv_all[kSegWarpsPerCta][kSegWarpMax];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    unsigned long long *sk = sk_all[w];
+    uint32_t *sv = sv_all[w];
+    const int64_t ng = (int64_t)*d_ng;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < ng; g += nw) {
+        const uint2 gs = groups[g];
+        const int n = (int)gs.y;
+        int n2 = 64;
+        while (n2 < n) n2 <<= 1;
+        for (int i = lane; i < n2; i += 32) {
+            sk[i] = i < n ? keys[gs.x + i] : ~0ull;
+            sv[i] = i < n ? vals[gs.x + i] : ~0u;
+        }
+        __syncwarp();
+        for (int size = 2; size <= n2; size <<= 1) {
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                for (int i = lane; i < n2; i += 32) {
+                    int ixj = i ^ stride;
+                    if (ixj > i) {
+                        bool asc = (i & size) == 0;
+                        if (asc == kv_less(sk[ixj], sv[ixj], sk[i], sv[i])) {
+                            unsigned long long tk = sk[i]; sk[i] = sk[ixj]; sk[ixj] = tk;
+                            uint32_t tv = sv[i]; sv[i] = sv[ixj]; sv[ixj] = tv;
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        for (int i = lane; i < n; i += 32) {
+            keys[gs.x + i] = sk[i];
+            vals[gs.x + i] = sv[i];
+        }
+        __syncwarp();
+    }
+}
+
+__global__ void __launch_bounds__(kSegThreads) k_seg_block(const uint2 *__restrict__ groups,
+                                                           const unsigned long long *__restrict__ d_ng,
+                                                           unsigned long long *__restrict__ keys,
+                                                           uint32_t *__restrict__ vals) {
+    __shared__ unsigned long long sk[kSegMax];
+    __shared__ uint32_t sv[kSegMax];
+    const int64_t ng = (int64_t)*d_ng;
+    for (int64_t g = blockIdx.x; g < ng; g += gridDim.x) {
+        const uint2 gs = groups[g];                    // kSegWarpMax+1..kSegMax members
+        const int n = (int)gs.y;
+        int n2 = 512;
+        while (n2 < n) n2 <<= 1;
+        for (int i = threadIdx.x; i < n2; i += kSegThreads) {
+            sk[i] = i < n ? keys[gs.x + i] : ~0ull;
+            sv[i] = i < n ? vals[gs.x + i] : ~0u;
+        }
+        __syncthreads();
+        for (int size = 2; size <= n2; size <<= 1) {
+            for (int stride = size >> 1; stride > 0; stride >>= 1) {
+                for (int i = threadIdx.x; i < n2; i += kSegThreads) {
+                    int ixj = i ^ stride;
+                    if (ixj > i) {
+                        bool asc = (i & size) == 0;
+                        bool hi_less = kv_less(sk[ixj], sv[ixj], sk[i], sv[i]);
+                        if (asc == hi_less) {   // ascending: smaller first; descending: larger first
+                            unsigned long long tk = sk[i]; sk[i] = sk[ixj]; sk[ixj] = tk;
+                            uint32_t tv = sv[i]; sv[i] = sv[ixj]; sv[ixj] = tv;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        for (int i = threadIdx.x; i < n; i += kSegThreads) {
+            keys[gs.x + i] = sk[i];
+            vals[gs.x + i] = sv[i];
+        }
+        __syncthreads();
+    }
+}
+
+// Marks the members of the groups larger than kSegMax (flags zeroed beforehand).
+__global__ void k_flag_large(const uint2 *__restrict__ groups,
+                             const unsigned long long *__restrict__ d_ng, uint8_t *__restrict__ flags) {
+    const int64_t ng = (int64_t)*d_ng;
+    for (int64_t g = blockIdx.x; g < ng; g += gridDim.x) {
+        const uint2 gs = groups[g];
+        for (uint32_t i = threadIdx.x; i < gs.y; i += blockDim.x) flags[(size_t)gs.x + i] = 1;
+    }
+}
+
+__global__ void k_take(const uint32_t *__restrict__ idx, const unsigned long long *__restrict__ d_m,
+                       const unsigned long long *__restrict__ keys, const uint32_t *__restrict__ vals,
+                       unsigned long long *__restrict__ ck, uint32_t *__restrict__ cv) {
+    const int64_t m = (int64_t)*d_m;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t t = idx[i];
+        ck[i] = keys[t];
+        cv[i] = vals[t];
+    }
+}
+
+// Sorted large-group members back to their ranges: the i-th of the sorted list
+// belongs at the i-th large-group index (groups keep their order: ascending head
+// rank = ascending position in the active list).
+__global__ void k_put(const uint32_t *__restrict__ idx, const unsigned long long *__restrict__ d_m,
+                      const unsigned long long *__restrict__ ck, const uint32_t *__restrict__ cv,
+                      unsigned long long *__restrict__ keys, uint32_t *__restrict__ vals) {
+    const int64_t m = (int64_t)*d_m;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t t = idx[i];
+        keys[t] = ck[i];
+        vals[t] = cv[i];
+    }
+}
+
+// Ranks of the members the finisher placed: rank[sa[slot]] = slot, so that the
+// rank array ends as the inverse suffix array.  (A separate launch: the
+// finisher's own comparisons read rank[] and must see it unchanged.)
+__global__ void k_finish_ranks(const uint2 *__restrict__ groups,
+                               const unsigned long long *__restrict__ ngroups,
+                               const uint32_t *__restrict__ nslots, const uint32_t *__restrict__ sa,
+                               int64_t N, uint32_t *__restrict__ rank) {
+    const int64_t ng = (int64_t)*ngroups;
+    for (int64_t g = blockIdx.x; g < ng; g += gridDim.x) {
+        const uint2 gs = groups[g];
+        const uint32_t slot0 = nslots[gs.x];
+        for (uint32_t i = threadIdx.x; i < gs.y; i += blockDim.x) {
+            int64_t slot = (int64_t)slot0 + i;
+            if (slot < N) {
+                uint32_t pos = sa[slot];
+                if ((int64_t)pos < N) rank[pos] = (uint32_t)slot;
+            }
+        }
+    }
+}
+
+// fid[p] = fragment of text position p: each warp walks 32 * 8 consecutive
+// positions after one binary search per lane.
+__global__ void __launch_bounds__(256) k_fid(TextDesc t, uint32_t *__restrict__ fid) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t p0 = warp * 32 * 8 + lane;
+    if (warp * 32 * 8 >= t.N) return;
+    int64_t r = read_of(t.toff, t.n_reads, min(p0, t.N - 1));
+    for (int i = 0; i < 8; ++i) {
+        int64_t p = p0 + (int64_t)i * 32;
+        if (p >= t.N) break;
+        while (__ldg(t.toff + r + 1) <= p) ++r;
+        fid[p] = (uint32_t)r;
+    }
+}
+
 __global__ void k_widen(const uint32_t *__restrict__ a, int64_t n, int64_t *__restrict__ b) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
@@ -484,7 +755,7 @@ int h0_for(int64_t N, int n_inst, int *inst_bits) {
 }
 
 int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_opts *opts_in,
-                 cudaStream_t s) {
+                 cudaStream_t s, uint32_t *isa_out) {
     dnasa_opts opts{};
     if (opts_in) opts = *opts_in;
     const int tile_items = opts.tile_items ? opts.tile_items : radix_tile_default();
@@ -492,6 +763,8 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
         opts.finish_threshold == 0 ? (int64_t)1 << 20 : opts.finish_threshold;
     const int max_rounds = opts.max_rounds > 0 ? std::min(opts.max_rounds, 63) : 63;
     const int lbw = opts.lookback == 1 ? 1 : 8;
+    // largest group a doubling round sorts on chip (larger ones: radix passes)
+    const int seg_max = opts.seg_max == 0 ? 256 : std::max(8, std::min(opts.seg_max, kSegMax));
     const int64_t N = t.N;
     int ib;
     const int h0 = h0_for(N, t.n_inst, &ib);
@@ -511,6 +784,9 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
     add((n / 2 + 1) * 8);                   // groups
     add((size_t)rr_tiles * 8);              // rerank status
     add((size_t)kMaxBuckets * 4);           // rank-write bucket fill counts
+    add(n); add(n * 4); add(n * 8); add(n * 4);   // large-group flags, indices, sort buffers
+    for (int i = 0; i < 5; ++i) add((n / 2 + 1) * 8);   // group lists by size class
+    add(compact_scratch_bytes(N));
     add(radix_scratch_bytes(N, 64, tile_items));
     DNASA_TRY(ws_reserve(ctx, need + 4096, s));
     Arena a = ws_arena(ctx);
@@ -523,6 +799,13 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
     uint2 *groups = a.take<uint2>(n / 2 + 1);
     unsigned long long *rr_status = a.take<unsigned long long>((size_t)rr_tiles);
     uint32_t *bucket_fill = a.take<uint32_t>((size_t)kMaxBuckets);
+    uint8_t *lflags = a.take<uint8_t>(n);
+    uint2 *gtiny = a.take<uint2>(n / 2 + 1);
+    uint2 *gsmall = a.take<uint2>(n / 2 + 1), *gwmid = a.take<uint2>(n / 2 + 1);
+    uint2 *gmid = a.take<uint2>(n / 2 + 1), *glarge = a.take<uint2>(n / 2 + 1);
+    uint32_t *lidx = a.take<uint32_t>(n);
+    unsigned long long *ck2 = a.take<unsigned long long>(n);
+    uint32_t *cv2 = a.take<uint32_t>(n);
     RadixScratch rs = radix_scratch_take(a, N, 64, tile_items);
     if (!rs.hist || !rr_status) return fail(ctx, DNASA_OOM, "sa_build workspace");
 
@@ -621,6 +904,11 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
                                                                    L[cur][0], rank, (uint32_t)h, N,
                                                                    sa32, &c->err);
             }
+            {
+                LaunchScope ls_(ctx, PK_FINISH, s, 0);
+                k_finish_ranks<<<std::max(grid, 1), 256, 0, s>>>(groups, cnt + CNT_GROUPS, L[cur][0],
+                                                                 sa32, N, rank);
+            }
             DNASA_CUDA(ctx, cudaGetLastError());
             tr.finished_direct = 1;
             break;
@@ -635,21 +923,75 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
                                                        (uint32_t)h, b, keys[0], vals[0], N, &c->err);
         }
         DNASA_CUDA(ctx, cudaGetLastError());
-        int which;
-        DNASA_TRY(radix_sort_pairs<unsigned long long>(ctx, rs, keys, vals, kept, nullptr, 2 * b,
-                                                       false, tile_items, &which, s, lbw));
+        // order every group by rank[i+h]: small groups on chip, large ones by radix
+        DNASA_CUDA(ctx, cudaMemsetAsync(cnt + CNT_SEG, 0, 5 * sizeof(unsigned long long), s));
+        {
+            LaunchScope ls_(ctx, PK_SEGSORT, s, 8.0 * ngroups);
+            int gc = (int)std::min<int64_t>(ceil_div(ngroups, 256), (int64_t)ctx->num_sms * 16);
+            k_classify<<<std::max(gc, 1), 256, 0, s>>>(groups, ngroups, seg_max, gtiny, gsmall, gwmid, gmid,
+                                                       glarge, cnt + CNT_SEG);
+        }
+        {
+            LaunchScope ls_(ctx, PK_SEGSORT, s, 24.0 * kept);
+            int gt = (int)std::min<int64_t>(ceil_div(ngroups, 256), (int64_t)ctx->num_sms * 16);
+            k_seg_thread<<<std::max(gt, 1), 256, 0, s>>>(gtiny, cnt + CNT_SEG, keys[0], vals[0]);
+        }
+        if (maxgroup > 8 && seg_max > 8) {
+            LaunchScope ls_(ctx, PK_SEGSORT, s, 0.0);
+            int gw = (int)std::min<int64_t>(ceil_div(ngroups, 8), (int64_t)ctx->num_sms * 32);
+            k_seg_warp<<<std::max(gw, 1), 256, 0, s>>>(gsmall, cnt + CNT_SEG + 1, keys[0], vals[0]);
+        }
+        if (maxgroup > 32 && seg_max > 32) {
+            LaunchScope ls_(ctx, PK_SEGSORT, s, 0.0);
+            int gw = (int)std::min<int64_t>(ceil_div(ngroups, kSegWarpsPerCta), (int64_t)ctx->num_sms * 8);
+            k_seg_warpsm<<<std::max(gw, 1), 32 * kSegWarpsPerCta, 0, s>>>(gwmid, cnt + CNT_SEG + 2,
+                                                                          keys[0], vals[0]);
+        }
+        if (maxgroup > kSegWarpMax && seg_max > kSegWarpMax) {
+            LaunchScope ls_(ctx, PK_SEGSORT, s, 0.0);
+            int gb = (int)std::min<int64_t>(ngroups, (int64_t)ctx->num_sms * 8);
+            k_seg_block<<<std::max(gb, 1), kSegThreads, 0, s>>>(gmid, cnt + CNT_SEG + 3, keys[0], vals[0]);
+        }
+        DNASA_CUDA(ctx, cudaGetLastError());
+        if (maxgroup > seg_max) {
+            DNASA_CUDA(ctx, cudaMemsetAsync(lflags, 0, (size_t)kept, s));
+            {
+                LaunchScope ls_(ctx, PK_SEGSORT, s, 0.0);
+                k_flag_large<<<ctx->num_sms * 2, 256, 0, s>>>(glarge, cnt + CNT_SEG + 4, lflags);
+            }
+            Arena rest = a;
+            DNASA_TRY(compact_flags(ctx, rest, lflags, kept, lidx, cnt + CNT_TMP, s));
+            DNASA_CUDA(ctx, cudaMemcpyAsync(ctx->pinned, cnt + CNT_TMP, 8, cudaMemcpyDeviceToHost, s));
+            DNASA_TRY(check_device_status(ctx, s, "sa_build"));
+            const int64_t m = (int64_t)ctx->pinned[0];
+            unsigned long long *ck[2] = {keys[1], ck2};
+            uint32_t *cv[2] = {vals[1], cv2};
+            int g2 = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(m, 256), (int64_t)ctx->num_sms * 16));
+            {
+                LaunchScope ls_(ctx, PK_SEGSORT, s, 24.0 * m);
+                k_take<<<g2, 256, 0, s>>>(lidx, cnt + CNT_TMP, keys[0], vals[0], ck[0], cv[0]);
+            }
+            int which;
+            DNASA_TRY(radix_sort_pairs<unsigned long long>(ctx, rs, ck, cv, m, nullptr, 2 * b,
+                                                           false, tile_items, &which, s, lbw));
+            {
+                LaunchScope ls_(ctx, PK_SEGSORT, s, 24.0 * m);
+                k_put<<<g2, 256, 0, s>>>(lidx, cnt + CNT_TMP, ck[which], cv[which], keys[0], vals[0]);
+            }
+            DNASA_CUDA(ctx, cudaGetLastError());
+        }
         DNASA_TRY(reset_counters());
         ro.nslots = L[cur ^ 1][0]; ro.npos = L[cur ^ 1][1]; ro.nhead = L[cur ^ 1][2];
-        ro.stage = reinterpret_cast<uint2 *>(keys[which ^ 1]);
+        ro.stage = reinterpret_cast<uint2 *>(keys[1]);   // free again: stage the rank writes
         int tiles = ceil_div(kept, kRrTile);
         {
             LaunchScope ls_(ctx, PK_RERANK, s, 24.0 * kept);
-            k_rerank<false><<<tiles, kRrThreads, sizeof(RerankSmem), s>>>(keys[which], vals[which], L[cur][0], kept,
+            k_rerank<false><<<tiles, kRrThreads, sizeof(RerankSmem), s>>>(keys[0], vals[0], L[cur][0], kept,
                                                          nullptr, h0, ro, rr_status, c->tile_ctr + 32,
                                                          &c->err);
         }
         DNASA_CUDA(ctx, cudaGetLastError());
-        DNASA_TRY(apply_ranks(kept, which ^ 1));
+        DNASA_TRY(apply_ranks(kept, 1));
         DNASA_CUDA(ctx, cudaGetLastError());
         DNASA_TRY(read_counters(&kept, &ngroups, &maxgroup));
         cur ^= 1;
@@ -657,7 +999,17 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
         tr.rounds = round;
         if (round < 64) tr.active[round] = kept;
     }
+    if (isa_out)   // every rank is now final: the rank array is the inverse SA
+        DNASA_CUDA(ctx, cudaMemcpyAsync(isa_out, rank, (size_t)N * 4, cudaMemcpyDeviceToDevice, s));
     return check_device_status(ctx, s, "sa_build");
+}
+
+int fragment_ids(dnasa_ctx *ctx, const TextDesc &t, uint32_t *fid, cudaStream_t s) {
+    int warps = ceil_div(t.N, 32 * 8);
+    LaunchScope ls_(ctx, PK_OTHER, s, 4.0 * t.N);
+    k_fid<<<std::max(1, ceil_div(warps, 8)), 256, 0, s>>>(t, fid);
+    DNASA_CUDA(ctx, cudaGetLastError());
+    return DNASA_OK;
 }
 
 int widen_u32_to_i64(dnasa_ctx *ctx, const uint32_t *a, int64_t n, int64_t *b, cudaStream_t s) {
