@@ -74,7 +74,10 @@ typedef struct {
                                   8 (default) or 1 */
     int32_t seg_max;           /* largest group a doubling round sorts on chip (8..2048,
                                   default 256); larger groups go through radix passes */
-    int32_t reserved;
+    int32_t pack_position;     /* initial sort: 0 (default) packs the suffix position under
+                                  the key and sorts one 64-bit word per suffix when the
+                                  key can still hold enough symbols; -1 never packs and
+                                  sorts (key, position) pairs */
 } dnasa_opts;
 
 /* One suffix-prefix overlap: the last L bases of fragment j equal the first L
@@ -88,7 +91,7 @@ typedef struct {
     int32_t rounds;            /* doubling rounds run after the initial sort */
     int32_t finished_direct;   /* 1 if the direct-comparison finisher ran */
     int32_t h0;                /* symbols in the initial packed key */
-    int32_t reserved;
+    int32_t pack_bits;         /* position bits packed under the initial key (0: pairs) */
     int64_t active[64];        /* unsorted suffixes after the initial sort and each round */
 } dnasa_trace;
 

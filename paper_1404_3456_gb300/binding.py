@@ -33,12 +33,13 @@ class DnasaError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("digit_bits", ctypes.c_int32), ("tile_items", ctypes.c_int32),
                 ("finish_threshold", ctypes.c_int64), ("max_rounds", ctypes.c_int32),
-                ("lookback", ctypes.c_int32), ("seg_max", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("lookback", ctypes.c_int32), ("seg_max", ctypes.c_int32),
+                ("pack_position", ctypes.c_int32)]
 
 
 class Trace(ctypes.Structure):
     _fields_ = [("rounds", ctypes.c_int32), ("finished_direct", ctypes.c_int32),
-                ("h0", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("h0", ctypes.c_int32), ("pack_bits", ctypes.c_int32),
                 ("active", ctypes.c_int64 * 64)]
 
 
@@ -161,7 +162,7 @@ class Context:
         tr = Trace()
         self.check(lib().dnasa_get_trace(self.handle, ctypes.byref(tr)))
         return dict(rounds=tr.rounds, finished_direct=tr.finished_direct, h0=tr.h0,
-                    active=list(tr.active[: tr.rounds + 1]))
+                    pack_bits=tr.pack_bits, active=list(tr.active[: tr.rounds + 1]))
 
     def profile(self, enable: bool = True):
         """Start (or stop) recording CUDA events around every kernel launch."""
@@ -190,8 +191,10 @@ class Context:
             pass
 
 
-def make_opts(digit_bits=0, tile_items=0, finish_threshold=0, max_rounds=0, lookback=0, seg_max=0):
-    return Opts(digit_bits, tile_items, finish_threshold, max_rounds, lookback, seg_max, 0)
+def make_opts(digit_bits=0, tile_items=0, finish_threshold=0, max_rounds=0, lookback=0, seg_max=0,
+              pack_position=0):
+    return Opts(digit_bits, tile_items, finish_threshold, max_rounds, lookback, seg_max,
+                pack_position)
 
 
 # ---------------------------------------------------------------- entry points

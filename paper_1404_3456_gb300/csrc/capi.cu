@@ -222,6 +222,8 @@ int sa_build(dnasa_ctx *ctx, const uint64_t *packed, const int64_t *toff, int64_
         return fail(ctx, DNASA_INVALID_ARG, "sa_build: lookback must be 0, 1 or 8");
     if (opts && opts->seg_max != 0 && (opts->seg_max < 8 || opts->seg_max > 2048))
         return fail(ctx, DNASA_INVALID_ARG, "sa_build: seg_max must be 0 or in [8, 2048]");
+    if (opts && opts->pack_position != 0 && opts->pack_position != -1)
+        return fail(ctx, DNASA_INVALID_ARG, "sa_build: pack_position must be 0 or -1");
     cudaSetDevice(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
     TextDesc t = one_instance(packed, toff, n_reads, N);

@@ -138,11 +138,12 @@ struct RadixScratch {
 };
 size_t radix_scratch_bytes(int64_t n_max, int key_bits, int tile_items);
 RadixScratch radix_scratch_take(Arena &a, int64_t n_max, int key_bits, int tile_items);
-// lbw = look-back loads in flight per digit (1 or 8).
+// lbw = look-back loads in flight per digit (1 or 8).  The sort is on key bits
+// [lo_bit, lo_bit + key_bits).
 template <typename K>
 int radix_sort_pairs(dnasa_ctx *ctx, const RadixScratch &rs, K *keys[2], uint32_t *vals[2],
                      int64_t n_host, const unsigned long long *d_n, int key_bits, bool hist_ready,
-                     int tile_items, int *which, cudaStream_t s, int lbw = 8);
+                     int tile_items, int *which, cudaStream_t s, int lbw = 8, int lo_bit = 0);
 // Launch of the histogram kernel alone (used when a producer cannot fuse it).
 int radix_tile_default();
 
@@ -181,9 +182,10 @@ int overlap_impl(dnasa_ctx *ctx, const TextDesc &t, const uint32_t *sa32, const 
                  int32_t min_overlap, dnasa_edge *edges, int64_t cap, int64_t *n_edges,
                  uint8_t *contained, cudaStream_t s, const uint32_t *isa = nullptr);
 int widen_u32_to_i64(dnasa_ctx *ctx, const uint32_t *a, int64_t n, int64_t *b, cudaStream_t s);
-// Symbols in the initial packed key for an N-symbol text of n_inst instances
-// (and the instance bits).
-int h0_for(int64_t N, int n_inst, int *inst_bits);
+// Symbols in the initial packed key for an N-symbol text of n_inst instances,
+// the instance bits, and the position bits packed under the key (0: none;
+// pack_bits == nullptr asks for the unpacked key).
+int h0_for(int64_t N, int n_inst, int *inst_bits, int *pack_bits);
 int pack_impl(dnasa_ctx *ctx, const uint8_t *text, int64_t N, uint64_t *packed, int64_t *toff,
               int64_t toff_cap, int64_t *n_reads, cudaStream_t s);
 

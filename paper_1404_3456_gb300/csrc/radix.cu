@@ -65,7 +65,8 @@ __device__ __forceinline__ uint32_t match_digit(uint32_t d, uint32_t vmask) {
 template <typename K>
 __global__ void __launch_bounds__(kThreads) k_hist(const K *__restrict__ keys, int64_t n_host,
                                                    const unsigned long long *__restrict__ d_n,
-                                                   int passes, uint32_t *__restrict__ ghist) {
+                                                   int passes, uint32_t *__restrict__ ghist,
+                                                   int lo_bit = 0) {
     __shared__ uint32_t sh[8 * kRadix];
     for (int i = threadIdx.x; i < passes * kRadix; i += kThreads) sh[i] = 0;
     __syncthreads();
@@ -76,7 +77,8 @@ __global__ void __launch_bounds__(kThreads) k_hist(const K *__restrict__ keys, i
     (void)lane;
     for (int64_t i = warp_global * 32 + lane; i < n; i += nwarps * 32) {
         K k = keys[i];
-        for (int p = 0; p < passes; ++p) atomicAdd(&sh[p * kRadix + digit_of(k, p * kRadixBits)], 1u);
+        for (int p = 0; p < passes; ++p)
+            atomicAdd(&sh[p * kRadix + digit_of(k, lo_bit + p * kRadixBits)], 1u);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < passes * kRadix; i += kThreads) {
@@ -389,10 +391,11 @@ static int lb_prepare(dnasa_ctx *ctx, size_t words, cudaStream_t s, unsigned lon
 template <typename K>
 int radix_sort_pairs(dnasa_ctx *ctx, const RadixScratch &rs, K *keys[2], uint32_t *vals[2],
                      int64_t n_host, const unsigned long long *d_n, int key_bits, bool hist_ready,
-                     int tile_items, int *which, cudaStream_t s, int lbw) {
+                     int tile_items, int *which, cudaStream_t s, int lbw, int lo_bit) {
     *which = 0;
     if (n_host <= 0) return DNASA_OK;
-    if (key_bits > (int)(8 * sizeof(K))) return fail(ctx, DNASA_INVALID_ARG, "radix: key_bits");
+    if (lo_bit < 0 || lo_bit + key_bits > (int)(8 * sizeof(K)))
+        return fail(ctx, DNASA_INVALID_ARG, "radix: key bit range");
     const int passes = (key_bits + kRadixBits - 1) / kRadixBits;
     if (passes > 8) return fail(ctx, DNASA_INVALID_ARG, "radix: too many passes");
     const int items = items_for_tile(tile_items);
@@ -405,7 +408,7 @@ int radix_sort_pairs(dnasa_ctx *ctx, const RadixScratch &rs, K *keys[2], uint32_
         if (grid < 1) grid = 1;
         {
             LaunchScope ls_(ctx, PK_HIST, s, (double)n_host * sizeof(K));
-            k_hist<K><<<grid, kThreads, 0, s>>>(keys[0], n_host, d_n, passes, rs.hist);
+            k_hist<K><<<grid, kThreads, 0, s>>>(keys[0], n_host, d_n, passes, rs.hist, lo_bit);
         }
         DNASA_CUDA(ctx, cudaGetLastError());
     }
@@ -430,9 +433,9 @@ int radix_sort_pairs(dnasa_ctx *ctx, const RadixScratch &rs, K *keys[2], uint32_
 #define DNASA_PASS(IT, HV)                                                                    \
     e = lbw == 1 ? launch_pass<K, IT, HV, 1>(tiles, s, kin, vin, kout, vout, rs.hist + p * kRadix,  \
                                              status, ctx->ctrl->tile_ctr + p, n_host, d_n,          \
-                                             p * kRadixBits, epoch, &ctx->ctrl->err)                \
+                                             lo_bit + p * kRadixBits, epoch, &ctx->ctrl->err)       \
                  : launch_pass<K, IT, HV, 8>(tiles, s, kin, vin, kout, vout, rs.hist + p * kRadix, status, \
-                               ctx->ctrl->tile_ctr + p, n_host, d_n, p * kRadixBits, epoch,  \
+                               ctx->ctrl->tile_ctr + p, n_host, d_n, lo_bit + p * kRadixBits, epoch, \
                                &ctx->ctrl->err)
         if (has_vals) {
             if (items == 8) DNASA_PASS(8, true);
@@ -453,11 +456,11 @@ int radix_sort_pairs(dnasa_ctx *ctx, const RadixScratch &rs, K *keys[2], uint32_
 
 template int radix_sort_pairs<uint32_t>(dnasa_ctx *, const RadixScratch &, uint32_t *[2],
                                         uint32_t *[2], int64_t, const unsigned long long *, int,
-                                        bool, int, int *, cudaStream_t, int);
+                                        bool, int, int *, cudaStream_t, int, int);
 template int radix_sort_pairs<unsigned long long>(dnasa_ctx *, const RadixScratch &,
                                                   unsigned long long *[2], uint32_t *[2], int64_t,
                                                   const unsigned long long *, int, bool, int,
-                                                  int *, cudaStream_t, int);
+                                                  int *, cudaStream_t, int, int);
 
 // Histogram accumulation entry used by fused producers: nothing here; the
 // producer kernels call radix_digit_count() below.

@@ -30,7 +30,10 @@ namespace {
 constexpr int kInitThreads = 256;
 constexpr int kInitItems = 8;
 
+// pb > 0: the position is packed under the key, (key << pb) | p, and no value
+// array is written (a keys-only sort then moves 8 instead of 12 bytes per item).
 __global__ void __launch_bounds__(kInitThreads) k_init_keys(TextDesc t, int h0, int inst_shift,
+                                                            int pb,
                                                             unsigned long long *__restrict__ keys,
                                                             uint32_t *__restrict__ vals) {
     const int lane = threadIdx.x & 31;
@@ -55,8 +58,12 @@ __global__ void __launch_bounds__(kInitThreads) k_init_keys(TextDesc t, int h0, 
         if (lc < h0) kmer &= ~((1ull << (2 * (h0 - lc))) - 1ull);
         unsigned long long key = ((unsigned long long)kmer << 5) | (unsigned long long)lc;
         if (t.n_inst > 1) key |= (unsigned long long)inst << inst_shift;
-        keys[p] = key;
-        vals[p] = (uint32_t)p;
+        if (pb) {
+            keys[p] = (key << pb) | (unsigned long long)p;
+        } else {
+            keys[p] = key;
+            vals[p] = (uint32_t)p;
+        }
     }
 }
 
@@ -89,6 +96,7 @@ struct RerankOut {
     uint2 *stage;       // [N]: bucket b's (pos, rank) pairs start at b << bshift
     uint32_t *bucket_fill;   // [kMaxBuckets]
     int bshift;
+    int pb;             // round 0 only: keys hold (key << pb) | position, no value array
 };
 
 // Shared memory of one rerank tile (dynamic, > 48 KB).
@@ -134,12 +142,15 @@ __global__ void __launch_bounds__(kRrThreads) k_rerank(
     const int tile_n = (int)min((int64_t)kRrTile, n - base);
 
     // ---- striped, coalesced loads
+    const int pb = ROUND0 ? o.pb : 0;
     for (int i = tid; i < tile_n + 2; i += kRrThreads) {
         int64_t j = base - 1 + i;
-        S.u.k[i] = (j >= 0 && j < n) ? keys[j] : 0ull;
+        unsigned long long w = (j >= 0 && j < n) ? keys[j] : 0ull;
+        S.u.k[i] = w >> pb;
+        if (pb && i >= 1 && i <= tile_n) S.v[i - 1] = (uint32_t)(w & ((1ull << pb) - 1ull));
     }
     for (int i = tid; i < tile_n; i += kRrThreads) {
-        S.v[i] = vals[base + i];
+        if (!pb) S.v[i] = vals[base + i];
         if (!ROUND0) S.sl[i] = slots[base + i];
     }
     __syncthreads();
@@ -743,15 +754,20 @@ __global__ void k_widen(const uint32_t *__restrict__ a, int64_t n, int64_t *__re
 // unsorted (4^h0 >= 32 * symbols per instance: expected colliding pairs at most
 // N/64), then as many as fit in the same number of 8-bit passes: the key is
 // [instance | 2*h0 bits of bases | 5 bits of lc], and its passes are the cost.
-int h0_for(int64_t N, int n_inst, int *inst_bits) {
+int h0_for(int64_t N, int n_inst, int *inst_bits, int *pack_bits) {
     int ib = n_inst > 1 ? bits_for((uint64_t)(n_inst - 1)) : 0;
     *inst_bits = ib;
     double per = (double)N / (double)(n_inst > 0 ? n_inst : 1);
     int hmin = (int)std::ceil((std::log2(std::max(per, 2.0)) + 5.0) / 2.0);
     hmin = std::max(8, std::min(hmin, 29));
     int passes = (ib + 2 * hmin + 5 + 7) / 8;
-    int h0 = (8 * passes - 5 - ib) / 2;
-    return std::max(1, std::min(h0, 29));
+    int h0 = std::max(1, std::min((8 * passes - 5 - ib) / 2, 29));
+    // the position fits under a key of at least hmin bases: sort one word per suffix
+    const int pb = bits_for((uint64_t)(N - 1));
+    const int hp = std::min((64 - pb - 5 - ib) / 2, h0);
+    if (!pack_bits) return h0;
+    *pack_bits = hp >= hmin ? pb : 0;
+    return hp >= hmin ? hp : h0;
 }
 
 int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_opts *opts_in,
@@ -766,8 +782,12 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
     // largest group a doubling round sorts on chip (larger ones: radix passes)
     const int seg_max = opts.seg_max == 0 ? 256 : std::max(8, std::min(opts.seg_max, kSegMax));
     const int64_t N = t.N;
-    int ib;
-    const int h0 = h0_for(N, t.n_inst, &ib);
+    int ib, pb;
+    int h0 = h0_for(N, t.n_inst, &ib, &pb);
+    if (opts.pack_position < 0 && pb) {
+        pb = 0;
+        h0 = h0_for(N, t.n_inst, &ib, nullptr);
+    }
     const int inst_shift = 2 * h0 + 5;
     const int key_bits0 = inst_shift + ib;
     const int b = bits_for((uint64_t)(N - 1));
@@ -823,6 +843,7 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
     dnasa_trace &tr = ctx->trace;
     memset(&tr, 0, sizeof(tr));
     tr.h0 = h0;
+    tr.pack_bits = pb;
 
     auto reset_counters = [&]() -> int {
         DNASA_CUDA(ctx, cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * 4, s));
@@ -864,19 +885,21 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
     ro.maxgroup = cnt + CNT_MAXGROUP;
     ro.bucket_fill = bucket_fill;
     ro.bshift = bshift;
+    ro.pb = pb;
 
     // ---- round 0: initial keys, sort, rerank
     {
         int warps = ceil_div(N, 32 * kInitItems);
         {
-            LaunchScope ls_(ctx, PK_INIT, s, 12.25 * N);
-            k_init_keys<<<ceil_div(warps, kInitThreads / 32), kInitThreads, 0, s>>>(t, h0, inst_shift,
+            LaunchScope ls_(ctx, PK_INIT, s, (pb ? 8.25 : 12.25) * N);
+            k_init_keys<<<ceil_div(warps, kInitThreads / 32), kInitThreads, 0, s>>>(t, h0, inst_shift, pb,
                                                                                   keys[0], vals[0]);
         }
         DNASA_CUDA(ctx, cudaGetLastError());
         int which;
-        DNASA_TRY(radix_sort_pairs<unsigned long long>(ctx, rs, keys, vals, N, nullptr, key_bits0,
-                                                       false, tile_items, &which, s, lbw));
+        uint32_t *novals[2] = {nullptr, nullptr};
+        DNASA_TRY(radix_sort_pairs<unsigned long long>(ctx, rs, keys, pb ? novals : vals, N, nullptr,
+                                                       key_bits0, false, tile_items, &which, s, lbw, pb));
         DNASA_TRY(reset_counters());
         ro.nslots = L[0][0]; ro.npos = L[0][1]; ro.nhead = L[0][2];
         ro.stage = reinterpret_cast<uint2 *>(keys[which ^ 1]);   // the free key buffer

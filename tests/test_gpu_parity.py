@@ -130,6 +130,29 @@ def test_sa_finisher_and_doubling_agree(ctx, finish):
     assert ctx.trace()["finished_direct"] == (1 if finish > 0 else 0)
 
 
+@pytest.mark.parametrize("pack", [0, -1])
+@pytest.mark.parametrize("seed,n_reads,lo,hi", [(21, 1, 300_001, 300_001), (22, 700, 1, 900)])
+def test_sa_packed_and_pair_initial_sort(ctx, pack, seed, n_reads, lo, hi):
+    """The initial sort on one packed (key, position) word and on (key, position)
+    pairs: the same suffix array; the trace says which form ran."""
+    rng = np.random.default_rng(seed)
+    t = random_text(rng, n_reads, lo, hi)
+    sa = gpu_sa(ctx, t, opts=B().make_opts(pack_position=pack))[0]
+    assert np.array_equal(sa.cpu().numpy().astype(np.int64), oracle.suffix_array(t))
+    pb = ctx.trace()["pack_bits"]
+    if pack < 0:
+        assert pb == 0
+    else:
+        assert pb == int(t.size - 1).bit_length()
+
+
+def test_sa_pack_position_rejected(ctx):
+    rng = np.random.default_rng(23)
+    t = random_text(rng, 3, 10, 20)
+    with pytest.raises(B().DnasaError):
+        gpu_sa(ctx, t, opts=B().make_opts(pack_position=1))
+
+
 @pytest.mark.parametrize("tile", [2048, 3840, 5120])
 def test_sa_tile_sizes(ctx, tile):
     rng = np.random.default_rng(9)
