@@ -480,18 +480,27 @@ __global__ void __launch_bounds__(kFinThreads) k_finish(const uint2 *__restrict_
 // memory (bitonic networks); only the members of larger groups go through the
 // global radix sort.  Each item is then read and written once instead of once
 // per radix pass.
-constexpr int kSegMax = 2048;
-constexpr int kSegWarpMax = 256;   // one warp, shared-memory slice
-constexpr int kSegThreads = 256;
+constexpr int kSegMax = 16384;     // largest group sorted on chip (one CTA, shared memory)
+constexpr int kSegWarpMax = 256;   // one warp, registers
+constexpr int kSegThreads = 512;
 
-__device__ __forceinline__ bool kv_less(unsigned long long ka, uint32_t va, unsigned long long kb,
-                                        uint32_t vb) {
-    return ka < kb || (ka == kb && va < vb);
+// Inside one group every key has the same high part (the head rank), so a
+// member is ordered by its low key part rank[i+h] and, to make every word
+// distinct, its position: one 64-bit word (rank[i+h] << 32 | position) per
+// member, compared as an integer.
+__device__ __forceinline__ unsigned long long seg_word(unsigned long long k, uint32_t v,
+                                                       unsigned long long rmask) {
+    return ((k & rmask) << 32) | v;
+}
+
+__device__ __forceinline__ unsigned long long shfl_xor_u64(unsigned long long x, int m) {
+    uint32_t lo = __shfl_xor_sync(0xffffffffu, (uint32_t)x, m);
+    uint32_t hi = __shfl_xor_sync(0xffffffffu, (uint32_t)(x >> 32), m);
+    return ((unsigned long long)hi << 32) | lo;
 }
 
 // Splits the group list into five lists by size (<= 8, <= 32, <= kSegWarpMax,
-// <= kSegMax, larger; nothing above seg_max is sorted on chip), one atomic per
-// warp and list.
+// <= seg_max, larger), one atomic per warp and list.
 __global__ void __launch_bounds__(256) k_classify(const uint2 *__restrict__ groups, int64_t ng,
                                                   int seg_max, uint2 *__restrict__ tiny,
                                                   uint2 *__restrict__ small, uint2 *__restrict__ wmid,
@@ -521,148 +530,161 @@ __global__ void __launch_bounds__(256) k_classify(const uint2 *__restrict__ grou
 // Groups of at most 8 members: one thread each, insertion sort in registers.
 __global__ void __launch_bounds__(256) k_seg_thread(const uint2 *__restrict__ groups,
                                                     const unsigned long long *__restrict__ d_ng,
-                                                    unsigned long long *__restrict__ keys,
+                                                    int b, unsigned long long *__restrict__ keys,
                                                     uint32_t *__restrict__ vals) {
     const int64_t ng = (int64_t)*d_ng;
+    const unsigned long long rmask = (1ull << b) - 1ull;
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ng;
          g += (int64_t)gridDim.x * blockDim.x) {
         const uint2 gs = groups[g];
         const int n = (int)gs.y;   // 2..8
-        unsigned long long k[8];
-        uint32_t v[8];
+        const unsigned long long hi = keys[gs.x] & ~rmask;
+        unsigned long long w[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i)
-            if (i < n) { k[i] = keys[gs.x + i]; v[i] = vals[gs.x + i]; }
+            w[i] = i < n ? seg_word(keys[gs.x + i], vals[gs.x + i], rmask) : ~0ull;
 #pragma unroll
         for (int i = 1; i < 8; ++i) {
-            if (i < n) {
 #pragma unroll
-                for (int j = i; j > 0; --j) {
-                    if (kv_less(k[j], v[j], k[j - 1], v[j - 1])) {
-                        unsigned long long tk = k[j]; k[j] = k[j - 1]; k[j - 1] = tk;
-                        uint32_t tv = v[j]; v[j] = v[j - 1]; v[j - 1] = tv;
-                    }
-                }
+            for (int j = i; j > 0; --j) {
+                unsigned long long a = w[j - 1], c = w[j];
+                w[j - 1] = min(a, c);
+                w[j] = max(a, c);
             }
         }
 #pragma unroll
         for (int i = 0; i < 8; ++i)
-            if (i < n) { keys[gs.x + i] = k[i]; vals[gs.x + i] = v[i]; }
+            if (i < n) {
+                keys[gs.x + i] = hi | (w[i] >> 32);
+                vals[gs.x + i] = (uint32_t)w[i];
+            }
     }
 }
 
+// Bitonic network over 32 * E words held E per lane (word i = e * 32 + lane):
+// strides below 32 exchange across lanes by shuffles, larger ones inside a lane.
+// With E == 1 only the first n2 lanes take part (n2 a power of two, 2..32);
+// with E > 1 all 32 * E words do.
+template <int E>
+__device__ __forceinline__ void warp_bitonic(unsigned long long (&w)[E], int lane, int n2) {
+    const int lim = E == 1 ? n2 : 32 * E;
+#pragma unroll
+    for (int size = 2; size <= 32 * E; size <<= 1) {
+        if (size > lim) continue;
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            if (stride >= 32) {
+                const int es = stride >> 5;
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    if ((e & es) == 0) {
+                        const bool asc = ((e * 32) & size) == 0;   // size >= 64: lane bits are below it
+                        unsigned long long a = w[e], c = w[e | es];
+                        unsigned long long lo = min(a, c), hi = max(a, c);
+                        w[e] = asc ? lo : hi;
+                        w[e | es] = asc ? hi : lo;
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < E; ++e) {
+                    unsigned long long o = shfl_xor_u64(w[e], stride);
+                    const bool keep_min = ((lane & stride) == 0) == (((e * 32 + lane) & size) == 0);
+                    w[e] = keep_min ? min(w[e], o) : max(w[e], o);
+                }
+            }
+        }
+    }
+}
+
+template <int E>
+__device__ __forceinline__ void warp_sort_group(uint2 gs, int lane, int n2, unsigned long long rmask,
+                                                unsigned long long *__restrict__ keys,
+                                                uint32_t *__restrict__ vals) {
+    const int n = (int)gs.y;
+    const unsigned long long hi = keys[gs.x] & ~rmask;
+    unsigned long long w[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int i = e * 32 + lane;
+        w[e] = i < n ? seg_word(keys[gs.x + i], vals[gs.x + i], rmask) : ~0ull;
+    }
+    warp_bitonic<E>(w, lane, n2);
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int i = e * 32 + lane;
+        if (i < n) {
+            keys[gs.x + i] = hi | (w[e] >> 32);
+            vals[gs.x + i] = (uint32_t)w[e];
+        }
+    }
+}
+
+// Groups of 9..kSegWarpMax members: one warp per group, the words in registers
+// (one per lane up to 32 members; 2, 4 or 8 per lane above).
 __global__ void __launch_bounds__(256) k_seg_warp(const uint2 *__restrict__ groups,
-                                                  const unsigned long long *__restrict__ d_ng,
+                                                  const unsigned long long *__restrict__ d_ng, int b,
                                                   unsigned long long *__restrict__ keys,
                                                   uint32_t *__restrict__ vals) {
     const int lane = threadIdx.x & 31;
     const int64_t ng = (int64_t)*d_ng;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < ng; g += nw) {
-        const uint2 gs = groups[g];                    // 2..32 members
-        const int n = (int)gs.y;
-        int n2 = 2;
-        while (n2 < n) n2 <<= 1;                       // network only as wide as the group
-        unsigned long long k = lane < n ? keys[gs.x + lane] : ~0ull;
-        uint32_t v = lane < n ? vals[gs.x + lane] : ~0u;
-        for (int size = 2; size <= n2; size <<= 1) {
-            for (int stride = size >> 1; stride > 0; stride >>= 1) {
-                unsigned long long ok = __shfl_xor_sync(0xffffffffu, k, stride);
-                uint32_t ov = __shfl_xor_sync(0xffffffffu, v, stride);
-                bool keep_min = ((lane & stride) == 0) == ((lane & size) == 0);
-                bool mine_less = kv_less(k, v, ok, ov);
-                if (keep_min != mine_less) { k = ok; v = ov; }
-            }
-        }
-        if (lane < n) {
-            keys[gs.x + lane] = k;
-            vals[gs.x + lane] = v;
-        }
-    }
-}
-
-// 33..kSegWarpMax members: one warp per group, bitonic network over a private
-// shared-memory slice (warp-level synchronisation only).
-constexpr int kSegWarpsPerCta = 8;
-__global__ void __launch_bounds__(32 * kSegWarpsPerCta) k_seg_warpsm(
-    const uint2 *__restrict__ groups, const unsigned long long *__restrict__ d_ng,
-    unsigned long long *__restrict__ keys, uint32_t *__restrict__ vals) {
-    __shared__ unsigned long long sk_all[kSegWarpsPerCta][kSegWarpMax];
-    __shared__ uint32_t sv_all[kSegWarpsPerCta][kSegWarpMax];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    unsigned long long *sk = sk_all[w];
-    uint32_t *sv = sv_all[w];
-    const int64_t ng = (int64_t)*d_ng;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const unsigned long long rmask = (1ull << b) - 1ull;
     for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < ng; g += nw) {
         const uint2 gs = groups[g];
         const int n = (int)gs.y;
-        int n2 = 64;
-        while (n2 < n) n2 <<= 1;
-        for (int i = lane; i < n2; i += 32) {
-            sk[i] = i < n ? keys[gs.x + i] : ~0ull;
-            sv[i] = i < n ? vals[gs.x + i] : ~0u;
-        }
-        __syncwarp();
-        for (int size = 2; size <= n2; size <<= 1) {
-            for (int stride = size >> 1; stride > 0; stride >>= 1) {
-                for (int i = lane; i < n2; i += 32) {
-                    int ixj = i ^ stride;
-                    if (ixj > i) {
-                        bool asc = (i & size) == 0;
-                        if (asc == kv_less(sk[ixj], sv[ixj], sk[i], sv[i])) {
-                            unsigned long long tk = sk[i]; sk[i] = sk[ixj]; sk[ixj] = tk;
-                            uint32_t tv = sv[i]; sv[i] = sv[ixj]; sv[ixj] = tv;
-                        }
-                    }
-                }
-                __syncwarp();
-            }
-        }
-        for (int i = lane; i < n; i += 32) {
-            keys[gs.x + i] = sk[i];
-            vals[gs.x + i] = sv[i];
-        }
-        __syncwarp();
+        int n2 = 2;
+        while (n2 < n) n2 <<= 1;   // network only as wide as the group
+        if (n2 <= 32) warp_sort_group<1>(gs, lane, n2, rmask, keys, vals);
+        else if (n2 <= 64) warp_sort_group<2>(gs, lane, n2, rmask, keys, vals);
+        else if (n2 <= 128) warp_sort_group<4>(gs, lane, n2, rmask, keys, vals);
+        else warp_sort_group<8>(gs, lane, n2, rmask, keys, vals);
     }
 }
 
+// Groups of kSegWarpMax+1 .. kSegMax members: one CTA per group, bitonic network
+// over the words in dynamic shared memory (cap words, a power of two >= every
+// group of the list), each thread taking whole compare-exchange pairs.
 __global__ void __launch_bounds__(kSegThreads) k_seg_block(const uint2 *__restrict__ groups,
                                                            const unsigned long long *__restrict__ d_ng,
+                                                           int b, int cap,
                                                            unsigned long long *__restrict__ keys,
-                                                           uint32_t *__restrict__ vals) {
-    __shared__ unsigned long long sk[kSegMax];
-    __shared__ uint32_t sv[kSegMax];
+                                                           uint32_t *__restrict__ vals,
+                                                           uint32_t *err) {
+    extern __shared__ unsigned long long sw[];
     const int64_t ng = (int64_t)*d_ng;
+    const unsigned long long rmask = (1ull << b) - 1ull;
     for (int64_t g = blockIdx.x; g < ng; g += gridDim.x) {
-        const uint2 gs = groups[g];                    // kSegWarpMax+1..kSegMax members
+        const uint2 gs = groups[g];
         const int n = (int)gs.y;
         int n2 = 512;
         while (n2 < n) n2 <<= 1;
-        for (int i = threadIdx.x; i < n2; i += kSegThreads) {
-            sk[i] = i < n ? keys[gs.x + i] : ~0ull;
-            sv[i] = i < n ? vals[gs.x + i] : ~0u;
+        if (n2 > cap) {   // the list holds only groups that fit: never taken
+            if (threadIdx.x == 0) atomicOr(err, DERR_BOUNDS);
+            continue;
         }
+        const unsigned long long hi = keys[gs.x] & ~rmask;
+        for (int i = threadIdx.x; i < n2; i += kSegThreads)
+            sw[i] = i < n ? seg_word(keys[gs.x + i], vals[gs.x + i], rmask) : ~0ull;
         __syncthreads();
         for (int size = 2; size <= n2; size <<= 1) {
             for (int stride = size >> 1; stride > 0; stride >>= 1) {
-                for (int i = threadIdx.x; i < n2; i += kSegThreads) {
-                    int ixj = i ^ stride;
-                    if (ixj > i) {
-                        bool asc = (i & size) == 0;
-                        bool hi_less = kv_less(sk[ixj], sv[ixj], sk[i], sv[i]);
-                        if (asc == hi_less) {   // ascending: smaller first; descending: larger first
-                            unsigned long long tk = sk[i]; sk[i] = sk[ixj]; sk[ixj] = tk;
-                            uint32_t tv = sv[i]; sv[i] = sv[ixj]; sv[ixj] = tv;
-                        }
+                for (int p = threadIdx.x; p < (n2 >> 1); p += kSegThreads) {
+                    const int i = ((p & ~(stride - 1)) << 1) | (p & (stride - 1));
+                    const int j = i | stride;
+                    const bool asc = (i & size) == 0;
+                    unsigned long long a = sw[i], c = sw[j];
+                    if (asc ? a > c : a < c) {
+                        sw[i] = c;
+                        sw[j] = a;
                     }
                 }
                 __syncthreads();
             }
         }
         for (int i = threadIdx.x; i < n; i += kSegThreads) {
-            keys[gs.x + i] = sk[i];
-            vals[gs.x + i] = sv[i];
+            keys[gs.x + i] = hi | (sw[i] >> 32);
+            vals[gs.x + i] = (uint32_t)sw[i];
         }
         __syncthreads();
     }
@@ -780,7 +802,7 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
     const int max_rounds = opts.max_rounds > 0 ? std::min(opts.max_rounds, 63) : 63;
     const int lbw = opts.lookback == 1 ? 1 : 8;
     // largest group a doubling round sorts on chip (larger ones: radix passes)
-    const int seg_max = opts.seg_max == 0 ? 256 : std::max(8, std::min(opts.seg_max, kSegMax));
+    const int seg_max = opts.seg_max == 0 ? kSegMax : std::max(8, std::min(opts.seg_max, kSegMax));
     const int64_t N = t.N;
     int ib, pb;
     int h0 = h0_for(N, t.n_inst, &ib, &pb);
@@ -833,6 +855,9 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
     static const cudaError_t smem_set = [] {
         cudaError_t e = cudaFuncSetAttribute(k_rerank<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)sizeof(RerankSmem));
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(k_seg_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kSegMax * 8);
         if (e != cudaSuccess) return e;
         return cudaFuncSetAttribute(k_rerank<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)sizeof(RerankSmem));
@@ -957,23 +982,23 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
         {
             LaunchScope ls_(ctx, PK_SEGSORT, s, 24.0 * kept);
             int gt = (int)std::min<int64_t>(ceil_div(ngroups, 256), (int64_t)ctx->num_sms * 16);
-            k_seg_thread<<<std::max(gt, 1), 256, 0, s>>>(gtiny, cnt + CNT_SEG, keys[0], vals[0]);
+            k_seg_thread<<<std::max(gt, 1), 256, 0, s>>>(gtiny, cnt + CNT_SEG, b, keys[0], vals[0]);
         }
-        if (maxgroup > 8 && seg_max > 8) {
+        for (int cls = 1; cls <= 2; ++cls) {   // 9..32 and 33..kSegWarpMax members: a warp each
+            if (maxgroup <= (cls == 1 ? 8 : 32) || seg_max <= (cls == 1 ? 8 : 32)) break;
             LaunchScope ls_(ctx, PK_SEGSORT, s, 0.0);
-            int gw = (int)std::min<int64_t>(ceil_div(ngroups, 8), (int64_t)ctx->num_sms * 32);
-            k_seg_warp<<<std::max(gw, 1), 256, 0, s>>>(gsmall, cnt + CNT_SEG + 1, keys[0], vals[0]);
-        }
-        if (maxgroup > 32 && seg_max > 32) {
-            LaunchScope ls_(ctx, PK_SEGSORT, s, 0.0);
-            int gw = (int)std::min<int64_t>(ceil_div(ngroups, kSegWarpsPerCta), (int64_t)ctx->num_sms * 8);
-            k_seg_warpsm<<<std::max(gw, 1), 32 * kSegWarpsPerCta, 0, s>>>(gwmid, cnt + CNT_SEG + 2,
-                                                                          keys[0], vals[0]);
+            int gw = (int)std::min<int64_t>(ceil_div(ngroups, 8), (int64_t)ctx->num_sms * 16);
+            k_seg_warp<<<std::max(gw, 1), 256, 0, s>>>(cls == 1 ? gsmall : gwmid, cnt + CNT_SEG + cls, b,
+                                                       keys[0], vals[0]);
         }
         if (maxgroup > kSegWarpMax && seg_max > kSegWarpMax) {
+            int cap = 512;
+            while (cap < std::min<int64_t>(maxgroup, seg_max)) cap <<= 1;
+            const int per_sm = std::max(1, std::min(4, (200 << 10) / (cap * 8)));
             LaunchScope ls_(ctx, PK_SEGSORT, s, 0.0);
-            int gb = (int)std::min<int64_t>(ngroups, (int64_t)ctx->num_sms * 8);
-            k_seg_block<<<std::max(gb, 1), kSegThreads, 0, s>>>(gmid, cnt + CNT_SEG + 3, keys[0], vals[0]);
+            int gb = (int)std::min<int64_t>(ngroups, (int64_t)ctx->num_sms * per_sm);
+            k_seg_block<<<std::max(gb, 1), kSegThreads, (size_t)cap * 8, s>>>(gmid, cnt + CNT_SEG + 3, b, cap,
+                                                                               keys[0], vals[0], &c->err);
         }
         DNASA_CUDA(ctx, cudaGetLastError());
         if (maxgroup > seg_max) {

@@ -130,6 +130,19 @@ def test_sa_finisher_and_doubling_agree(ctx, finish):
     assert ctx.trace()["finished_direct"] == (1 if finish > 0 else 0)
 
 
+@pytest.mark.parametrize("seg_max", [8, 32, 256, 2048, 16384])
+def test_sa_group_sort_tiers(ctx, seg_max):
+    """Doubling rounds only, on a text whose groups span every in-group sorting
+    tier (thread, warp registers, CTA shared memory, radix passes): 3,000 copies
+    of a 40 bp element give groups of thousands of members."""
+    rng = synth.rng_for(12, 11)
+    g = synth.genome_with_repeats(rng, 400_000, 0.05, (2, 50), (10, 200), 0.30, 40, 0.01)
+    t = synth.genome_text(g)
+    sa = gpu_sa(ctx, t, opts=B().make_opts(finish_threshold=-1, seg_max=seg_max))[0]
+    assert np.array_equal(sa.cpu().numpy().astype(np.int64), oracle.suffix_array(t))
+    assert ctx.trace()["rounds"] >= 2
+
+
 @pytest.mark.parametrize("pack", [0, -1])
 @pytest.mark.parametrize("seed,n_reads,lo,hi", [(21, 1, 300_001, 300_001), (22, 700, 1, 900)])
 def test_sa_packed_and_pair_initial_sort(ctx, pack, seed, n_reads, lo, hi):
