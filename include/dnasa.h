@@ -72,8 +72,9 @@ typedef struct {
     int32_t max_rounds;        /* safety bound on doubling rounds (default 63) */
     int32_t lookback;          /* look-back loads in flight per digit in a onesweep pass:
                                   8 (default) or 1 */
-    int32_t seg_max;           /* largest group a doubling round sorts on chip (8..16384,
-                                  default 16384); larger groups go through radix passes */
+    int32_t seg_max;           /* largest group a doubling round sorts on chip (8..12288,
+                                  default 12288); larger groups go through global radix
+                                  passes */
     int32_t pack_position;     /* initial sort: 0 (default) packs the suffix position under
                                   the key and sorts one 64-bit word per suffix when the
                                   key can still hold enough symbols; -1 never packs and

@@ -220,8 +220,8 @@ int sa_build(dnasa_ctx *ctx, const uint64_t *packed, const int64_t *toff, int64_
         return fail(ctx, DNASA_INVALID_ARG, "sa_build: digit_bits must be 0 or 8");
     if (opts && opts->lookback != 0 && opts->lookback != 1 && opts->lookback != 8)
         return fail(ctx, DNASA_INVALID_ARG, "sa_build: lookback must be 0, 1 or 8");
-    if (opts && opts->seg_max != 0 && (opts->seg_max < 8 || opts->seg_max > 16384))
-        return fail(ctx, DNASA_INVALID_ARG, "sa_build: seg_max must be 0 or in [8, 16384]");
+    if (opts && opts->seg_max != 0 && (opts->seg_max < 8 || opts->seg_max > 12288))
+        return fail(ctx, DNASA_INVALID_ARG, "sa_build: seg_max must be 0 or in [8, 12288]");
     if (opts && opts->pack_position != 0 && opts->pack_position != -1)
         return fail(ctx, DNASA_INVALID_ARG, "sa_build: pack_position must be 0 or -1");
     cudaSetDevice(ctx->device);
@@ -398,7 +398,7 @@ int dnasa_autotune(dnasa_ctx *ctx, const uint64_t *packed, const int64_t *toff, 
     dnasa_opts bopt{};
     const int tiles[3] = {2048, 3840, 5120};
     const int64_t fins[4] = {-1, std::max<int64_t>(N / 64, 1), std::max<int64_t>(N / 8, 1), N};
-    const int segs[3] = {256, 2048, 16384};
+    const int segs[3] = {256, 2048, 12288};
     for (int ti = 0; ti < 3 && rc == DNASA_OK; ++ti) {
         for (int fi = 0; fi < 4 * 3 && rc == DNASA_OK; ++fi) {
             dnasa_opts o{};

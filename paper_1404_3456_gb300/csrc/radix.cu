@@ -123,8 +123,10 @@ __device__ __forceinline__ void cp_async_commit_wait_all() {
 //   4. scatter keys, then values, into shared memory in digit order;
 //   5. look back over the predecessors' counts; publish the inclusive prefix;
 //   6. write keys and values, each digit's run as one contiguous burst.
+// Keys-only passes are held to 64 registers so that four CTAs share an SM (the
+// pass is latency-bound; with values, shared memory allows three anyway).
 template <typename K, int ITEMS, bool HAS_VALS, int LBW>
-__global__ void __launch_bounds__(kThreads) k_onesweep(
+__global__ void __launch_bounds__(kThreads, HAS_VALS ? 1 : 4) k_onesweep(
     const K *__restrict__ kin, const uint32_t *__restrict__ vin, K *__restrict__ kout,
     uint32_t *__restrict__ vout, const uint32_t *__restrict__ bucket, unsigned long long *status,
     uint32_t *tile_ctr, int64_t n_host, const unsigned long long *__restrict__ d_n, int shift,

@@ -475,12 +475,13 @@ __global__ void __launch_bounds__(kFinThreads) k_finish(const uint2 *__restrict_
 // From round 1 on, a round only has to order the members of each group by
 // rank[i+h] (all members of a group share the high key part, the head rank),
 // and members with equal keys stay together in one group that a later round
-// sorts again, so no stable order is needed.  Groups of at most 32 members are
-// sorted by one warp in registers, up to kSegMax members by one CTA in shared
-// memory (bitonic networks); only the members of larger groups go through the
-// global radix sort.  Each item is then read and written once instead of once
-// per radix pass.
-constexpr int kSegMax = 16384;     // largest group sorted on chip (one CTA, shared memory)
+// sorts again, so no stable order is needed.  Groups of at most 8 members are
+// sorted by one thread, up to 256 by one warp in registers (bitonic networks),
+// up to kSegMax by one CTA (radix passes in shared memory); only the members of
+// larger groups go through the global radix sort.  Each item is then read and
+// written once instead of once per global radix pass, and a group whose members
+// all carry the same rank[i+h] is left as it is.
+constexpr int kSegMax = 12288;     // largest group sorted on chip (one CTA, shared memory)
 constexpr int kSegWarpMax = 256;   // one warp, registers
 constexpr int kSegThreads = 512;
 
@@ -602,13 +603,17 @@ __device__ __forceinline__ void warp_sort_group(uint2 gs, int lane, int n2, unsi
                                                 unsigned long long *__restrict__ keys,
                                                 uint32_t *__restrict__ vals) {
     const int n = (int)gs.y;
-    const unsigned long long hi = keys[gs.x] & ~rmask;
+    const unsigned long long k0 = keys[gs.x];
+    const unsigned long long hi = k0 & ~rmask;
     unsigned long long w[E];
+    uint32_t x = 0;   // bits in which some rank differs from the first
 #pragma unroll
     for (int e = 0; e < E; ++e) {
         const int i = e * 32 + lane;
         w[e] = i < n ? seg_word(keys[gs.x + i], vals[gs.x + i], rmask) : ~0ull;
+        if (i < n) x |= (uint32_t)(w[e] >> 32) ^ (uint32_t)(k0 & rmask);
     }
+    if (!__any_sync(0xffffffffu, x != 0)) return;   // one rank for all: already in order
     warp_bitonic<E>(w, lane, n2);
 #pragma unroll
     for (int e = 0; e < E; ++e) {
@@ -642,49 +647,130 @@ __global__ void __launch_bounds__(256) k_seg_warp(const uint2 *__restrict__ grou
     }
 }
 
-// Groups of kSegWarpMax+1 .. kSegMax members: one CTA per group, bitonic network
-// over the words in dynamic shared memory (cap words, a power of two >= every
-// group of the list), each thread taking whole compare-exchange pairs.
-__global__ void __launch_bounds__(kSegThreads) k_seg_block(const uint2 *__restrict__ groups,
+// Groups of kSegWarpMax+1 .. kSegMax members: one CTA per group, LSD radix sort
+// on rank[i+h] in shared memory (ping-pong buffers of up to 512 * ROWS words).
+// Only the bits in which the group's ranks differ are sorted, 8 per pass; each
+// pass ranks the digits within each warp by ballots (stable: warp w holds the
+// w-th contiguous slice, rows in order) and scatters through per-warp digit
+// offsets.  Equal ranks keep their order, which is all a doubling round needs.
+constexpr int kSegRadixWarps = kSegThreads / 32;
+
+template <int ROWS>
+constexpr size_t seg_radix_smem() {
+    return (size_t)2 * kSegThreads * ROWS * 8 + (size_t)kSegRadixWarps * 256 * 4;
+}
+
+template <int ROWS>
+__global__ void __launch_bounds__(kSegThreads) k_seg_radix(const uint2 *__restrict__ groups,
                                                            const unsigned long long *__restrict__ d_ng,
-                                                           int b, int cap,
-                                                           unsigned long long *__restrict__ keys,
-                                                           uint32_t *__restrict__ vals,
-                                                           uint32_t *err) {
-    extern __shared__ unsigned long long sw[];
+                                                           int b, unsigned long long *__restrict__ keys,
+                                                           uint32_t *__restrict__ vals, uint32_t *err) {
+    constexpr int NW = kSegRadixWarps, CAP = kSegThreads * ROWS;
+    extern __shared__ __align__(16) unsigned char seg_raw[];
+    unsigned long long *buf0 = reinterpret_cast<unsigned long long *>(seg_raw);
+    unsigned long long *buf1 = buf0 + CAP;
+    uint32_t *wh = reinterpret_cast<uint32_t *>(buf1 + CAP);   // [NW][256] digit offsets
+    __shared__ uint32_t s_tmp[NW + 1];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t ng = (int64_t)*d_ng;
     const unsigned long long rmask = (1ull << b) - 1ull;
     for (int64_t g = blockIdx.x; g < ng; g += gridDim.x) {
         const uint2 gs = groups[g];
         const int n = (int)gs.y;
-        int n2 = 512;
-        while (n2 < n) n2 <<= 1;
-        if (n2 > cap) {   // the list holds only groups that fit: never taken
-            if (threadIdx.x == 0) atomicOr(err, DERR_BOUNDS);
+        if (n > CAP) {   // the host sizes ROWS for the list: never taken
+            if (tid == 0) atomicOr(err, DERR_BOUNDS);
             continue;
         }
-        const unsigned long long hi = keys[gs.x] & ~rmask;
-        for (int i = threadIdx.x; i < n2; i += kSegThreads)
-            sw[i] = i < n ? seg_word(keys[gs.x + i], vals[gs.x + i], rmask) : ~0ull;
+        const unsigned long long k0 = keys[gs.x];
+        const unsigned long long hi = k0 & ~rmask;
+        const uint32_t r0 = (uint32_t)(k0 & rmask);
+        uint32_t x = 0;   // bits in which some rank differs from the first
+        for (int i = tid; i < n; i += kSegThreads) {
+            const unsigned long long k = keys[gs.x + i];
+            buf0[i] = seg_word(k, vals[gs.x + i], rmask);
+            x |= (uint32_t)(k & rmask) ^ r0;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x |= __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0) s_tmp[warp] = x;
         __syncthreads();
-        for (int size = 2; size <= n2; size <<= 1) {
-            for (int stride = size >> 1; stride > 0; stride >>= 1) {
-                for (int p = threadIdx.x; p < (n2 >> 1); p += kSegThreads) {
-                    const int i = ((p & ~(stride - 1)) << 1) | (p & (stride - 1));
-                    const int j = i | stride;
-                    const bool asc = (i & size) == 0;
-                    unsigned long long a = sw[i], c = sw[j];
-                    if (asc ? a > c : a < c) {
-                        sw[i] = c;
-                        sw[j] = a;
+        x = 0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) x |= s_tmp[w];
+        const int passes = x ? (32 - __clz(x) + 7) / 8 : 0;
+        if (passes == 0) {   // one rank for all: the group is already in order
+            __syncthreads();
+            continue;
+        }
+        const int chunk = ((n + NW * 32 - 1) / (NW * 32)) * 32;   // warp slice, whole rows
+        const int rows = chunk / 32;
+        unsigned long long *src = buf0, *dst = buf1;
+        uint32_t *mh = wh + warp * 256;
+        for (int pass = 0; pass < passes; ++pass) {
+            const int shift = 32 + 8 * pass;
+            for (int i = tid; i < NW * 256; i += kSegThreads) wh[i] = 0;
+            __syncthreads();
+            uint16_t lr[ROWS];
+#pragma unroll
+            for (int r = 0; r < ROWS; ++r) {
+                lr[r] = 0;
+                if (r < rows) {   // warp-uniform
+                    const int i = warp * chunk + r * 32 + lane;
+                    const bool valid = i < n;
+                    const uint32_t d = valid ? (uint32_t)(src[i] >> shift) & 255u : 0u;
+                    const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
+                    uint32_t peers = vmask;
+#pragma unroll
+                    for (int bb = 0; bb < 8; ++bb) {
+                        const uint32_t bit = (d >> bb) & 1u;
+                        const uint32_t bal = __ballot_sync(0xffffffffu, bit);
+                        peers &= bit ? bal : ~bal;
+                    }
+                    const int leader = peers ? __ffs(peers) - 1 : 0;
+                    uint32_t old = 0;
+                    if (valid && lane == leader) {   // one lane per digit: plain update
+                        old = mh[d];
+                        mh[d] = old + (uint32_t)__popc(peers);
+                    }
+                    old = __shfl_sync(0xffffffffu, old, leader);
+                    lr[r] = (uint16_t)(old + __popc(peers & lanemask_lt()));
+                    __syncwarp();
+                }
+            }
+            __syncthreads();
+            // digit d starts after all smaller digits, and after digit d of lower warps
+            uint32_t tot = 0;
+            if (tid < 256)
+                for (int w = 0; w < NW; ++w) tot += wh[w * 256 + tid];
+            uint32_t total;
+            const uint32_t start = block_exclusive_sum<kSegThreads>(tot, s_tmp, &total);
+            if (tid < 256) {
+                uint32_t run = start;
+                for (int w = 0; w < NW; ++w) {
+                    const uint32_t c = wh[w * 256 + tid];
+                    wh[w * 256 + tid] = run;
+                    run += c;
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int r = 0; r < ROWS; ++r) {
+                if (r < rows) {
+                    const int i = warp * chunk + r * 32 + lane;
+                    if (i < n) {
+                        const unsigned long long w = src[i];
+                        dst[mh[(uint32_t)(w >> shift) & 255u] + lr[r]] = w;
                     }
                 }
-                __syncthreads();
             }
+            __syncthreads();
+            unsigned long long *t = src;
+            src = dst;
+            dst = t;
         }
-        for (int i = threadIdx.x; i < n; i += kSegThreads) {
-            keys[gs.x + i] = hi | (sw[i] >> 32);
-            vals[gs.x + i] = (uint32_t)sw[i];
+        for (int i = tid; i < n; i += kSegThreads) {
+            keys[gs.x + i] = hi | (src[i] >> 32);
+            vals[gs.x + i] = (uint32_t)src[i];
         }
         __syncthreads();
     }
@@ -856,8 +942,14 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
         cudaError_t e = cudaFuncSetAttribute(k_rerank<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)sizeof(RerankSmem));
         if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(k_seg_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 kSegMax * 8);
+        e = cudaFuncSetAttribute(k_seg_radix<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)seg_radix_smem<4>());
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(k_seg_radix<12>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)seg_radix_smem<12>());
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(k_seg_radix<24>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)seg_radix_smem<24>());
         if (e != cudaSuccess) return e;
         return cudaFuncSetAttribute(k_rerank<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)sizeof(RerankSmem));
@@ -992,13 +1084,17 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
                                                        keys[0], vals[0]);
         }
         if (maxgroup > kSegWarpMax && seg_max > kSegWarpMax) {
-            int cap = 512;
-            while (cap < std::min<int64_t>(maxgroup, seg_max)) cap <<= 1;
-            const int per_sm = std::max(1, std::min(4, (200 << 10) / (cap * 8)));
+            const int64_t biggest = std::min<int64_t>(maxgroup, seg_max);
             LaunchScope ls_(ctx, PK_SEGSORT, s, 0.0);
-            int gb = (int)std::min<int64_t>(ngroups, (int64_t)ctx->num_sms * per_sm);
-            k_seg_block<<<std::max(gb, 1), kSegThreads, (size_t)cap * 8, s>>>(gmid, cnt + CNT_SEG + 3, b, cap,
-                                                                               keys[0], vals[0], &c->err);
+            auto launch = [&](auto kern, size_t smem) {
+                const int per_sm = std::max(1, (int)((200u << 10) / smem));
+                const int gb = (int)std::min<int64_t>(ngroups, (int64_t)ctx->num_sms * per_sm);
+                kern<<<std::max(gb, 1), kSegThreads, smem, s>>>(gmid, cnt + CNT_SEG + 3, b, keys[0], vals[0],
+                                                                &c->err);
+            };
+            if (biggest <= kSegThreads * 4) launch(k_seg_radix<4>, seg_radix_smem<4>());
+            else if (biggest <= kSegThreads * 12) launch(k_seg_radix<12>, seg_radix_smem<12>());
+            else launch(k_seg_radix<24>, seg_radix_smem<24>());
         }
         DNASA_CUDA(ctx, cudaGetLastError());
         if (maxgroup > seg_max) {

@@ -130,10 +130,10 @@ def test_sa_finisher_and_doubling_agree(ctx, finish):
     assert ctx.trace()["finished_direct"] == (1 if finish > 0 else 0)
 
 
-@pytest.mark.parametrize("seg_max", [8, 32, 256, 2048, 16384])
+@pytest.mark.parametrize("seg_max", [8, 32, 256, 2048, 12288])
 def test_sa_group_sort_tiers(ctx, seg_max):
     """Doubling rounds only, on a text whose groups span every in-group sorting
-    tier (thread, warp registers, CTA shared memory, radix passes): 3,000 copies
+    tier (thread, warp registers, CTA radix in shared memory, global radix passes): 3,000 copies
     of a 40 bp element give groups of thousands of members."""
     rng = synth.rng_for(12, 11)
     g = synth.genome_with_repeats(rng, 400_000, 0.05, (2, 50), (10, 200), 0.30, 40, 0.01)
