@@ -190,7 +190,7 @@ int dnasa_selftest_timeout(dnasa_ctx *ctx, void *stream);
  * stream before returning; DNASA_DEVICE_TIMEOUT if a bounded device wait gave up. */
 int dnasa_sort_pairs_noalloc(uint64_t *keys, uint32_t *vals, int64_t n, int key_bits, void *stream);
 
-/* ---- S1: pack (Sec. III alphabet; the SA of Sec. IV is over this text) ------- */
+/* ---- pack (Sec. III alphabet; the SA of Sec. IV is over this text) ------- */
 
 /* Validates text[0..N) and writes its packed form and fragment offsets.
  *   text      device, N bytes of A/C/G/T/'$', last byte '$', no empty fragment
@@ -202,11 +202,13 @@ int dnasa_sort_pairs_noalloc(uint64_t *keys, uint32_t *vals, int64_t n, int key_
 int dnasa_pack(dnasa_ctx *ctx, const uint8_t *text, int64_t N, uint64_t *packed,
                int64_t *toff, int64_t toff_cap, int64_t *n_reads, void *stream);
 
-/* ---- S2-S6: suffix array (Sec. IV "sorted array Pos of all the suffixes") ---- */
+/* ---- suffix array (Sec. IV "sorted array Pos of all the suffixes") ---- */
 
-/* Builds the suffix array of the packed text by prefix doubling: packed 29-mer
- * initial keys, then rounds that radix sort (rank[i], rank[i+h]) pairs of the
- * still-unsorted suffixes, with an optional direct-comparison finisher.
+/* Builds the suffix array of the packed text by prefix doubling: a radix sort of
+ * packed initial keys (the first h0 <= 29 bases and the distance to the
+ * fragment's '$'), then rounds that order each group of suffixes still equal on
+ * their first h symbols by rank[i+h], with an optional direct-comparison
+ * finisher.
  *   packed, toff   as written by dnasa_pack (toff: n_reads + 1 entries)
  *   N              text length including every '$' (N >= 1, N < 2^31)
  *   sa             device, N entries of int32 or int64 (idx_width): sa[j] is
@@ -216,7 +218,7 @@ int dnasa_pack(dnasa_ctx *ctx, const uint8_t *text, int64_t N, uint64_t *packed,
 int sa_build(dnasa_ctx *ctx, const uint64_t *packed, const int64_t *toff, int64_t n_reads,
              int64_t N, void *sa, int idx_width, const dnasa_opts *opts, void *stream);
 
-/* ---- S7: LCP ----------------------------------------------------------------- */
+/* ---- LCP ----------------------------------------------------------------- */
 
 /* lcp[0] = 0; lcp[j] = number of equal bases at the start of suffixes sa[j-1]
  * and sa[j], stopping at the first '$' of either (a '$' never matches).
@@ -226,7 +228,7 @@ int sa_build(dnasa_ctx *ctx, const uint64_t *packed, const int64_t *toff, int64_
 int lcp_build(dnasa_ctx *ctx, const uint64_t *packed, const int64_t *toff, int64_t n_reads,
               int64_t N, const void *sa, int idx_width, int32_t *lcp, void *stream);
 
-/* ---- S8-S9: overlap search + containment (Sec. III "fir", Sec. IV search) ----- */
+/* ---- overlap search + containment (Sec. III "fir", Sec. IV search) ----- */
 
 /* For every fragment j and every suffix X of it with min_overlap <= |X| < |r_j|,
  * finds the fragments k != j whose first |X| bases equal X and |X| < |r_k|,
@@ -243,7 +245,7 @@ int overlap_search(dnasa_ctx *ctx, const uint64_t *packed, const int64_t *toff, 
                    int32_t min_overlap, dnasa_edge *edges, int64_t cap, int64_t *n_edges,
                    uint8_t *contained, void *stream);
 
-/* ---- S10: whole method on one fragment set (Sec. III, Fig. 3 -> superstring) -- */
+/* ---- whole method on one fragment set (Sec. III, Fig. 3 -> superstring) -- */
 
 /* text -> pack -> SA -> LCP -> overlaps -> greedy layout -> contigs.  Greedy:
  * edges between non-contained fragments in order of (L desc, j asc, k asc);
@@ -259,7 +261,7 @@ int assemble(dnasa_ctx *ctx, const uint8_t *text, int64_t N, int32_t min_overlap
              uint8_t *contigs, int64_t cap, int64_t *contig_off, int64_t off_cap,
              int64_t *n_contigs, int64_t *needed, void *stream);
 
-/* ---- S11: batched -- many independent fragment sets in one pass ------------- */
+/* ---- batched -- many independent fragment sets in one pass ------------- */
 
 /* Suffix arrays of n_inst independent fragment texts stored one after another
  * (instance i = text[inst_off[i] .. inst_off[i+1]), itself '$'-terminated
@@ -301,7 +303,7 @@ int dnasa_autotune(dnasa_ctx *ctx, const uint64_t *packed, const int64_t *toff, 
                    int64_t N, const int64_t *inst_off, int32_t n_inst, const char *cache_path,
                    dnasa_opts *best, double *best_ms, void *stream);
 
-/* ---- S12: served -- continuous batching of arriving assembly jobs ------------ */
+/* ---- served -- continuous batching of arriving assembly jobs ------------ */
 
 /* One assembly job: a '$'-terminated fragment text in HOST memory (copied at
  * submit, so the caller may free it afterwards). */

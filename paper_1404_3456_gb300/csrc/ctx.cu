@@ -1,4 +1,4 @@
-// ctx.cu -- context, workspace, status handling, the pack step (S1) and the
+// ctx.cu -- context, workspace, status handling, the pack step and the
 // order-preserving compaction used by several steps.
 #include <algorithm>
 #include <cstdio>
@@ -197,7 +197,7 @@ int compact_flags(dnasa_ctx *ctx, Arena &a, const uint8_t *flags, int64_t n, uin
     return DNASA_OK;
 }
 
-// ------------------------------------------------------------------ pack (S1)
+// ------------------------------------------------------------------ pack
 constexpr int kPackThreads = 256;
 constexpr int kPackChunk = 32;                         // bytes per thread
 constexpr int kPackTile = kPackThreads * kPackChunk;   // 8192 bytes

@@ -1,4 +1,4 @@
-// layout.cu -- greedy layout of the overlap graph and spelling of contigs (S10).
+// layout.cu -- greedy layout of the overlap graph and spelling of contigs.
 //
 // Sec. III turns the fragments into a weighted directed graph (Fig. 3) whose
 // maximal path spells the reconstructed sequence, and concatenates the chosen

@@ -1,4 +1,4 @@
-// lcp.cu -- LCP array over the suffix array (S7).
+// lcp.cu -- LCP array over the suffix array.
 //
 // lcp[0] = 0 and lcp[j] = the number of equal bases at the start of suffixes
 // SA[j-1] and SA[j], never counting a '$' (so no LCP crosses a fragment end),

@@ -1,4 +1,4 @@
-// overlap.cu -- suffix-array driven overlap search and containment (S8, S9).
+// overlap.cu -- suffix-array driven overlap search and containment.
 //
 // Sec. III reconstructs the sequence from "fir" relations: fragment D_k is a
 // prefix of another fragment, or the remainder of a cut fragment is the

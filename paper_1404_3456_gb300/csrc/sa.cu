@@ -1,4 +1,4 @@
-// sa.cu -- suffix array by prefix doubling over the 2-bit packed text (S2-S6).
+// sa.cu -- suffix array by prefix doubling over the 2-bit packed text.
 //
 // Sec. IV of the paper builds the suffix array "Pos" by radix sorting suffix
 // keys on the GPU.  Here the keys are:
@@ -9,8 +9,10 @@
 //             and are final at once (distinct sentinels ordered by position).
 //   round r   (rank[i], rank[i+h]) for the suffixes still in groups of equal
 //             rank, h = h0 * 2^(r-1): the doubling step of Manber & Myers.
-// Each round is a stable LSD radix sort (radix.cu) followed by one rerank
-// kernel that, in a single pass with decoupled look-back, marks group heads,
+// Round 0 is a stable LSD radix sort (radix.cu) of every suffix; each later
+// round only orders the members of every group by rank[i+h] (in-group sorts on
+// chip, global radix passes for the largest groups).  After each sort one
+// rerank kernel, in a single pass with decoupled look-back, marks group heads,
 // writes SA entries and new ranks (rank = SA index of the group head, i.e. the
 // number of smaller suffixes, Sec. IV's "rank"), drops groups that became
 // singletons and compacts the rest.  When few suffixes remain, a finisher
@@ -26,7 +28,7 @@ namespace dnasa {
 
 namespace {
 
-// ------------------------------------------------------------------ S2: initial keys
+// ------------------------------------------------------------------ initial keys
 constexpr int kInitThreads = 256;
 constexpr int kInitItems = 8;
 
@@ -67,7 +69,7 @@ __global__ void __launch_bounds__(kInitThreads) k_init_keys(TextDesc t, int h0, 
     }
 }
 
-// ------------------------------------------------------------------ S4: rerank + compact
+// ------------------------------------------------------------------ rerank + compact
 constexpr int kRrThreads = 256;
 constexpr int kRrItems = 8;
 constexpr int kRrTile = kRrThreads * kRrItems;
@@ -371,7 +373,7 @@ __global__ void __launch_bounds__(256) k_rank_apply(const uint2 *__restrict__ st
     }
 }
 
-// ------------------------------------------------------------------ S5: doubling gather
+// ------------------------------------------------------------------ doubling gather
 __global__ void __launch_bounds__(256) k_gather(const uint32_t *__restrict__ npos,
                                                 const uint32_t *__restrict__ nhead, int64_t n,
                                                 const uint32_t *__restrict__ rank, uint32_t h,
@@ -389,7 +391,7 @@ __global__ void __launch_bounds__(256) k_gather(const uint32_t *__restrict__ npo
     }
 }
 
-// ------------------------------------------------------------------ S6: direct finisher
+// ------------------------------------------------------------------ direct finisher
 // Each remaining group shares its first h symbols.  rank[] holds h-ranks (equal
 // ranks <=> equal first h symbols; a rank that contains a '$' is unique), so two
 // members p, q compare as the sequences rank[p+h], rank[p+2h], rank[p+3h], ...:
@@ -471,7 +473,7 @@ __global__ void __launch_bounds__(kFinThreads) k_finish(const uint2 *__restrict_
     }
 }
 
-// ------------------------------------------------------------------ S5: in-group sorting
+// ------------------------------------------------------------------ in-group sorting
 // From round 1 on, a round only has to order the members of each group by
 // rank[i+h] (all members of a group share the high key part, the head rank),
 // and members with equal keys stay together in one group that a later round

@@ -1,4 +1,4 @@
-// serve.cu -- S12: a continuous-batching assembly server on one GPU.
+// serve.cu -- a continuous-batching assembly server on one GPU.
 //
 // Jobs (one fragment text each, host memory) are queued in arrival order.  The
 // server runs `slots` workers, each with its own context (workspace) and CUDA

@@ -1,4 +1,4 @@
-"""S11 batched: many independent fragment sets in one pass.  Each instance's
+"""Batched: many independent fragment sets in one pass.  Each instance's
 result must equal the oracle's and, byte for byte, the same instance
 assembled alone (integer work: tolerance zero)."""
 import numpy as np

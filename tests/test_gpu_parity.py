@@ -54,7 +54,7 @@ def gpu_sa(ctx, text_np, dtype=torch.int32, opts=None):
     return sa, packed, toff, nr, text
 
 
-# ---------------------------------------------------------------- S1 pack
+# ---------------------------------------------------------------- pack
 
 
 def test_pack_offsets_and_codes(ctx):
@@ -81,7 +81,7 @@ def test_pack_rejects_bad_text(ctx, bad):
     assert e.value.status == B().BAD_ALPHABET
 
 
-# ---------------------------------------------------------------- S2-S6 suffix array
+# ---------------------------------------------------------------- suffix array
 
 
 @pytest.mark.parametrize("text", [b"A$", b"AAAAAAAA$", b"ACGTACGTACGT$", b"A$A$AA$",
@@ -188,7 +188,7 @@ def test_sa_all_same_base(ctx):
     assert np.array_equal(sa.cpu().numpy().astype(np.int64), np.arange(t.size)[::-1])
 
 
-# ---------------------------------------------------------------- S7 LCP
+# ---------------------------------------------------------------- LCP
 
 
 @pytest.mark.parametrize("seed", [0, 1, 2])
@@ -202,7 +202,7 @@ def test_lcp_parity(ctx, seed):
     assert np.array_equal(lcp.cpu().numpy(), want)
 
 
-# ---------------------------------------------------------------- S8-S9 overlaps
+# ---------------------------------------------------------------- overlaps and containment
 
 
 def overlaps_gpu(ctx, t, lmin):
@@ -243,7 +243,7 @@ def test_overlap_parity_batched_instance(ctx):
     assert np.array_equal(c, oracle.contained(inst["text"]))
 
 
-# ---------------------------------------------------------------- S10 assemble
+# ---------------------------------------------------------------- assemble
 
 
 @pytest.mark.parametrize("seed", range(10))

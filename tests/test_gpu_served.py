@@ -1,4 +1,4 @@
-"""S12 served: jobs submitted while others run are batched and overlapped; each
+"""Served: jobs submitted while others run are batched and overlapped; each
 result must be, byte for byte, the job assembled alone (tolerance zero)."""
 import threading
 import time
