@@ -118,7 +118,7 @@ int64_t dnasa_packed_words(int64_t N);
 enum {
     DNASA_PROF_ONESWEEP = 0,  /* one radix digit pass (decoupled look-back scatter) */
     DNASA_PROF_HIST = 1,      /* digit histograms of a sort */
-    DNASA_PROF_RERANK = 2,    /* head flags, SA/rank writes, compaction */
+    DNASA_PROF_RERANK = 2,    /* head flags, SA writes, staged ranks, compaction */
     DNASA_PROF_GATHER = 3,    /* doubling keys (rank[i], rank[i+h]) */
     DNASA_PROF_INIT = 4,      /* initial packed keys */
     DNASA_PROF_FINISH = 5,    /* direct-comparison finisher */
@@ -128,7 +128,8 @@ enum {
     DNASA_PROF_PACK = 9,
     DNASA_PROF_OTHER = 10,
     DNASA_PROF_SEGSORT = 11,  /* in-group sorting of a doubling round */
-    DNASA_PROF_KINDS = 12
+    DNASA_PROF_APPLY = 12,    /* staged rank writes applied bucket by bucket */
+    DNASA_PROF_KINDS = 13
 };
 
 /* Per kernel class: launches, summed device time (CUDA events recorded on the

@@ -49,7 +49,7 @@ class ProfEntry(ctypes.Structure):
 
 
 PROF_KINDS = ["onesweep", "hist", "rerank", "gather", "init_keys", "finish", "lcp", "overlap",
-              "layout", "pack", "other", "segsort"]
+              "layout", "pack", "other", "segsort", "apply"]
 
 class Job(ctypes.Structure):
     _fields_ = [("text", ctypes.c_void_p), ("N", ctypes.c_int64), ("min_overlap", ctypes.c_int32),

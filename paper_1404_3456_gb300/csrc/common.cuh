@@ -53,7 +53,7 @@ namespace dnasa {
 // Kernel classes the profiler aggregates (same numbering as DNASA_PROF_* in dnasa.h).
 enum ProfKind { PK_ONESWEEP = 0, PK_HIST = 1, PK_RERANK = 2, PK_GATHER = 3, PK_INIT = 4,
                 PK_FINISH = 5, PK_LCP = 6, PK_OVERLAP = 7, PK_LAYOUT = 8, PK_PACK = 9,
-                PK_OTHER = 10, PK_SEGSORT = 11, PK_COUNT = 12 };
+                PK_OTHER = 10, PK_SEGSORT = 11, PK_APPLY = 12, PK_COUNT = 13 };
 struct ProfRec {
     int kind;
     cudaEvent_t a, b;

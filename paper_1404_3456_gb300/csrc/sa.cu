@@ -978,7 +978,7 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
     auto apply_ranks = [&](int64_t n_items, int stage_buf) -> int {
         int64_t per = std::min<int64_t>((int64_t)1 << bshift, n_items);
         int per_bucket = std::max(1, ceil_div(per, kApplyItems));
-        LaunchScope ls_(ctx, PK_RERANK, s, 12.0 * n_items);
+        LaunchScope ls_(ctx, PK_APPLY, s, 12.0 * n_items);
         k_rank_apply<<<nbuckets * per_bucket, 256, 0, s>>>(
             reinterpret_cast<const uint2 *>(keys[stage_buf]), bucket_fill, bshift, per_bucket, N,
             rank, &c->err);
