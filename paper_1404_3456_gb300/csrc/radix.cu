@@ -123,16 +123,13 @@ __device__ __forceinline__ void cp_async_commit_wait_all() {
 //   4. scatter keys, then values, into shared memory in digit order;
 //   5. look back over the predecessors' counts; publish the inclusive prefix;
 //   6. write keys and values, each digit's run as one contiguous burst.
-// Keys-only passes are held to 64 registers so that four CTAs share an SM (the
-// pass is latency-bound; with values, shared memory allows three anyway).
-template <typename K, int ITEMS, bool HAS_VALS, int LBW>
-__global__ void __launch_bounds__(kThreads, HAS_VALS ? 1 : 4) k_onesweep(
+template <typename K, int ITEMS, bool HAS_VALS, int LBW, bool FULL>
+__device__ __forceinline__ void onesweep_tile(
     const K *__restrict__ kin, const uint32_t *__restrict__ vin, K *__restrict__ kout,
     uint32_t *__restrict__ vout, const uint32_t *__restrict__ bucket, unsigned long long *status,
-    uint32_t *tile_ctr, int64_t n_host, const unsigned long long *__restrict__ d_n, int shift,
-    uint32_t epoch, uint32_t *err, uint32_t spin_limit) {
+    int64_t n, uint32_t tile, int64_t base, int tile_n, int shift, uint32_t epoch, uint32_t *err,
+    uint32_t spin_limit, unsigned char *smem_raw) {
     constexpr int TILE = kThreads * ITEMS;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     K *s_keys = reinterpret_cast<K *>(smem_raw);
     uint32_t *s_vals = reinterpret_cast<uint32_t *>(s_keys + TILE);
     uint32_t *s_whist = s_vals + (HAS_VALS ? TILE : 0);          // [kWarps][kRadix]
@@ -140,42 +137,34 @@ __global__ void __launch_bounds__(kThreads, HAS_VALS ? 1 : 4) k_onesweep(
     uint32_t *s_start = s_count + kRadix;                         // [kRadix] tile-local start
     uint32_t *s_gbase = s_start + kRadix;                         // [kRadix] global base - start
     uint32_t *s_misc = s_gbase + kRadix;                          // [kWarps + 2]
-
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) {
-        s_misc[kWarps] = atomicAdd(tile_ctr, 1u);
-        s_misc[kWarps + 1] = 0;   // set when a look-back gave up: skip the writes
-    }
-    for (int i = tid; i < kWarps * kRadix; i += kThreads) s_whist[i] = 0;
-    for (int i = tid; i < kRadix; i += kThreads) s_count[i] = 0;
-    __syncthreads();
-    const uint32_t tile = s_misc[kWarps];
-    const int64_t n = d_n ? (int64_t)*d_n : n_host;
-    const int64_t base = (int64_t)tile * TILE;
-    if (base >= n) return;   // uniform over the CTA; later tiles are empty too
-    const int tile_n = (int)min((int64_t)TILE, n - base);
     // warp-striped layout: warp w owns [w*32*ITEMS, (w+1)*32*ITEMS) of the tile
     const int wbase = warp * 32 * ITEMS;
+    auto valid_at = [&](int idx) -> bool { return FULL || idx < tile_n; };
 
     // ---- 1. values start arriving in shared memory while the keys are ranked
     if (HAS_VALS) {
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) {
             int idx = wbase + i * 32 + lane;
-            if (idx < tile_n) cp_async4(s_vals + idx, vin + base + idx);
+            if (valid_at(idx)) cp_async4(s_vals + idx, vin + base + idx);
         }
     }
-    // ---- 2. keys; the tile's digit counts, published before any ranking work
+    // ---- 2. keys and their digits; the tile's digit counts, published before
+    // any ranking work.  dl[i] keeps the digit (bits 0-7) and, after step 3, the
+    // rank among the warp's equal digits (bits 8-31).
     K key[ITEMS];
+    uint32_t dl[ITEMS];
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
         int idx = wbase + i * 32 + lane;
-        key[i] = idx < tile_n ? kin[base + idx] : K(0);
+        key[i] = valid_at(idx) ? kin[base + idx] : K(0);
+        dl[i] = digit_of(key[i], shift);
     }
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
         int idx = wbase + i * 32 + lane;
-        if (idx < tile_n) atomicAdd(&s_count[digit_of(key[i], shift)], 1u);
+        if (valid_at(idx)) atomicAdd(&s_count[dl[i]], 1u);
     }
     __syncthreads();
     for (int d = tid; d < kRadix; d += kThreads)
@@ -184,20 +173,19 @@ __global__ void __launch_bounds__(kThreads, HAS_VALS ? 1 : 4) k_onesweep(
     // ---- 3. rank within the warp, item by item (tile order: stable).  The lanes
     // holding the same digit are found by ballots; the lowest of them bumps the
     // warp's counter for that digit and broadcasts the old count.
-    uint16_t lrank[ITEMS];
     uint32_t *wh = s_whist + warp * kRadix;
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
         int idx = wbase + i * 32 + lane;
-        bool valid = idx < tile_n;
-        uint32_t vmask = __ballot_sync(0xffffffffu, valid);
-        uint32_t d = digit_of(key[i], shift);
-        uint32_t peers = match_digit(d, vmask);
-        int leader = peers ? __ffs(peers) - 1 : 0;
+        const bool valid = valid_at(idx);
+        const uint32_t vmask = FULL ? 0xffffffffu : __ballot_sync(0xffffffffu, valid);
+        const uint32_t d = dl[i];
+        const uint32_t peers = match_digit(d, vmask);
+        const int leader = __ffs(peers) - 1;   // valid lanes: peers holds the lane itself
         uint32_t old = 0;
         if (valid && lane == leader) old = atomicAdd(&wh[d], (uint32_t)__popc(peers));
-        old = __shfl_sync(0xffffffffu, old, leader);
-        lrank[i] = (uint16_t)(old + __popc(peers & lanemask_lt()));
+        old = __shfl_sync(0xffffffffu, old, leader < 0 ? 0 : leader);
+        dl[i] = d | ((old + __popc(peers & lanemask_lt())) << kRadixBits);
         __syncwarp();
     }
     // tile-local start of each digit (kThreads == kRadix: one digit per thread)
@@ -225,16 +213,14 @@ __global__ void __launch_bounds__(kThreads, HAS_VALS ? 1 : 4) k_onesweep(
     }
     __syncthreads();
     // ---- 4. keys, then values, into shared memory in digit order
-    uint16_t lpos[ITEMS];
 #pragma unroll
     for (int i = 0; i < ITEMS; ++i) {
         int idx = wbase + i * 32 + lane;
-        lpos[i] = 0;
-        if (idx < tile_n) {
-            uint32_t d = digit_of(key[i], shift);
-            uint32_t p = s_start[d] + s_whist[warp * kRadix + d] + lrank[i];
-            lpos[i] = (uint16_t)p;
+        if (valid_at(idx)) {
+            const uint32_t d = dl[i] & (kRadix - 1);
+            const uint32_t p = s_start[d] + wh[d] + (dl[i] >> kRadixBits);
             s_keys[p] = key[i];
+            dl[i] = p;   // from here on: the item's place in the tile
         }
     }
     if (HAS_VALS) {
@@ -244,13 +230,13 @@ __global__ void __launch_bounds__(kThreads, HAS_VALS ? 1 : 4) k_onesweep(
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) {
             int idx = wbase + i * 32 + lane;
-            v[i] = idx < tile_n ? s_vals[idx] : 0u;
+            v[i] = valid_at(idx) ? s_vals[idx] : 0u;
         }
         __syncthreads();
 #pragma unroll
         for (int i = 0; i < ITEMS; ++i) {
             int idx = wbase + i * 32 + lane;
-            if (idx < tile_n) s_vals[lpos[i]] = v[i];
+            if (valid_at(idx)) s_vals[dl[i]] = v[i];
         }
     }
     // ---- 5. look back and form the global base of each digit
@@ -299,9 +285,12 @@ __global__ void __launch_bounds__(kThreads, HAS_VALS ? 1 : 4) k_onesweep(
     __syncthreads();
     if (s_misc[kWarps + 1]) return;   // offsets unknown: write nothing
     // ---- 6. global writes
-    for (int idx = tid; idx < tile_n; idx += kThreads) {
-        K k = s_keys[idx];
-        uint32_t o = s_gbase[digit_of(k, shift)] + (uint32_t)idx;
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+        const int idx = tid + i * kThreads;
+        if (!valid_at(idx)) break;
+        const K k = s_keys[idx];
+        const uint32_t o = s_gbase[digit_of(k, shift)] + (uint32_t)idx;
         if (o < (uint64_t)n) {
             kout[o] = k;
             if (HAS_VALS) vout[o] = s_vals[idx];
@@ -309,6 +298,42 @@ __global__ void __launch_bounds__(kThreads, HAS_VALS ? 1 : 4) k_onesweep(
             atomicOr(err, DERR_BOUNDS);
         }
     }
+}
+
+// Held to 80 registers so that three CTAs share an SM whatever the variant
+// (the pass is latency- and issue-bound).  Every tile but the last is full and
+// runs without per-item bounds tests.
+template <typename K, int ITEMS, bool HAS_VALS, int LBW>
+__global__ void __launch_bounds__(kThreads, 3) k_onesweep(
+    const K *__restrict__ kin, const uint32_t *__restrict__ vin, K *__restrict__ kout,
+    uint32_t *__restrict__ vout, const uint32_t *__restrict__ bucket, unsigned long long *status,
+    uint32_t *tile_ctr, int64_t n_host, const unsigned long long *__restrict__ d_n, int shift,
+    uint32_t epoch, uint32_t *err, uint32_t spin_limit) {
+    constexpr int TILE = kThreads * ITEMS;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint32_t *s_whist = reinterpret_cast<uint32_t *>(smem_raw + (size_t)TILE * sizeof(K)) +
+                        (HAS_VALS ? TILE : 0);
+    uint32_t *s_count = s_whist + kWarps * kRadix;
+    uint32_t *s_misc = s_count + 3 * kRadix;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        s_misc[kWarps] = atomicAdd(tile_ctr, 1u);
+        s_misc[kWarps + 1] = 0;   // set when a look-back gave up: skip the writes
+    }
+    for (int i = tid; i < kWarps * kRadix; i += kThreads) s_whist[i] = 0;
+    for (int i = tid; i < kRadix; i += kThreads) s_count[i] = 0;
+    __syncthreads();
+    const uint32_t tile = s_misc[kWarps];
+    const int64_t n = d_n ? (int64_t)*d_n : n_host;
+    const int64_t base = (int64_t)tile * TILE;
+    if (base >= n) return;   // uniform over the CTA; later tiles are empty too
+    const int tile_n = (int)min((int64_t)TILE, n - base);
+    if (tile_n == TILE)
+        onesweep_tile<K, ITEMS, HAS_VALS, LBW, true>(kin, vin, kout, vout, bucket, status, n, tile, base,
+                                                     tile_n, shift, epoch, err, spin_limit, smem_raw);
+    else
+        onesweep_tile<K, ITEMS, HAS_VALS, LBW, false>(kin, vin, kout, vout, bucket, status, n, tile, base,
+                                                      tile_n, shift, epoch, err, spin_limit, smem_raw);
 }
 
 template <typename K, int ITEMS, bool HAS_VALS>
