@@ -74,6 +74,46 @@ def dist_env():
             int(os.environ.get("WORLD_SIZE", 1)))
 
 
+def rank_setup(local_rank: int, world: int, backend: str = "nccl"):
+    """One process per GPU: joins the process group (NCCL between GPUs; gloo for
+    the CPU tests of this logic) when there is more than one rank."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        if backend == "nccl":
+            torch.cuda.set_device(local_rank)
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+        else:
+            dist.init_process_group(backend)
+
+
+def rank_barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def over_ranks(values, world: int, op: str = "max", device=None):
+    """values reduced over the ranks (max or sum); the values themselves at one rank."""
+    if world <= 1:
+        return [float(v) for v in values]
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return [float(x) for x in t.tolist()]
+
+
+def rank_teardown(world: int):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
 def measured_peak():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -214,7 +254,10 @@ def run_batched(args):
     from paper_1404_3456_gb300 import binding, synth
 
     rank, local_rank, world = dist_env()
+    rank_setup(local_rank, world)
     torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    # instances shard by rank: each rank draws its own fragment sets
     insts = [synth.batched_instance(args.seed + 1000 * rank, i) for i in range(args.instances)]
     texts = [x["text"] for x in insts]
     inst_off = np.concatenate([[0], np.cumsum([t.size for t in texts])]).astype(np.int64)
@@ -242,12 +285,18 @@ def run_batched(args):
     torch.cuda.synchronize()
     l0 = ctx.launch_count()
     ctx.profile(True)
+    clocks = ClockSampler(local_rank)
+    rank_barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
         nc, nb = step()
     e1.record(stream)
     torch.cuda.synchronize()
+    rank_barrier(world)
+    clk = clocks.stop()
     prof = ctx.profile_read()
     ctx.profile(False)
     launches = ctx.launch_count() - l0
@@ -265,6 +314,8 @@ def run_batched(args):
     x1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = x0.elapsed_time(x1) / args.steps
+    ms, e2e_ms = over_ranks([ms, e2e_ms], world, "max", dev)
+    launches = int(over_ranks([launches], world, "sum", dev)[0])
     # one job per launch on the first M instances, and the batch of the same M
     M = min(args.solo_sample, len(texts))
     d_solo = [torch.from_numpy(t).cuda() for t in texts[:M]]
@@ -291,7 +342,7 @@ def run_batched(args):
     torch.cuda.synchronize()
     sub_s = time.perf_counter() - t0
     cpu = None
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and world == 1:
         sample = texts[:4]
         t0 = time.perf_counter()
         for t in sample:
@@ -318,10 +369,11 @@ def run_batched(args):
         "e2e": {"value": len(texts) / (e2e_ms / 1000.0), "unit": "assemblies/s",
                 "h2d_bytes_per_step": N, "d2h_bytes_per_step": int(nb) + 8 * (int(nc) + 1),
                 "ms_per_step": e2e_ms},
-        "gpu_launches": launches, "kernels": kernels,
+        "gpu_launches": launches, "clocks": clk, "kernels": kernels,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
+    rank_teardown(world)
     return 0
 
 
@@ -356,6 +408,8 @@ def run_served(args):
     rng = np.random.default_rng(args.seed)
     results = []
     srv = binding.Server(local_rank, slots=args.slots, max_batch=args.max_batch)
+    clocks = ClockSampler(local_rank)
+    clocks.start()
     for f in [float(x) for x in args.lambdas.split(",")]:
         lam = f * capacity
         arrivals = np.cumsum(rng.exponential(1.0 / lam, size=len(jobs)))
@@ -393,6 +447,7 @@ def run_served(args):
                         "one_job_per_launch": {"jobs_per_s": len(jobs) / fifo_span,
                                                "p50_ms": pctl(lat, 50), "p99_ms": pctl(lat, 99)}})
     srv.close()
+    clk = clocks.stop()
     top = results[-1]
     line = {
         "metric": "served jobs/s and p99 latency vs one-job-per-launch (continuous batching)",
@@ -408,6 +463,7 @@ def run_served(args):
         "e2e": {"value": top["served"]["jobs_per_s"], "unit": "jobs/s",
                 "h2d_bytes_per_step": float(np.mean([j["text"].size for j in jobs])),
                 "d2h_bytes_per_step": None},
+        "clocks": clk,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -425,11 +481,7 @@ def main():
     import torch
 
     rank, local_rank, world = dist_env()
-    if world > 1:
-        import torch.distributed as dist
-
-        torch.cuda.set_device(local_rank)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    rank_setup(local_rank, world)
     torch.cuda.set_device(local_rank)
     from paper_1404_3456_gb300 import binding
 
@@ -468,10 +520,7 @@ def main():
 
     # ---- timed region (device): K steps between two events on the stream
     def barrier():
-        if world > 1:
-            import torch.distributed as dist
-
-            dist.barrier()
+        rank_barrier(world)
         torch.cuda.synchronize()
 
     clocks = ClockSampler(local_rank)
@@ -533,17 +582,14 @@ def main():
         e2e_ms = x0.elapsed_time(x1) / args.steps
         e2e = {"ms": e2e_ms, "h2d": h_packed.numel() * 8 + h_toff.numel() * 8, "d2h": 8 * N}
 
-    if world > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([ms, e2e["ms"] if e2e else 0.0], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t[0])
-        if e2e:
-            e2e["ms"] = float(t[1])
+    ms, e2e_max = over_ranks([ms, e2e["ms"] if e2e else 0.0], world, "max", dev)
+    if e2e:
+        e2e["ms"] = e2e_max
+    launches = int(over_ranks([launches], world, "sum", dev)[0])
     value = N * world / (ms / 1000.0) / 1e6
 
     if rank != 0:
+        rank_teardown(world)
         return 0
     # ---- roofline of the dominant kernel class
     peak, peak_src = measured_peak()
@@ -575,7 +621,7 @@ def main():
                      "share": v["ms"] / max(1e-9, sum(x["ms"] for x in prof.values()))}
                  for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])}
     cpu = None
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and world == 1:   # the oracle's baseline: rank 0 at N = 1 only
         if large:
             from paper_1404_3456_gb300 import synth
 
@@ -609,10 +655,7 @@ def main():
         "kernels": breakdown,
     }
     print(json.dumps(line), flush=True)
-    if world > 1:
-        import torch.distributed as dist
-
-        dist.destroy_process_group()
+    rank_teardown(world)
     return 0
 
 

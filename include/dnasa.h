@@ -7,7 +7,8 @@
  * through a suffix array over the fragments (Sec. IV), built on the GPU by
  * radix sorting (Sec. IV, Algorithm 1 in Sec. V), then answers the
  * prefix/suffix relations between fragments by searching that suffix array
- * (Sec. IV, "binary search ... whether one fragment is the prefix of X").
+ * (Sec. IV: a binary search tells whether some fragment starts with a given
+ * string).
  *
  * Conventions shared by every entry point
  * ---------------------------------------
@@ -203,7 +204,7 @@ int dnasa_sort_pairs_noalloc(uint64_t *keys, uint32_t *vals, int64_t n, int key_
 int dnasa_pack(dnasa_ctx *ctx, const uint8_t *text, int64_t N, uint64_t *packed,
                int64_t *toff, int64_t toff_cap, int64_t *n_reads, void *stream);
 
-/* ---- suffix array (Sec. IV "sorted array Pos of all the suffixes") ---- */
+/* ---- suffix array (Sec. IV: all suffixes in sorted order, the array Pos) -- */
 
 /* Builds the suffix array of the packed text by prefix doubling: a radix sort of
  * packed initial keys (the first h0 <= 29 bases and the distance to the

@@ -4,9 +4,9 @@
 // SA[j-1] and SA[j], never counting a '$' (so no LCP crosses a fragment end),
 // and 0 where an instance of a batch starts.  Each thread compares one adjacent
 // pair 32 bases at a time: XOR of two packed words and a count of leading zero
-// bits, capped by the bases left in both fragments.  The paper needs these
-// prefix lengths for its "is one fragment a prefix of X" tests (Sec. IV); they
-// drive the containment test and the overlap interval scan here.
+// bits, capped by the bases left in both fragments.  The paper's prefix tests
+// between fragments (Sec. IV) rest on these common-prefix lengths; here they
+// drive the containment test and the overlap interval scan.
 #include <algorithm>
 
 #include "common.cuh"
@@ -41,7 +41,7 @@ __device__ __forceinline__ PairInfo pair_info(const TextDesc &t, const uint32_t 
 }
 
 // One thread per adjacent pair: the first 64 bases.  Pairs still equal there
-// (repeats) are queued for k_lcp_long.
+// (repeats) are queued for k_lcp_chain.
 __global__ void __launch_bounds__(256) k_lcp(TextDesc t, const uint32_t *__restrict__ sa,
                                              int32_t *__restrict__ lcp, uint32_t *__restrict__ qpos,
                                              uint32_t *__restrict__ qj,

@@ -248,11 +248,11 @@ int overlap_impl(dnasa_ctx *ctx, const TextDesc &t, const uint32_t *sa32, const 
 
         DNASA_CUDA(ctx, cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * 8, s));
         if (!isa_in) {
-            LaunchScope ls_(ctx, PK_OVERLAP, s, 0);
+            LaunchScope ls_(ctx, PK_OVERLAP, s, 8.0 * N);   // read sa[j], write isa[sa[j]]
             k_isa<<<grid_for(ctx, N), 256, 0, s>>>(sa32, N, isa_ws);
         }
         {
-            LaunchScope ls_(ctx, PK_OVERLAP, s, 0);
+            LaunchScope ls_(ctx, PK_OVERLAP, s, 24.0 * nr);   // toff, isa, key and value
             k_read_keys<<<grid_for(ctx, nr), 256, 0, s>>>(t, isa, rk[0], rv[0], cnt + CNT_TMP);
         }
         DNASA_CUDA(ctx, cudaGetLastError());
@@ -261,7 +261,7 @@ int overlap_impl(dnasa_ctx *ctx, const TextDesc &t, const uint32_t *sa32, const 
                                              bits_for((uint64_t)(N - 1)), false, tile, &which, s));
         const uint32_t *Rslot = rk[which], *R = rv[which];
         {
-            LaunchScope ls_(ctx, PK_OVERLAP, s, 0);
+            LaunchScope ls_(ctx, PK_OVERLAP, s, 24.0 * nr);   // R, two starts, LCP_R
             k_lcp_r<<<grid_for(ctx, nr), 256, 0, s>>>(t, R, lcpr);
         }
         DNASA_CUDA(ctx, cudaMemcpyAsync(ctx->pinned, cnt + CNT_TMP, 8, cudaMemcpyDeviceToHost, s));
@@ -276,7 +276,8 @@ int overlap_impl(dnasa_ctx *ctx, const TextDesc &t, const uint32_t *sa32, const 
         qa.kb = kb; qa.lb = lb; qa.cand = ck[0]; qa.cap = (unsigned long long)cand_cap;
         qa.count = cnt + CNT_CAND;
         {
-            LaunchScope ls_(ctx, PK_OVERLAP, s, 0);
+            // per position: isa[q] (and its fragment id), one packed word
+            LaunchScope ls_(ctx, PK_OVERLAP, s, (t.fid ? 8.25 : 4.25) * N);
             k_query<<<grid_for(ctx, N), 256, 0, s>>>(t, qa);
         }
         DNASA_CUDA(ctx, cudaGetLastError());
@@ -296,19 +297,19 @@ int overlap_impl(dnasa_ctx *ctx, const TextDesc &t, const uint32_t *sa32, const 
             DNASA_TRY(radix_sort_pairs<unsigned long long>(ctx, rs2, ck, nov, ncand, nullptr,
                                                            2 * kb + lb, false, tile, &which2, s));
             {
-                LaunchScope ls_(ctx, PK_OVERLAP, s, 0);
+                LaunchScope ls_(ctx, PK_OVERLAP, s, 9.0 * ncand);
                 k_unique_flags<<<grid_for(ctx, ncand), 256, 0, s>>>(ck[which2], ncand, lb, flags);
             }
             DNASA_TRY(compact_flags(ctx, a, flags, ncand, cidx, cnt + CNT_EDGES, s));
             {
-                LaunchScope ls_(ctx, PK_OVERLAP, s, 0);
+                LaunchScope ls_(ctx, PK_OVERLAP, s, 20.0 * ncand);
                 k_emit_edges<<<grid_for(ctx, ncand), 256, 0, s>>>(ck[which2], cidx, cnt + CNT_EDGES, kb,
                                                                  lb, edges, cap);
             }
             DNASA_CUDA(ctx, cudaGetLastError());
         }
         {
-            LaunchScope ls_(ctx, PK_OVERLAP, s, 0);
+            LaunchScope ls_(ctx, PK_OVERLAP, s, 24.0 * nr);
             k_contained<<<grid_for(ctx, nr), 256, 0, s>>>(t, sa32, isa, lcp, contained);
         }
         DNASA_CUDA(ctx, cudaGetLastError());
