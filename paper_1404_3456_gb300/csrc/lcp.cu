@@ -40,8 +40,11 @@ __device__ __forceinline__ PairInfo pair_info(const TextDesc &t, const uint32_t 
     return r;
 }
 
-// One thread per adjacent pair: the first 64 bases.  Pairs still equal there
-// (repeats) are queued for k_lcp_chain.
+// One thread per adjacent pair: the first 64 bases.  Each lane fetches the
+// first 32 bases of its own suffix SA[j] and takes those of SA[j-1] from the
+// lane before it (lane 0 fetches both), so a pair costs one random text fetch
+// instead of two.  Pairs still equal after 64 bases (repeats) are queued for
+// k_lcp_chain.
 __global__ void __launch_bounds__(256) k_lcp(TextDesc t, const uint32_t *__restrict__ sa,
                                              int32_t *__restrict__ lcp, uint32_t *__restrict__ qpos,
                                              uint32_t *__restrict__ qj,
@@ -49,23 +52,40 @@ __global__ void __launch_bounds__(256) k_lcp(TextDesc t, const uint32_t *__restr
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane; b < t.N; b += stride) {
-        int64_t j = b + lane;
+        const int64_t j = b + lane;
+        const bool in = j < t.N;
+        // own suffix q = SA[j]: base coordinate, bases left in its fragment, first 32 bases
+        int64_t q = in ? (int64_t)sa[j] : 0;
+        int64_t rq = in ? frag_of(t, q) : 0;
+        int64_t left_q = in ? __ldg(t.toff + rq + 1) - 1 - q : 0;
+        uint64_t bq = (uint64_t)(q - rq);
+        uint64_t wq = in ? bases32(t.packed, bq) : 0ull;
+        // the previous suffix p = SA[j-1]: from the lane before, or fetched by lane 0
+        int64_t left_p = __shfl_up_sync(0xffffffffu, left_q, 1);
+        uint64_t bp = __shfl_up_sync(0xffffffffu, bq, 1);
+        uint64_t wp = __shfl_up_sync(0xffffffffu, wq, 1);
         bool queue = false;
-        if (j < t.N) {
+        if (in) {
             if (j == 0 || instance_start(t, j)) {
                 lcp[j] = 0;
             } else {
-                PairInfo pi = pair_info(t, sa, j);
-                int64_t h = 0;
-                bool done = false;
-#pragma unroll
-                for (int w = 0; w < kShortBases / 32; ++w) {
-                    if (h >= pi.m) { done = true; break; }
-                    uint64_t d = bases32(t.packed, pi.bp + h) ^ bases32(t.packed, pi.bq + h);
-                    if (d) { h += __clzll((long long)d) >> 1; done = true; break; }
-                    h += 32;
+                if (lane == 0) {
+                    const int64_t p = sa[j - 1];
+                    const int64_t rp = frag_of(t, p);
+                    left_p = __ldg(t.toff + rp + 1) - 1 - p;
+                    bp = (uint64_t)(p - rp);
+                    wp = bases32(t.packed, bp);
                 }
-                if (done || h >= pi.m) lcp[j] = (int32_t)min(h, pi.m);
+                const int64_t m = min(left_p, left_q);
+                int64_t h;
+                uint64_t d = wp ^ wq;
+                if (d || m <= 32) {
+                    h = d ? (int64_t)(__clzll((long long)d) >> 1) : 32;
+                } else {
+                    d = bases32(t.packed, bp + 32) ^ bases32(t.packed, bq + 32);
+                    h = d ? 32 + (int64_t)(__clzll((long long)d) >> 1) : kShortBases;
+                }
+                if (h < kShortBases || h >= m) lcp[j] = (int32_t)min(h, m);
                 else queue = true;
             }
         }
