@@ -231,17 +231,20 @@ def pctl(xs, q):
     return xs[k]
 
 
-def roofline_of(prof, peak, peak_src):
+ROOF_TIMING = "per-launch CUDA events on the launching stream, second pass of the same K steps"
+
+
+def roofline_of(prof, peak, peak_src, steps):
     if not prof:
         return None, {}
     name, d = max(prof.items(), key=lambda kv: kv[1]["ms"])
     achieved = d["bytes"] / (d["ms"] / 1000.0) / 1e9 if d["ms"] > 0 else 0.0
     total = sum(x["ms"] for x in prof.values())
-    kernels = {k: {"launches": v["launches"], "ms": v["ms"], "share": v["ms"] / total}
+    kernels = {k: {"launches": v["launches"], "ms_per_step": v["ms"] / steps, "share": v["ms"] / total}
                for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])}
     return ({"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
              "frac": achieved / peak, "peak_source": peak_src, "traffic": None,
-             "launches": d["launches"]}, kernels)
+             "launches": d["launches"], "timing": ROOF_TIMING}, kernels)
 
 
 def run_batched(args):
@@ -284,7 +287,6 @@ def run_batched(args):
         step()
     torch.cuda.synchronize()
     l0 = ctx.launch_count()
-    ctx.profile(True)
     clocks = ClockSampler(local_rank)
     rank_barrier(world)
     torch.cuda.synchronize()
@@ -297,10 +299,15 @@ def run_batched(args):
     torch.cuda.synchronize()
     rank_barrier(world)
     clk = clocks.stop()
-    prof = ctx.profile_read()
-    ctx.profile(False)
     launches = ctx.launch_count() - l0
     ms = e0.elapsed_time(e1) / args.steps
+    # per-kernel durations for the roofline: the same steps with per-launch events
+    ctx.profile(True)
+    for _ in range(args.steps):
+        step()
+    torch.cuda.synchronize()
+    prof = ctx.profile_read()
+    ctx.profile(False)
     # end to end: text from pinned host memory, contigs and offsets back
     h_contigs = torch.empty(N, dtype=torch.uint8).pin_memory()
     x0, x1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -352,7 +359,7 @@ def run_batched(args):
                "sample": f"oracle assemble of the first {len(sample)} instances "
                          f"({sum(t.size for t in sample):,} symbols), {dt:.1f} s"}
     peak, src = measured_peak()
-    roof, kernels = roofline_of(prof, peak, src)
+    roof, kernels = roofline_of(prof, peak, src, args.steps)
     value = len(texts) * world / (ms / 1000.0)
     line = {
         "metric": "batched assemblies/s (assemble_batched, 4096 fragment sets)", "value": value,
@@ -527,7 +534,6 @@ def main():
     barrier()
     clocks.start()
     l0 = ctx.launch_count()
-    ctx.profile(True)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -535,12 +541,19 @@ def main():
         step()
     e1.record(stream)
     torch.cuda.synchronize()
-    prof = ctx.profile_read()
-    ctx.profile(False)
     launches = ctx.launch_count() - l0
     barrier()
     clk = clocks.stop()
     ms = e0.elapsed_time(e1) / args.steps
+    # the same K steps again with an event pair around every kernel launch: the
+    # per-kernel durations of the roofline (kept out of the step time above,
+    # which the per-launch events would lengthen by a few percent)
+    ctx.profile(True)
+    for _ in range(args.steps):
+        step()
+    torch.cuda.synchronize()
+    prof = ctx.profile_read()
+    ctx.profile(False)
 
     # SA-only time of one more step, for information
     s0 = torch.cuda.Event(enable_timing=True)
@@ -616,7 +629,7 @@ def main():
                     "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_src,
                     "traffic": traffic, "launches": d["launches"],
                     "algorithmic_bytes_per_launch": d["bytes"] / d["launches"],
-                    "avg_launch_ms": d["ms"] / d["launches"]}
+                    "avg_launch_ms": d["ms"] / d["launches"], "timing": ROOF_TIMING}
     breakdown = {k: {"launches": v["launches"], "ms_per_step": v["ms"] / args.steps,
                      "share": v["ms"] / max(1e-9, sum(x["ms"] for x in prof.values()))}
                  for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])}

@@ -353,21 +353,55 @@ __global__ void __launch_bounds__(kRrThreads) k_rerank(
     }
 }
 
-// Applies the staged rank writes, bucket-major: CTA c handles bucket
-// c / per_bucket, chunk c % per_bucket (CTAs are issued roughly in index order,
-// so one bucket's 8 MB of rank[] is written at a time).
+// Applies the staged rank writes, bucket-major: the buckets' filled parts are
+// taken as one concatenated list, each CTA a kApplyItems slice of it, so the
+// grid matches the items staged (CTAs are issued roughly in index order, so one
+// bucket's 8 MB of rank[] is written at a time).
 constexpr int kApplyItems = 4096;
 __global__ void __launch_bounds__(256) k_rank_apply(const uint2 *__restrict__ stage,
                                                     const uint32_t *__restrict__ bucket_fill,
-                                                    int bshift, int per_bucket, int64_t N,
+                                                    int nbuckets, int bshift, int64_t N,
                                                     uint32_t *__restrict__ rank, uint32_t *err) {
-    const int b = blockIdx.x / per_bucket;
-    const int chunk = blockIdx.x % per_bucket;
-    const uint32_t fill = bucket_fill[b];
-    const uint64_t b0 = (uint64_t)b << bshift;
-    for (uint32_t i = chunk * kApplyItems + threadIdx.x;
-         i < fill && i < (uint32_t)(chunk + 1) * kApplyItems; i += 256) {
-        uint2 pr = stage[b0 + i];
+    __shared__ uint32_t s_off[kMaxBuckets + 1];   // exclusive prefix of the fills
+    __shared__ uint32_t s_tmp[256 / 32 + 1];
+    {
+        static_assert(kMaxBuckets == 4 * 256, "four buckets per thread");
+        uint32_t c[4], sum = 0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int bb = 4 * threadIdx.x + q;
+            c[q] = bb < nbuckets ? bucket_fill[bb] : 0u;
+            sum += c[q];
+        }
+        uint32_t tot;
+        uint32_t run = block_exclusive_sum<256>(sum, s_tmp, &tot);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int bb = 4 * threadIdx.x + q;
+            if (bb < nbuckets) s_off[bb] = run;
+            run += c[q];
+        }
+        if (threadIdx.x == 0) s_off[nbuckets] = tot;
+    }
+    __syncthreads();
+    const uint32_t total = s_off[nbuckets];
+    const uint32_t f0 = blockIdx.x * kApplyItems;
+    if (f0 >= total) return;
+    const uint32_t f1 = min(total, f0 + kApplyItems);
+    // first bucket holding flat index f0
+    int b = 0;
+    {
+        int lo = 0, hi = nbuckets - 1;
+        while (lo < hi) {
+            int m = (lo + hi + 1) >> 1;
+            if (s_off[m] <= f0) lo = m; else hi = m - 1;
+        }
+        b = lo;
+    }
+    for (uint32_t f = f0 + threadIdx.x; f < f1; f += 256) {
+        while (f >= s_off[b + 1]) ++b;   // non-decreasing f per thread
+        const uint64_t si = ((uint64_t)b << bshift) + (f - s_off[b]);
+        const uint2 pr = stage[si];
         if ((int64_t)pr.x < N && (pr.x >> bshift) == (uint32_t)b) rank[pr.x] = pr.y;
         else atomicOr(err, DERR_BOUNDS);
     }
@@ -976,12 +1010,10 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
     while (((N - 1) >> bshift) + 1 > kMaxBuckets) ++bshift;
     const int nbuckets = (int)(((N - 1) >> bshift) + 1);
     auto apply_ranks = [&](int64_t n_items, int stage_buf) -> int {
-        int64_t per = std::min<int64_t>((int64_t)1 << bshift, n_items);
-        int per_bucket = std::max(1, ceil_div(per, kApplyItems));
         LaunchScope ls_(ctx, PK_APPLY, s, 12.0 * n_items);
-        k_rank_apply<<<nbuckets * per_bucket, 256, 0, s>>>(
-            reinterpret_cast<const uint2 *>(keys[stage_buf]), bucket_fill, bshift, per_bucket, N,
-            rank, &c->err);
+        k_rank_apply<<<std::max(1, ceil_div(n_items, kApplyItems)), 256, 0, s>>>(
+            reinterpret_cast<const uint2 *>(keys[stage_buf]), bucket_fill, nbuckets, bshift, N, rank,
+            &c->err);
         return DNASA_OK;
     };
     auto read_counters = [&](int64_t *kept, int64_t *ngroups, int64_t *maxgroup) -> int {
