@@ -91,6 +91,7 @@ constexpr int kMaxBuckets = 1024;
 
 struct RerankOut {
     int64_t N;          // text length: bound of every SA slot and text position
+    int kb;             // rounds >= 1: keys hold (old head rank << kb) | rank[i+h]
     uint32_t *sa, *rank;
     uint32_t *nslots, *npos, *nhead;
     uint2 *groups;
@@ -101,7 +102,9 @@ struct RerankOut {
     int pb;             // round 0 only: keys hold (key << pb) | position, no value array
 };
 
-// Shared memory of one rerank tile (dynamic, > 48 KB).
+// Shared memory of one rerank tile (dynamic, > 48 KB).  Round 0 needs neither
+// the slots (slot = item index) nor the old head ranks.
+template <bool ROUND0>
 struct RerankSmem {
     union {
         unsigned long long k[kRrTile + 2];   // keys with one halo key on each side
@@ -111,7 +114,8 @@ struct RerankSmem {
         } o;
     } u;
     uint32_t v[kRrTile];                 // positions
-    uint32_t sl[kRrTile];                // slots (rounds >= 1)
+    uint32_t sl[ROUND0 ? 1 : kRrTile];   // slots (rounds >= 1)
+    uint32_t oh[ROUND0 ? 1 : kRrTile];   // old head rank (rounds >= 1)
     uint8_t f[kRrTile];                  // bit0 head, bit1 next is head
     int64_t tmp[kRrThreads / 32 + 1];
     int64_t incmax[kRrThreads];
@@ -130,7 +134,7 @@ __global__ void __launch_bounds__(kRrThreads) k_rerank(
     const uint32_t *__restrict__ slots, int64_t n_host, const unsigned long long *__restrict__ d_n,
     int h0, RerankOut o, unsigned long long *status, uint32_t *tile_ctr, uint32_t *err) {
     extern __shared__ __align__(16) unsigned char rr_raw[];
-    RerankSmem &S = *reinterpret_cast<RerankSmem *>(rr_raw);
+    RerankSmem<ROUND0> &S = *reinterpret_cast<RerankSmem<ROUND0> *>(rr_raw);
     const int tid = threadIdx.x;
     if (tid == 0) {
         S.tile = atomicAdd(tile_ctr, 1u);
@@ -150,6 +154,7 @@ __global__ void __launch_bounds__(kRrThreads) k_rerank(
         unsigned long long w = (j >= 0 && j < n) ? keys[j] : 0ull;
         S.u.k[i] = w >> pb;
         if (pb && i >= 1 && i <= tile_n) S.v[i - 1] = (uint32_t)(w & ((1ull << pb) - 1ull));
+        if (!ROUND0 && i >= 1 && i <= tile_n) S.oh[i - 1] = (uint32_t)(w >> o.kb);
     }
     for (int i = tid; i < tile_n; i += kRrThreads) {
         if (!pb) S.v[i] = vals[base + i];
@@ -312,16 +317,18 @@ __global__ void __launch_bounds__(kRrThreads) k_rerank(
         if (lane == 0 && my_maxsize) atomicMax(o.maxgroup, (unsigned long long)my_maxsize);
     }
     __syncthreads();
-    // ---- striped, coalesced writes; rank[pos] goes to its position bucket
+    // ---- striped, coalesced writes; rank[pos] goes to its position bucket,
+    // unless it is unchanged (rounds >= 1: the item's group head kept its slot)
     const int nb = (int)((o.N + (1ll << o.bshift) - 1) >> o.bshift);
     for (int b = tid; b < nb; b += kRrThreads) S.bcnt[b] = 0;
     __syncthreads();
+    auto restage = [&](int li) -> bool { return ROUND0 || S.u.o.head[li] != S.oh[li]; };
     uint32_t bidx[kRrItems];
 #pragma unroll
     for (int i = 0; i < kRrItems; ++i) {
         int li = tid + i * kRrThreads;
         bidx[i] = 0;
-        if (li < tile_n) bidx[i] = atomicAdd(&S.bcnt[S.v[li] >> o.bshift], 1u);
+        if (li < tile_n && restage(li)) bidx[i] = atomicAdd(&S.bcnt[S.v[li] >> o.bshift], 1u);
     }
     __syncthreads();
     for (int b = tid; b < nb; b += kRrThreads) {
@@ -344,7 +351,7 @@ __global__ void __launch_bounds__(kRrThreads) k_rerank(
             continue;
         }
         o.sa[slot] = pos;
-        o.stage[st] = make_uint2(pos, hs);
+        if (restage(li)) o.stage[st] = make_uint2(pos, hs);
         if (kp >= 0) {
             o.nslots[kp] = slot;
             o.npos[kp] = pos;
@@ -976,7 +983,7 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
     // once per process (thread-safe static initialisation)
     static const cudaError_t smem_set = [] {
         cudaError_t e = cudaFuncSetAttribute(k_rerank<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)sizeof(RerankSmem));
+                                             (int)sizeof(RerankSmem<true>));
         if (e != cudaSuccess) return e;
         e = cudaFuncSetAttribute(k_seg_radix<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)seg_radix_smem<4>());
@@ -988,7 +995,7 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
                                  (int)seg_radix_smem<24>());
         if (e != cudaSuccess) return e;
         return cudaFuncSetAttribute(k_rerank<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)sizeof(RerankSmem));
+                                    (int)sizeof(RerankSmem<false>));
     }();
     DNASA_CUDA(ctx, smem_set);
     DevCtrl *c = ctx->ctrl;
@@ -1036,6 +1043,7 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
     ro.maxgroup = cnt + CNT_MAXGROUP;
     ro.bucket_fill = bucket_fill;
     ro.bshift = bshift;
+    ro.kb = b;
     ro.pb = pb;
 
     // ---- round 0: initial keys, sort, rerank
@@ -1056,7 +1064,7 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
         ro.stage = reinterpret_cast<uint2 *>(keys[which ^ 1]);   // the free key buffer
         {
             LaunchScope ls_(ctx, PK_RERANK, s, 20.0 * N);
-            k_rerank<true><<<rr_tiles, kRrThreads, sizeof(RerankSmem), s>>>(keys[which], vals[which], nullptr, N, nullptr,
+            k_rerank<true><<<rr_tiles, kRrThreads, sizeof(RerankSmem<true>), s>>>(keys[which], vals[which], nullptr, N, nullptr,
                                                            h0, ro, rr_status, c->tile_ctr + 32, &c->err);
         }
         DNASA_CUDA(ctx, cudaGetLastError());
@@ -1164,7 +1172,7 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
         int tiles = ceil_div(kept, kRrTile);
         {
             LaunchScope ls_(ctx, PK_RERANK, s, 24.0 * kept);
-            k_rerank<false><<<tiles, kRrThreads, sizeof(RerankSmem), s>>>(keys[0], vals[0], L[cur][0], kept,
+            k_rerank<false><<<tiles, kRrThreads, sizeof(RerankSmem<false>), s>>>(keys[0], vals[0], L[cur][0], kept,
                                                          nullptr, h0, ro, rr_status, c->tile_ctr + 32,
                                                          &c->err);
         }
