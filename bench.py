@@ -61,7 +61,7 @@ def parse():
     ap.add_argument("--solo-sample", type=int, default=256,
                     help="batched: instances timed one job per launch")
     ap.add_argument("--jobs", type=int, default=48, help="served: distinct jobs in the trace")
-    ap.add_argument("--lambdas", default="0.5,0.9,1.25",
+    ap.add_argument("--lambdas", default="0.25,0.5,0.75,0.9,1.0,1.25",
                     help="served: arrival rates as multiples of one-job-per-launch capacity")
     ap.add_argument("--no-tune", action="store_true", help="skip the build-option autotuner")
     ap.add_argument("--slots", type=int, default=2)
@@ -247,6 +247,71 @@ def roofline_of(prof, peak, peak_src, steps):
              "launches": d["launches"], "timing": ROOF_TIMING}, kernels)
 
 
+def _oracle_assemble(text):
+    """Pool worker: the oracle's whole method on one fragment set (host only)."""
+    import oracle
+
+    oracle.assemble(text, 31)
+    return int(text.size)
+
+
+def oracle_all_cores(texts):
+    """The oracle, unchanged, on every host core at once: one instance per worker
+    process (spawned, so that no worker inherits the GPU context)."""
+    import multiprocessing as mp
+
+    cores = os.cpu_count() or 1
+    with mp.get_context("spawn").Pool(cores) as pool:
+        pool.map(_oracle_assemble, texts[:1])   # workers up and the library loaded
+        t0 = time.perf_counter()
+        pool.map(_oracle_assemble, texts, chunksize=1)
+        dt = time.perf_counter() - t0
+    return len(texts) / dt, cores, dt
+
+
+def large_reads_stage(args, ctx, binding, genome_np, dev, min_overlap=31, n_reads=10_000_000,
+                      read_len=150):
+    """Overlap search over 10 M reads of 150 bp drawn from the 1.5 Gbp genome (1x):
+    SA (int32) and LCP of the reads' text, then every suffix of every read with at
+    least min_overlap bases queried against the read starts.  One warm-up run,
+    then one timed run per stage (CUDA events)."""
+    import torch
+
+    from paper_1404_3456_gb300 import synth
+
+    text_np, _ = synth.large_reads(args.seed, genome_np, n_reads, read_len)
+    N = int(text_np.size)
+    text = torch.from_numpy(text_np).to(dev)
+    packed, toff, nr = binding.pack_text(ctx, text)
+    del text
+    sa = torch.empty(N, dtype=torch.int32, device=dev)
+    lcp = torch.empty(N, dtype=torch.int32, device=dev)
+    edges = torch.empty((64 << 20, 3), dtype=torch.int32, device=dev)   # first 64 M edges kept
+    contained = torch.empty(nr, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    ne = 0
+    for rep in range(2):
+        ev[0].record(stream)
+        binding.sa_build(ctx, packed, toff, nr, N, sa)
+        ev[1].record(stream)
+        binding.lcp_build(ctx, packed, toff, nr, N, sa, lcp)
+        ev[2].record(stream)
+        ne = binding.overlap_search(ctx, packed, toff, nr, N, sa, lcp, min_overlap, edges, contained,
+                                    count_only_past_cap=True)
+        ev[3].record(stream)
+        torch.cuda.synchronize()
+    sa_ms, lcp_ms, ovl_ms = (ev[i].elapsed_time(ev[i + 1]) for i in range(3))
+    queries = nr * max(0, read_len - min_overlap)   # suffixes r_j[o..], o >= 1, >= min_overlap bases
+    return {"workload": f"{nr:,} reads x {read_len} bp from the same genome (1x), min overlap "
+                        f"{min_overlap}; N = {N:,}", "sa_ms": sa_ms, "lcp_ms": lcp_ms,
+            "overlap_ms": ovl_ms, "queries": queries,
+            "overlap_queries_per_s": queries / (ovl_ms / 1000.0), "edges": int(ne),
+            "edges_stored": int(min(ne, edges.shape[0])),
+            "contained": int(contained.sum().item()),
+            "sa_msuffix_per_s": N / (sa_ms / 1000.0) / 1e6}
+
+
 def run_batched(args):
     """Batched workload: independent fragment sets (genome log-uniform 2-200 kbp,
     reads U{100..1000} at 8x, min overlap 31) assembled by one assemble_batched
@@ -348,7 +413,7 @@ def run_batched(args):
     binding.assemble_batched(ctx, d_sub, sub_off, 31, contigs, off, ioff[: M + 1], sub_opts)
     torch.cuda.synchronize()
     sub_s = time.perf_counter() - t0
-    cpu = None
+    cpu, cpu_all = None, None
     if not args.no_cpu_baseline and world == 1:
         sample = texts[:4]
         t0 = time.perf_counter()
@@ -358,6 +423,11 @@ def run_batched(args):
         cpu = {"value": len(sample) / dt, "unit": "assemblies/s", "cores": 1, "kind": "oracle",
                "sample": f"oracle assemble of the first {len(sample)} instances "
                          f"({sum(t.size for t in sample):,} symbols), {dt:.1f} s"}
+        many = texts[: 4 * (os.cpu_count() or 1)]
+        rate, cores, dt = oracle_all_cores(many)
+        cpu_all = {"value": rate, "unit": "assemblies/s", "cores": cores, "kind": "oracle",
+                   "sample": f"oracle assemble of the first {len(many)} instances, one per worker "
+                             f"process, {dt:.1f} s"}
     peak, src = measured_peak()
     roof, kernels = roofline_of(prof, peak, src, args.steps)
     value = len(texts) * world / (ms / 1000.0)
@@ -371,6 +441,7 @@ def run_batched(args):
                    "msuffix_per_s": N * world / (ms / 1000.0) / 1e6,
                    "one_job_per_launch": {"instances": M, "s": solo_s, "assemblies_per_s": M / solo_s},
                    "batched_same_instances": {"instances": M, "s": sub_s, "assemblies_per_s": M / sub_s},
+                   "oracle_all_cores": cpu_all,
                    "autotuned": tuned},
         "roofline": roof, "cpu_baseline": cpu,
         "e2e": {"value": len(texts) / (e2e_ms / 1000.0), "unit": "assemblies/s",
@@ -497,7 +568,8 @@ def main():
     if large:   # 1.5 Gbp, int64 SA (85 % i.i.d., 10 % tandem, 5 % copies of a 6 kbp element)
         from paper_1404_3456_gb300 import synth
 
-        text_np = synth.genome_text(synth.large_genome(args.seed))
+        genome_np = synth.large_genome(args.seed)
+        text_np = synth.genome_text(genome_np)
         args.no_e2e = True
     else:
         text_np = genome_text(args.seed, args.genome)
@@ -595,6 +667,11 @@ def main():
         e2e_ms = x0.elapsed_time(x1) / args.steps
         e2e = {"ms": e2e_ms, "h2d": h_packed.numel() * 8 + h_toff.numel() * 8, "d2h": 8 * N}
 
+    reads_info = None
+    if large:   # the 10 M x 150 bp reads of the same genome: their own SA, LCP, overlap search
+        del sa, lcp, packed, toff
+        torch.cuda.empty_cache()
+        reads_info = large_reads_stage(args, ctx, binding, genome_np, dev)
     ms, e2e_max = over_ranks([ms, e2e["ms"] if e2e else 0.0], world, "max", dev)
     if e2e:
         e2e["ms"] = e2e_max
@@ -625,7 +702,10 @@ def main():
                         traffic = tj["dram_per_algorithmic_byte"] * d["bytes"] / d["launches"]
             except Exception:
                 traffic = None
+        all_bytes = sum(v["bytes"] for v in prof.values())
+        all_ms = sum(v["ms"] for v in prof.values())
         roofline = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak,
+                    "whole_path_frac": all_bytes / (all_ms / 1000.0) / 1e9 / peak if all_ms else None,
                     "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_src,
                     "traffic": traffic, "launches": d["launches"],
                     "algorithmic_bytes_per_launch": d["bytes"] / d["launches"],
@@ -657,7 +737,7 @@ def main():
                    "l2": "working set >> L2 (no flush needed)",
                    "rounds": trace["rounds"], "finished_direct": trace["finished_direct"],
                    "active_per_round": trace["active"], "sa_only_ms": sa_only_ms,
-                   "autotuned": tuned},
+                   "autotuned": tuned, **({"reads": reads_info} if reads_info else {})},
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": ({"value": N * world / (e2e["ms"] / 1000.0) / 1e6, "unit": UNIT,

@@ -249,15 +249,19 @@ def lcp_build(ctx: Context, packed, toff, n_reads: int, N: int, sa, lcp, stream=
 
 
 def overlap_search(ctx: Context, packed, toff, n_reads: int, N: int, sa, lcp, min_overlap: int,
-                   edges, contained, stream=None) -> int:
-    """edges: int32 tensor (cap, 3) of (j, k, L).  Returns the edge count."""
+                   edges, contained, stream=None, count_only_past_cap: bool = False) -> int:
+    """edges: int32 tensor (cap, 3) of (j, k, L).  Returns the edge count.  With
+    count_only_past_cap, an edge set larger than the buffer is not an error: the
+    first `cap` edges are written and the full count is returned."""
     width = I64 if sa.dtype == torch.int64 else I32
     n = ctypes.c_int64(0)
     cap = edges.shape[0] if edges is not None else 0
-    ctx.check(lib().overlap_search(ctx.handle, _ptr(packed), _ptr(toff), n_reads, N, _ptr(sa),
-                                   _ptr(lcp), width, min_overlap,
-                                   _ptr(edges) if cap else None, cap, ctypes.byref(n),
-                                   _ptr(contained), _stream(stream)))
+    rc = lib().overlap_search(ctx.handle, _ptr(packed), _ptr(toff), n_reads, N, _ptr(sa),
+                              _ptr(lcp), width, min_overlap,
+                              _ptr(edges) if cap else None, cap, ctypes.byref(n),
+                              _ptr(contained), _stream(stream))
+    if not (count_only_past_cap and rc == CAPACITY):
+        ctx.check(rc)
     return n.value
 
 

@@ -211,9 +211,10 @@ def large_reads(seed: int, genome: np.ndarray, n_reads: int = 10_000_000, read_l
     """n_reads fragments of read_len at uniform starts, as one '$'-joined text."""
     rng = rng_for(seed, 6)
     starts = rng.integers(0, genome.size - read_len + 1, size=n_reads)
-    idx = starts[:, None] + np.arange(read_len)[None, :]
-    body = genome[idx]
     text = np.empty((n_reads, read_len + 1), dtype=np.uint8)
-    text[:, :read_len] = body
+    cols = np.arange(read_len)[None, :]
+    for c0 in range(0, n_reads, 1 << 20):   # bounded index arrays
+        c1 = min(n_reads, c0 + (1 << 20))
+        text[c0:c1, :read_len] = genome[starts[c0:c1, None] + cols]
     text[:, read_len] = SEP
     return text.ravel(), starts
