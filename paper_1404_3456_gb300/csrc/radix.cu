@@ -489,8 +489,6 @@ template int radix_sort_pairs<unsigned long long>(dnasa_ctx *, const RadixScratc
                                                   const unsigned long long *, int, bool, int,
                                                   int *, cudaStream_t, int, int);
 
-// Histogram accumulation entry used by fused producers: nothing here; the
-// producer kernels call radix_digit_count() below.
 
 }  // namespace dnasa
 

@@ -34,38 +34,56 @@ constexpr int kInitItems = 8;
 
 // pb > 0: the position is packed under the key, (key << pb) | p, and no value
 // array is written (a keys-only sort then moves 8 instead of 12 bytes per item).
+// The digit histograms of every pass of the initial sort (8-bit digits of the
+// sort word from bit lo_bit on) are counted here too, so that the sort does not
+// read the keys once more for them.  Grid-stride over chunks of 32 * kInitItems
+// positions per warp.
 __global__ void __launch_bounds__(kInitThreads) k_init_keys(TextDesc t, int h0, int inst_shift,
-                                                            int pb,
+                                                            int pb, int passes, int lo_bit,
+                                                            uint32_t *__restrict__ ghist,
                                                             unsigned long long *__restrict__ keys,
                                                             uint32_t *__restrict__ vals) {
+    __shared__ uint32_t sh[8 * 256];
+    for (int i = threadIdx.x; i < passes * 256; i += kInitThreads) sh[i] = 0;
+    __syncthreads();
     const int lane = threadIdx.x & 31;
-    const int64_t warp = ((int64_t)blockIdx.x * kInitThreads + threadIdx.x) >> 5;
-    const int64_t chunk = warp * 32 * kInitItems;
-    if (chunk >= t.N) return;
-    int64_t p0 = chunk + lane;
-    int64_t r = read_of(t.toff, t.n_reads, min(p0, t.N - 1));
-    int64_t inst = 0;
-    if (t.n_inst > 1) inst = upper_index(t.inst_toff, 0, t.n_inst, min(p0, t.N - 1));
+    const int64_t nwarps = ((int64_t)gridDim.x * kInitThreads) >> 5;
+    for (int64_t warp = ((int64_t)blockIdx.x * kInitThreads + threadIdx.x) >> 5;
+         warp * 32 * kInitItems < t.N; warp += nwarps) {
+        const int64_t p0 = warp * 32 * kInitItems + lane;
+        int64_t r = read_of(t.toff, t.n_reads, min(p0, t.N - 1));
+        int64_t inst = 0;
+        if (t.n_inst > 1) inst = upper_index(t.inst_toff, 0, t.n_inst, min(p0, t.N - 1));
 #pragma unroll
-    for (int i = 0; i < kInitItems; ++i) {
-        int64_t p = p0 + (int64_t)i * 32;
-        if (p >= t.N) break;
-        while (__ldg(t.toff + r + 1) <= p) ++r;
-        if (t.n_inst > 1)
-            while (__ldg(t.inst_toff + inst + 1) <= p) ++inst;
-        int64_t left = __ldg(t.toff + r + 1) - 1 - p;   // bases before this fragment's '$'
-        uint64_t x = bases32(t.packed, (uint64_t)(p - r));
-        uint64_t kmer = x >> (64 - 2 * h0);
-        int lc = (int)min(left, (int64_t)h0);
-        if (lc < h0) kmer &= ~((1ull << (2 * (h0 - lc))) - 1ull);
-        unsigned long long key = ((unsigned long long)kmer << 5) | (unsigned long long)lc;
-        if (t.n_inst > 1) key |= (unsigned long long)inst << inst_shift;
-        if (pb) {
-            keys[p] = (key << pb) | (unsigned long long)p;
-        } else {
-            keys[p] = key;
-            vals[p] = (uint32_t)p;
+        for (int i = 0; i < kInitItems; ++i) {
+            const int64_t p = p0 + (int64_t)i * 32;
+            if (p >= t.N) break;
+            while (__ldg(t.toff + r + 1) <= p) ++r;
+            if (t.n_inst > 1)
+                while (__ldg(t.inst_toff + inst + 1) <= p) ++inst;
+            const int64_t left = __ldg(t.toff + r + 1) - 1 - p;   // bases before this fragment's '$'
+            const uint64_t x = bases32(t.packed, (uint64_t)(p - r));
+            uint64_t kmer = x >> (64 - 2 * h0);
+            const int lc = (int)min(left, (int64_t)h0);
+            if (lc < h0) kmer &= ~((1ull << (2 * (h0 - lc))) - 1ull);
+            unsigned long long key = ((unsigned long long)kmer << 5) | (unsigned long long)lc;
+            if (t.n_inst > 1) key |= (unsigned long long)inst << inst_shift;
+            unsigned long long w;
+            if (pb) {
+                w = (key << pb) | (unsigned long long)p;
+            } else {
+                w = key;
+                vals[p] = (uint32_t)p;
+            }
+            keys[p] = w;
+            for (int q = 0; q < passes; ++q)
+                atomicAdd(&sh[q * 256 + (uint32_t)((w >> (lo_bit + 8 * q)) & 255ull)], 1u);
         }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < passes * 256; i += kInitThreads) {
+        const uint32_t c = sh[i];
+        if (c) atomicAdd(&ghist[i], c);
     }
 }
 
@@ -1048,17 +1066,21 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
 
     // ---- round 0: initial keys, sort, rerank
     {
-        int warps = ceil_div(N, 32 * kInitItems);
+        const int passes0 = ceil_div(key_bits0, 8);
+        DNASA_CUDA(ctx, cudaMemsetAsync(rs.hist, 0, (size_t)passes0 * 256 * 4, s));
         {
             LaunchScope ls_(ctx, PK_INIT, s, (pb ? 8.25 : 12.25) * N);
-            k_init_keys<<<ceil_div(warps, kInitThreads / 32), kInitThreads, 0, s>>>(t, h0, inst_shift, pb,
-                                                                                  keys[0], vals[0]);
+            const int warps = ceil_div(N, 32 * kInitItems);
+            const int grid = (int)std::min<int64_t>(ceil_div(warps, kInitThreads / 32),
+                                                    (int64_t)ctx->num_sms * 8);
+            k_init_keys<<<std::max(grid, 1), kInitThreads, 0, s>>>(t, h0, inst_shift, pb, passes0, pb,
+                                                                   rs.hist, keys[0], vals[0]);
         }
         DNASA_CUDA(ctx, cudaGetLastError());
         int which;
         uint32_t *novals[2] = {nullptr, nullptr};
         DNASA_TRY(radix_sort_pairs<unsigned long long>(ctx, rs, keys, pb ? novals : vals, N, nullptr,
-                                                       key_bits0, false, tile_items, &which, s, lbw, pb));
+                                                       key_bits0, true, tile_items, &which, s, lbw, pb));
         DNASA_TRY(reset_counters());
         ro.nslots = L[0][0]; ro.npos = L[0][1]; ro.nhead = L[0][2];
         ro.stage = reinterpret_cast<uint2 *>(keys[which ^ 1]);   // the free key buffer
