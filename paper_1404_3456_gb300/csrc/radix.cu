@@ -54,9 +54,8 @@ __device__ __forceinline__ uint32_t match_digit(uint32_t d, uint32_t vmask) {
     uint32_t peers = vmask;
 #pragma unroll
     for (int b = 0; b < kRadixBits; ++b) {
-        uint32_t bit = (d >> b) & 1u;
-        uint32_t bal = __ballot_sync(0xffffffffu, bit);
-        peers &= bit ? bal : ~bal;
+        const uint32_t m = (uint32_t)((int32_t)(d << (31 - b)) >> 31);   // all ones iff bit b set
+        peers &= ~(__ballot_sync(0xffffffffu, m) ^ m);   // lanes whose bit b equals ours
     }
     return peers;
 }
