@@ -126,15 +126,18 @@ template <bool ROUND0>
 struct RerankSmem {
     union {
         unsigned long long k[kRrTile + 2];   // keys with one halo key on each side
-        struct {                             // reused once the head flags are known
-            uint32_t head[kRrTile];          // new rank (SA slot of the group head)
-            int32_t kp[kRrTile];             // output index of a kept item, -1 if dropped
+        struct {                             // reused once the head flags are known;
+            // item li at li + li / 32 (padded: the blocked writes, eight
+            // consecutive items per thread, then hit 32 distinct banks)
+            uint32_t head[kRrTile + kRrTile / 32];   // new rank (SA slot of the group head)
+            int32_t kp[kRrTile + kRrTile / 32];      // output index of a kept item, -1 if dropped
         } o;
     } u;
     uint32_t v[kRrTile];                 // positions
     uint32_t sl[ROUND0 ? 1 : kRrTile];   // slots (rounds >= 1)
     uint32_t oh[ROUND0 ? 1 : kRrTile];   // old head rank (rounds >= 1)
-    uint8_t f[kRrTile];                  // bit0 head, bit1 next is head
+    uint32_t hb[kRrTile / 32];           // bit l of word w: item 32w + l starts a group
+    uint32_t nb[kRrTile / 32];           // ... the item after it starts one (or the data end)
     int64_t tmp[kRrThreads / 32 + 1];
     int64_t incmax[kRrThreads];
     int64_t prefix[2];
@@ -186,25 +189,37 @@ __global__ void __launch_bounds__(kRrThreads) k_rerank(
         if (ROUND0 && (int)(k & 31ull) < h0) return true;   // own '$' inside: final
         return k != S.u.k[j - base];
     };
-    for (int li = tid; li < tile_n; li += kRrThreads) {
-        int64_t j = base + li;
-        bool h = is_head(j);
-        bool nh = (j == n - 1) || is_head(j + 1);
-        S.f[li] = (uint8_t)(h | (nh << 1));
+    {   // one ballot per 32 consecutive items; the next item's flag is the next lane's
+        const int lane = tid & 31;
+        for (int b0 = tid - lane; b0 < tile_n; b0 += kRrThreads) {   // warp-uniform
+            const int li = b0 + lane;
+            const int64_t j = base + li;
+            const bool in = li < tile_n;
+            const bool h = in && is_head(j);
+            const uint32_t hm = __ballot_sync(0xffffffffu, h);
+            const bool nh = in && (j == n - 1 || (lane < 31 ? ((hm >> (lane + 1)) & 1u) != 0u
+                                                            : is_head(j + 1)));
+            const uint32_t nm = __ballot_sync(0xffffffffu, nh);
+            if (lane == 0) {
+                S.hb[b0 >> 5] = hm;
+                S.nb[b0 >> 5] = nm;
+            }
+        }
     }
     __syncthreads();
     // ---- blocked scan: max head index and kept count
     int64_t my_max = -1, my_keep = 0;
     uint32_t headbits = 0, keepbits = 0, lastbits = 0;
-#pragma unroll
-    for (int i = 0; i < kRrItems; ++i) {
-        int li = tid * kRrItems + i;
-        if (li >= tile_n) break;
-        uint8_t f = S.f[li];
-        bool h = f & 1, nh = f & 2;
-        if (h) { my_max = base + li; headbits |= 1u << i; }
-        if (!(h && nh)) { ++my_keep; keepbits |= 1u << i; }
-        if (nh) lastbits |= 1u << i;
+    {
+        static_assert(kRrItems == 8, "a thread's items are one byte of a flag word");
+        const int sh = (tid * kRrItems) & 31;
+        const uint32_t vm = tid * kRrItems >= tile_n ? 0u
+                            : (1u << min(kRrItems, tile_n - tid * kRrItems)) - 1u;
+        headbits = (S.hb[(tid * kRrItems) >> 5] >> sh) & vm;
+        lastbits = (S.nb[(tid * kRrItems) >> 5] >> sh) & vm;
+        keepbits = ~(headbits & lastbits) & vm;
+        my_keep = __popc(keepbits);
+        if (headbits) my_max = base + tid * kRrItems + 31 - __clz(headbits);
     }
     int64_t tile_max, tile_keep;
     int64_t inc_max = block_inclusive_max<kRrThreads>(my_max, S.tmp, &tile_max, (int64_t)-1);
@@ -316,9 +331,9 @@ __global__ void __launch_bounds__(kRrThreads) k_rerank(
             int64_t j = base + li;
             if (headbits >> i & 1u) cur = j;
             uint32_t slot = ROUND0 ? (uint32_t)j : S.sl[li];
-            S.u.o.head[li] = ROUND0 ? (uint32_t)cur : slot - (uint32_t)(j - cur);
+            S.u.o.head[li + (li >> 5)] = ROUND0 ? (uint32_t)cur : slot - (uint32_t)(j - cur);
             if (keepbits >> i & 1u) {
-                S.u.o.kp[li] = (int32_t)kp;
+                S.u.o.kp[li + (li >> 5)] = (int32_t)kp;
                 if (lastbits >> i & 1u) {
                     uint32_t size = (uint32_t)(j - cur + 1);
                     o.groups[gbase++] = make_uint2((uint32_t)(kp - size + 1), size);
@@ -326,7 +341,7 @@ __global__ void __launch_bounds__(kRrThreads) k_rerank(
                 }
                 ++kp;
             } else {
-                S.u.o.kp[li] = -1;
+                S.u.o.kp[li + (li >> 5)] = -1;
             }
         }
 #pragma unroll
@@ -340,7 +355,7 @@ __global__ void __launch_bounds__(kRrThreads) k_rerank(
     const int nb = (int)((o.N + (1ll << o.bshift) - 1) >> o.bshift);
     for (int b = tid; b < nb; b += kRrThreads) S.bcnt[b] = 0;
     __syncthreads();
-    auto restage = [&](int li) -> bool { return ROUND0 || S.u.o.head[li] != S.oh[li]; };
+    auto restage = [&](int li) -> bool { return ROUND0 || S.u.o.head[li + (li >> 5)] != S.oh[li]; };
     uint32_t bidx[kRrItems];
 #pragma unroll
     for (int i = 0; i < kRrItems; ++i) {
@@ -360,8 +375,8 @@ __global__ void __launch_bounds__(kRrThreads) k_rerank(
         if (li >= tile_n) break;
         uint32_t slot = ROUND0 ? (uint32_t)(base + li) : S.sl[li];
         uint32_t pos = S.v[li];
-        uint32_t hs = S.u.o.head[li];
-        int32_t kp = S.u.o.kp[li];
+        uint32_t hs = S.u.o.head[li + (li >> 5)];
+        int32_t kp = S.u.o.kp[li + (li >> 5)];
         uint32_t b = pos >> o.bshift;
         uint64_t st = ((uint64_t)b << o.bshift) + S.bcnt[b] + bidx[i];
         if ((int64_t)slot >= o.N || (int64_t)pos >= o.N || kp >= n || (int64_t)st >= o.N) {
@@ -783,9 +798,8 @@ __global__ void __launch_bounds__(kSegThreads) k_seg_radix(const uint2 *__restri
                     uint32_t peers = vmask;
 #pragma unroll
                     for (int bb = 0; bb < 8; ++bb) {
-                        const uint32_t bit = (d >> bb) & 1u;
-                        const uint32_t bal = __ballot_sync(0xffffffffu, bit);
-                        peers &= bit ? bal : ~bal;
+                        const uint32_t m = (uint32_t)((int32_t)(d << (31 - bb)) >> 31);
+                        peers &= ~(__ballot_sync(0xffffffffu, m) ^ m);
                     }
                     const int leader = peers ? __ffs(peers) - 1 : 0;
                     uint32_t old = 0;
