@@ -80,6 +80,7 @@ __global__ void k_lcp_r(TextDesc t, const uint32_t *__restrict__ R, int32_t *__r
 struct QueryArgs {
     const uint32_t *isa, *Rslot, *R;
     const int32_t *lcpr;
+    const uint2 *rrange;              // per fragment: its instance's range in R (batches)
     int32_t lmin;
     int kb, lb;                       // bits of k and of L in a candidate key
     unsigned long long *cand;
@@ -87,48 +88,68 @@ struct QueryArgs {
     unsigned long long *count;
 };
 
-// Walks the fragment starts that have X = r_j[q - toff[j] ..] as a prefix and
-// calls emit(k) for each overlap (j, k, |X|).  Returns false when q is no query.
-template <typename F>
-__device__ __forceinline__ void query_walk(const TextDesc &t, const QueryArgs &a, int64_t q, F emit) {
-    int64_t j = frag_of(t, q);
-    int64_t start = __ldg(t.toff + j);
-    int64_t o = q - start;
-    int64_t L = __ldg(t.toff + j + 1) - 1 - q;   // bases of X = r_j[o..]
-    if (o < 1 || L < a.lmin) return;
-    uint32_t s = a.isa[q];
-    int64_t ri0 = 0, ri1 = t.n_reads;
-    if (t.n_inst > 1) {
-        int64_t inst = inst_of_read(t, j);
-        ri0 = __ldg(t.inst_roff + inst);
-        ri1 = __ldg(t.inst_roff + inst + 1);
+// X = r_j[q - toff[j] ..]: the first fragment start at or after X's own SA slot
+// within X's instance (binary search of the slot among R's slots), checked by
+// one packed-word comparison.  Returns false when q is no query or the first
+// candidate does not start with X.
+struct QueryHit {
+    int j, L, lo, ri1;
+};
+__device__ __forceinline__ bool query_locate(const TextDesc &t, const QueryArgs &a, int64_t q,
+                                             QueryHit &h) {
+    const int64_t j = frag_of(t, q);
+    const int64_t start = __ldg(t.toff + j);
+    const int64_t o = q - start;
+    const int64_t L = __ldg(t.toff + j + 1) - 1 - q;   // bases of X = r_j[o..]
+    if (o < 1 || L < a.lmin) return false;
+    const uint32_t s = a.isa[q];
+    int lo = 0, hi = (int)t.n_reads;
+    if (a.rrange) {
+        const uint2 rg = __ldg(a.rrange + j);
+        lo = (int)rg.x;
+        hi = (int)rg.y;
     }
-    int64_t lo = ri0, hi = ri1;                  // first fragment start after X's slot
-    while (lo < hi) {
-        int64_t m = (lo + hi) >> 1;
+    const int ri1 = hi;
+    while (lo < hi) {   // first fragment start after X's slot
+        const int m = (lo + hi) >> 1;
         if (__ldg(a.Rslot + m) < s) lo = m + 1; else hi = m;
     }
-    if (lo >= ri1) return;
-    int64_t k = __ldg(a.R + lo);
-    if (frag_len(t.toff, k) < L) return;
-    if (common_bases(t.packed, (uint64_t)(q - j), (uint64_t)(__ldg(t.toff + k) - k), L) < L) return;
-    for (int64_t kk = lo; kk < ri1; ++kk) {
-        if (kk > lo && __ldg(a.lcpr + kk) < L) break;
-        k = __ldg(a.R + kk);
-        if (k != j && L < frag_len(t.toff, k)) emit(j, k, L);
+    if (lo >= ri1) return false;
+    const int64_t k = __ldg(a.R + lo);
+    if (frag_len(t.toff, k) < L) return false;
+    if (common_bases(t.packed, (uint64_t)(q - j), (uint64_t)(__ldg(t.toff + k) - k), L) < L)
+        return false;
+    h.j = (int)j;
+    h.L = (int)L;
+    h.lo = lo;
+    h.ri1 = ri1;
+    return true;
+}
+
+// The fragment starts that have X as a prefix: R[lo] and its successors while
+// LCP_R stays >= |X|; emit(k) for each proper overlap (j, k, |X|).
+template <typename F>
+__device__ __forceinline__ void query_walk(const TextDesc &t, const QueryArgs &a, const QueryHit &h,
+                                           F emit) {
+    for (int kk = h.lo; kk < h.ri1; ++kk) {
+        if (kk > h.lo && __ldg(a.lcpr + kk) < h.L) break;
+        const int64_t k = __ldg(a.R + kk);
+        if (k != h.j && h.L < frag_len(t.toff, k)) emit(k);
     }
 }
 
 // One thread per text position.  Each warp counts its overlaps, claims room
-// with one atomic, then walks again to write them.
+// with one atomic, then walks again from the located start to write them.
 __global__ void __launch_bounds__(256) k_query(TextDesc t, QueryArgs a) {
     const unsigned long long lmask = (1ull << a.lb) - 1ull;
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane; b < t.N; b += stride) {
-        int64_t q = b + lane;
+        const int64_t q = b + lane;
         uint32_t c = 0;
-        if (q < t.N) query_walk(t, a, q, [&](int64_t, int64_t, int64_t) { ++c; });
+        QueryHit h;
+        const bool hit = q < t.N && query_locate(t, a, q, h);
+        if (hit) query_walk(t, a, h, [&](int64_t) { ++c; });
         uint32_t inc = c;
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
@@ -139,14 +160,23 @@ __global__ void __launch_bounds__(256) k_query(TextDesc t, QueryArgs a) {
         if (lane == 31 && inc) base = atomicAdd(a.count, (unsigned long long)inc);
         base = __shfl_sync(0xffffffffu, base, 31) + (inc - c);
         if (c) {
-            query_walk(t, a, q, [&](int64_t j, int64_t k, int64_t L) {
-                unsigned long long key = ((unsigned long long)j << (a.kb + a.lb)) |
+            query_walk(t, a, h, [&](int64_t k) {
+                unsigned long long key = ((unsigned long long)h.j << (a.kb + a.lb)) |
                                          ((unsigned long long)k << a.lb) |
-                                         (lmask - (unsigned long long)L);
+                                         (lmask - (unsigned long long)h.L);
                 if (base < a.cap) a.cand[base] = key;
                 ++base;
             });
         }
+    }
+}
+
+// Per fragment: the range of R that holds its instance's fragment starts.
+__global__ void k_read_range(TextDesc t, uint2 *__restrict__ rrange) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < t.n_reads;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t inst = inst_of_read(t, r);
+        rrange[r] = make_uint2((uint32_t)__ldg(t.inst_roff + inst), (uint32_t)__ldg(t.inst_roff + inst + 1));
     }
 }
 
@@ -221,6 +251,7 @@ int overlap_impl(dnasa_ctx *ctx, const TextDesc &t, const uint32_t *sa32, const 
     add((size_t)N * 4);                              // isa
     for (int i = 0; i < 4; ++i) add((size_t)nr * 4); // R keys/vals x2
     add((size_t)nr * 4);                             // lcp_r
+    if (t.n_inst > 1) add((size_t)nr * 8);           // per-fragment instance range in R
     add(radix_scratch_bytes(nr, 64, tile));
     int64_t cand_cap = std::max<int64_t>(4 * nr, 1 << 16);
     auto cand_bytes = [&](int64_t cc) {
@@ -238,6 +269,7 @@ int overlap_impl(dnasa_ctx *ctx, const TextDesc &t, const uint32_t *sa32, const 
         uint32_t *rk[2] = {a.take<uint32_t>((size_t)nr), a.take<uint32_t>((size_t)nr)};
         uint32_t *rv[2] = {a.take<uint32_t>((size_t)nr), a.take<uint32_t>((size_t)nr)};
         int32_t *lcpr = a.take<int32_t>((size_t)nr);
+        uint2 *rrange = t.n_inst > 1 ? a.take<uint2>((size_t)nr) : nullptr;
         RadixScratch rs = radix_scratch_take(a, nr, 64, tile);
         unsigned long long *ck[2] = {a.take<unsigned long long>((size_t)cand_cap),
                                      a.take<unsigned long long>((size_t)cand_cap)};
@@ -271,8 +303,13 @@ int overlap_impl(dnasa_ctx *ctx, const TextDesc &t, const uint32_t *sa32, const 
         if (2 * kb + lb > 64)
             return fail(ctx, DNASA_INVALID_ARG, "overlap_search: fragments too many or too long "
                                                 "for a 64-bit edge key");
+        if (rrange) {
+            LaunchScope ls_(ctx, PK_OVERLAP, s, 24.0 * nr);
+            k_read_range<<<grid_for(ctx, nr), 256, 0, s>>>(t, rrange);
+        }
         QueryArgs qa;
-        qa.isa = isa; qa.Rslot = Rslot; qa.R = R; qa.lcpr = lcpr; qa.lmin = min_overlap;
+        qa.isa = isa; qa.Rslot = Rslot; qa.R = R; qa.lcpr = lcpr; qa.rrange = rrange;
+        qa.lmin = min_overlap;
         qa.kb = kb; qa.lb = lb; qa.cand = ck[0]; qa.cap = (unsigned long long)cand_cap;
         qa.count = cnt + CNT_CAND;
         {
