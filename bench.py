@@ -351,6 +351,7 @@ def run_batched(args):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
+    trace = ctx.trace()
     l0 = ctx.launch_count()
     clocks = ClockSampler(local_rank)
     rank_barrier(world)
@@ -442,6 +443,7 @@ def run_batched(args):
                    "one_job_per_launch": {"instances": M, "s": solo_s, "assemblies_per_s": M / solo_s},
                    "batched_same_instances": {"instances": M, "s": sub_s, "assemblies_per_s": M / sub_s},
                    "oracle_all_cores": cpu_all,
+                   "sa_rounds": trace["rounds"], "active_per_round": trace["active"],
                    "autotuned": tuned},
         "roofline": roof, "cpu_baseline": cpu,
         "e2e": {"value": len(texts) / (e2e_ms / 1000.0), "unit": "assemblies/s",
