@@ -548,7 +548,7 @@ __global__ void __launch_bounds__(kFinThreads) k_finish(const uint2 *__restrict_
 }
 
 // ------------------------------------------------------------------ in-group sorting
-// From round 1 on, a round only has to order the members of each group by
+// From the first doubling round on, a round only has to order the members of each group by
 // rank[i+h] (all members of a group share the high key part, the head rank),
 // and members with equal keys stay together in one group that a later round
 // sorts again, so no stable order is needed.  Groups of at most 8 members are

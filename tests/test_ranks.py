@@ -65,7 +65,7 @@ def test_over_ranks_single_rank_is_identity():
 
 
 def test_reference_arm_under_torchrun_world2():
-    """The driver's launch of the reference arm with two ranks: rank 0 alone
+    """The reference arm launched by torch.distributed.run with two ranks: rank 0 alone
     runs the oracle and prints one JSON line; the other rank exits 0."""
     pytest.importorskip("torch")
     port = _free_port()
