@@ -438,11 +438,25 @@ __global__ void __launch_bounds__(256) k_rank_apply(const uint2 *__restrict__ st
         }
         b = lo;
     }
-    for (uint32_t f = f0 + threadIdx.x; f < f1; f += 256) {
-        while (f >= s_off[b + 1]) ++b;   // non-decreasing f per thread
-        const uint64_t si = ((uint64_t)b << bshift) + (f - s_off[b]);
-        const uint2 pr = stage[si];
-        if ((int64_t)pr.x < N && (pr.x >> bshift) == (uint32_t)b) rank[pr.x] = pr.y;
+    // all of a thread's staged pairs are loaded before any rank write, so that
+    // the loads are in flight together
+    constexpr int kPer = kApplyItems / 256;
+    uint2 pr[kPer];
+    int pb_[kPer];
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+        const uint32_t f = f0 + threadIdx.x + q * 256;
+        pb_[q] = -1;
+        if (f < f1) {
+            while (f >= s_off[b + 1]) ++b;   // non-decreasing f per thread
+            pb_[q] = b;
+            pr[q] = stage[((uint64_t)b << bshift) + (f - s_off[b])];
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < kPer; ++q) {
+        if (pb_[q] < 0) continue;
+        if ((int64_t)pr[q].x < N && (pr[q].x >> bshift) == (uint32_t)pb_[q]) rank[pr[q].x] = pr[q].y;
         else atomicOr(err, DERR_BOUNDS);
     }
 }
