@@ -294,7 +294,7 @@ int assemble_batched(dnasa_ctx *ctx, const uint8_t *texts, const int64_t *inst_o
 /* Autotuner of the build options: times sa_build (batched when n_inst > 1) on
  * this text for every tile size (2048, 3840, 5120), doubling-to-direct switch
  * (never, N/64, N/8, as soon as every group fits the finisher) and on-chip group
- * limit (32, 256, 2048), and
+ * limit (256, 2048, 12288), and
  * writes the fastest to *best (host) and its time to *best_ms (host, may be
  * NULL).  The radix digit is 8 bits: the only width the kernels implement.
  * With cache_path (may be NULL), a line "key<TAB>tile<TAB>switch<TAB>lookback
