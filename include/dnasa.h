@@ -342,7 +342,11 @@ typedef struct dnasa_server dnasa_server;
  * slots overlap on the GPU.  Each result equals that job assembled alone. */
 int dnasa_server_create(int device, size_t hbm_budget, int32_t slots, int32_t max_batch,
                         dnasa_server **out);
-/* Queues a job (thread-safe; returns at once). */
+/* Queues a job (thread-safe; returns at once after checking the text on the
+ * host: DNASA_BAD_ALPHABET for a byte outside A/C/G/T/'$', an empty fragment or
+ * a missing final '$', so that a malformed job never enters a batch).  A batch
+ * that fails as a whole is run again job by job, so that each job's status is
+ * its own. */
 int dnasa_server_submit(dnasa_server *srv, const dnasa_job *job, uint64_t id);
 /* Moves up to max_results finished jobs into out (host array), waiting up to
  * wait_ms for the first one; *n_out = how many were written. */

@@ -162,6 +162,18 @@ void run_batch(dnasa_server *srv, Slot &sl, std::vector<Pending> &batch, std::ve
             sl.h_ioff[1] = nc;
         }
     }
+    if (rc != DNASA_OK && n > 1) {
+        // the batch failed as a whole (e.g. out of memory): every job again on its
+        // own, so that one job's failure is reported for that job alone
+        std::vector<Done> all, one;
+        for (int i = 0; i < n; ++i) {
+            std::vector<Pending> single(1, batch[i]);
+            run_batch(srv, sl, single, one);
+            all.push_back(std::move(one[0]));
+        }
+        out = std::move(all);
+        return;
+    }
     const double t_done = srv->now_ms();
     out.clear();
     for (int i = 0; i < n; ++i) {
@@ -276,7 +288,16 @@ int dnasa_server_create(int device, size_t hbm_budget, int32_t slots, int32_t ma
 
 int dnasa_server_submit(dnasa_server *srv, const dnasa_job *job, uint64_t id) {
     if (!srv || !job || !job->text || job->N <= 0 || job->min_overlap < 1) return DNASA_INVALID_ARG;
-    if (job->text[job->N - 1] != '$') return DNASA_BAD_ALPHABET;
+    // a malformed text is refused here, so that it can never fail a batch it shares
+    if (job->text[job->N - 1] != '$' || job->text[0] == '$') return DNASA_BAD_ALPHABET;
+    for (int64_t i = 0; i < job->N; ++i) {
+        const uint8_t c = job->text[i];
+        if (c == '$') {
+            if (i > 0 && job->text[i - 1] == '$') return DNASA_BAD_ALPHABET;   // empty fragment
+        } else if (c != 'A' && c != 'C' && c != 'G' && c != 'T') {
+            return DNASA_BAD_ALPHABET;
+        }
+    }
     Pending p;
     p.id = id;
     p.text.assign(job->text, job->text + job->N);

@@ -293,6 +293,28 @@ def test_assemble_worked_example_dna(ctx):
 # ---------------------------------------------------------------- radix sort (Algorithm 1)
 
 
+@pytest.mark.parametrize("kind", ["all_equal", "sorted", "reverse", "two_values"])
+def test_sort_pairs_special_orders(ctx, kind):
+    """Stable order on key distributions that stress the digit ranking: one key
+    for all, already sorted, reversed, two alternating keys."""
+    n = 3840 * 7 + 123
+    if kind == "all_equal":
+        k = np.full(n, 0x1234_5678_9ABC, dtype=np.uint64)
+    elif kind == "sorted":
+        k = np.arange(n, dtype=np.uint64) * np.uint64(0x10001)
+    elif kind == "reverse":
+        k = (np.arange(n, dtype=np.uint64)[::-1] * np.uint64(0x10001)).copy()
+    else:
+        k = np.where(np.arange(n) % 2 == 0, 7, 3).astype(np.uint64)
+    v = np.arange(n, dtype=np.uint32)
+    kt = torch.from_numpy(k.view(np.int64).copy()).cuda()
+    vt = torch.from_numpy(v.view(np.int32).copy()).cuda()
+    B().dnasa_sort_pairs(ctx, kt, vt, 48, 3840, 8)
+    order = np.argsort(k, kind="stable")
+    assert np.array_equal(kt.cpu().numpy().view(np.uint64), k[order])
+    assert np.array_equal(vt.cpu().numpy().view(np.uint32), v[order])
+
+
 @pytest.mark.parametrize("n,bits,tile,lb,with_vals", [
     (1, 64, 0, 0, True), (1000, 8, 2048, 1, True), (100_003, 63, 3840, 8, True),
     (300_000, 52, 5120, 8, True), (70_000, 32, 0, 1, False), (3840 * 5 + 17, 17, 3840, 1, True)])

@@ -81,3 +81,31 @@ def test_server_admission_by_budget():
     spans = sorted((r["t_start_ms"], r["t_done_ms"]) for r in got.values())
     for (a0, a1), (b0, b1) in zip(spans, spans[1:]):
         assert b0 >= a1 - 1e-6
+
+
+def test_server_refuses_malformed_jobs_and_keeps_serving():
+    """A malformed text is refused at submit (bad byte, empty fragment, missing
+    final '$', leading '$'); the jobs around it are served as if it never came."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    js = jobs(3, seed=6)
+    srv = B().Server(0, slots=2, max_batch=8)
+    bad = [b"ACGTN$", b"ACG$$TTA$", b"ACGT", b"$ACGT$"]
+    srv.submit(js[0]["text"], js[0]["min_overlap"], 0)
+    for t in bad:
+        with pytest.raises(B().DnasaError) as e:
+            srv.submit(np.frombuffer(t, dtype=np.uint8), 31, 99)
+        assert e.value.status == B().BAD_ALPHABET
+    srv.submit(js[1]["text"], js[1]["min_overlap"], 1)
+    srv.submit(js[2]["text"], js[2]["min_overlap"], 2)
+    got = {}
+    deadline = time.time() + 60
+    while len(got) < 3 and time.time() < deadline:
+        for r in srv.poll(64, wait_ms=200):
+            got[r["id"]] = r
+    srv.close()
+    assert sorted(got) == [0, 1, 2]
+    for i in range(3):
+        assert got[i]["status"] == 0
+        buf, off = oracle.assemble(js[i]["text"], js[i]["min_overlap"])
+        assert got[i]["contigs"] == oracle.contigs_as_list(buf, off)
