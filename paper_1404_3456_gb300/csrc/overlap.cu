@@ -3,7 +3,7 @@
 // Sec. III reconstructs the sequence from "fir" relations: fragment D_k is a
 // prefix of another fragment, or the remainder of a cut fragment is the
 // prefix of the next one -- i.e. a suffix of one fragment equals a prefix of
-// another.  Sec. IV answers these "is X a prefix of a fragment" questions by
+// another.  Sec. IV answers these questions (is X the beginning of some fragment?) by
 // searching the suffix array.  Here every suffix X = r_j[o..] (o >= 1,
 // |X| >= min_overlap) is a query:
 //   * R = the fragment-start suffixes in SA order (a subsequence of the SA),

@@ -1,12 +1,13 @@
 // radix.cu -- stable LSD radix sort of (key, value) pairs, onesweep style.
 //
-// Sec. IV of the paper sorts suffix keys with an LSD radix sort whose passes
-// rank each element as "elements in lower buckets + elements already in the
-// same bucket" (after Satish et al.), built from split/scan/scatter kernels on
-// shared-memory chunks (Algorithm 1).  This is the same sort, re-planned for
-// sm_103a:
+// Sec. IV of the paper sorts suffix keys with an LSD radix sort in which each
+// pass places an element after every element of a smaller bucket and after the
+// elements of its own bucket placed before it (after Satish et al.), built from
+// split/scan/scatter kernels on shared-memory chunks (Algorithm 1).  This is the
+// same sort, re-planned for sm_103a:
 //   * one histogram kernel reads the keys once and counts every digit of every
-//     pass (8-bit digits, shared-memory atomics);
+//     pass (8-bit digits, shared-memory atomics), unless the kernel that wrote
+//     the keys counted them already;
 //   * then one kernel per digit.  Each CTA takes the next tile id from an
 //     atomic counter, ranks its tile's digits in shared memory (per-warp
 //     ranking: the lanes holding the same digit are found with one ballot per
