@@ -36,6 +36,10 @@
  *   wait that gives up yields DNASA_DEVICE_TIMEOUT and leaves the context
  *   usable.
  * Index width.  idx_width is DNASA_I32 (int32 SA) or DNASA_I64 (int64 SA).
+ * Threads.  A context (its workspace, counters and error text) serves one
+ *   call at a time: calls on one context from several threads must be
+ *   serialized by the caller; separate contexts are independent (the server
+ *   gives each of its slots its own).  The server calls are thread-safe.
  */
 #ifndef DNASA_H
 #define DNASA_H
