@@ -298,9 +298,10 @@ int assemble_batched(dnasa_ctx *ctx, const uint8_t *texts, const int64_t *inst_o
 /* Autotuner of the build options: times sa_build (batched when n_inst > 1) on
  * this text for every tile size (2048, 3840, 5120), doubling-to-direct switch
  * (never, N/64, N/8, as soon as every group fits the finisher) and on-chip group
- * limit (256, 2048, 12288), and
- * writes the fastest to *best (host) and its time to *best_ms (host, may be
- * NULL).  The radix digit is 8 bits: the only width the kernels implement.
+ * limit (256, 2048, 12288), each once; then times the four fastest three more
+ * times each and writes the one with the best median to *best (host) and that
+ * median to *best_ms (host, may be NULL).  The radix digit is 8 bits: the only
+ * width the kernels implement.
  * With cache_path (may be NULL), a line "key<TAB>tile<TAB>switch<TAB>lookback
  * <TAB>seg_max<TAB>ms" keyed by GPU name, bits of N and bits of n_inst is looked up first
  * and appended after tuning.  inst_off as for sa_build_batched (host).
@@ -340,8 +341,11 @@ typedef struct dnasa_server dnasa_server;
 /* Starts a server on `device` with `slots` workers (own context and stream each,
  * 1..16) that admit queued jobs, in arrival order, as batches of at most
  * max_batch jobs of equal min_overlap, while their estimated device memory
- * (about 80 bytes per text symbol) fits in hbm_budget (0 = 90 % of the free
- * memory at creation) less what the batches already running hold.  A job larger
+ * (dnasa_server_job_bytes each) fits in the budget less what the batches already
+ * running reserved.  The budget is hbm_budget (0 = 90 % of the free memory at
+ * creation), lowered at each admission to 95 % of the device memory free at that
+ * moment plus what the running batches reserved and the admitting slot holds, so
+ * that memory taken by other users after creation is respected.  A job larger
  * than the whole budget runs alone once nothing else runs.  Batches of different
  * slots overlap on the GPU.  Each result equals that job assembled alone. */
 int dnasa_server_create(int device, size_t hbm_budget, int32_t slots, int32_t max_batch,
@@ -356,6 +360,11 @@ int dnasa_server_submit(dnasa_server *srv, const dnasa_job *job, uint64_t id);
  * wait_ms for the first one; *n_out = how many were written. */
 int dnasa_server_poll(dnasa_server *srv, dnasa_result *out, int32_t max_results, int32_t wait_ms,
                       int32_t *n_out);
+/* Device bytes the server reserves for one job of N text symbols holding n_reads
+ * fragments: the suffix-array workspace (~95 bytes per symbol, held with the
+ * context's growth margin), the buffers assemble keeps alongside it, the slot's
+ * text and contig buffers, and a fixed 32 MB.  -1 for sizes out of range. */
+int64_t dnasa_server_job_bytes(int64_t N, int64_t n_reads);
 /* Jobs queued or running. */
 int dnasa_server_pending(dnasa_server *srv);
 /* Finishes every queued job, then stops the workers and frees everything. */

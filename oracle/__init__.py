@@ -73,6 +73,12 @@ def _load():
             lib.oracle_lcp_direct.restype = ctypes.c_int
             lib.oracle_sa_check.argtypes = [P, I64, P]
             lib.oracle_sa_check.restype = I64
+            lib.oracle_inverse_sa.argtypes = [P, I64, P]
+            lib.oracle_inverse_sa.restype = I64
+            lib.oracle_sa_check_range.argtypes = [P, I64, P, P, I64, I64]
+            lib.oracle_sa_check_range.restype = I64
+            lib.oracle_lcp_kasai_range.argtypes = [P, I64, P, P, I64, I64, P]
+            lib.oracle_lcp_kasai_range.restype = ctypes.c_int
             lib.oracle_check_pairs.argtypes = [P, I64, P, P, P, I64]
             lib.oracle_check_pairs.restype = I64
             lib.oracle_split_sort_u64.argtypes = [P, P, I64, ctypes.c_int, ctypes.c_int]
@@ -145,6 +151,46 @@ def sa_check(text, sa) -> int:
     if sa.size != t.size:
         return 1
     return int(_load().oracle_sa_check(_ptr(t), t.size, _ptr(sa)))
+
+
+def _ranges(n0: int, n1: int, parts: int):
+    step = max(1, -(-(n1 - n0) // max(parts, 1)))
+    return [(a, min(a + step, n1)) for a in range(n0, n1, step)]
+
+
+def sa_check_and_lcp_threaded(text, sa, threads: int = 0):
+    """The Burkhardt-Kaerkkaeinen check of ``sa`` and Kasai's LCP, each split into
+    ranges run on host threads (ctypes releases the GIL during the C calls).
+    Returns (check code, lcp): code 0 means ``sa`` is the suffix array (same codes
+    as :func:`sa_check`; 2 + j names the smallest failing pair found in its range).
+    ``lcp`` is None when the check fails."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    t = _text(text)
+    N = t.size
+    sa = np.ascontiguousarray(sa, dtype=np.int64)
+    if sa.size != N:
+        return 1, None
+    lib = _load()
+    isa = np.empty(N, dtype=np.int64)
+    rc = int(lib.oracle_inverse_sa(_ptr(sa), N, _ptr(isa)))
+    if rc != 0:
+        return rc, None
+    threads = threads or (os.cpu_count() or 1)
+    with ThreadPoolExecutor(threads) as ex:
+        codes = list(ex.map(lambda r: int(lib.oracle_sa_check_range(_ptr(t), N, _ptr(sa), _ptr(isa),
+                                                                    r[0], r[1])),
+                            _ranges(1, N, 4 * threads)))
+        bad = [c for c in codes if c != 0]
+        if bad:
+            return min(bad), None
+        lcp = np.empty(N, dtype=np.int32)
+        rcs = list(ex.map(lambda r: int(lib.oracle_lcp_kasai_range(_ptr(t), N, _ptr(sa), _ptr(isa),
+                                                                  r[0], r[1], _ptr(lcp))),
+                          _ranges(0, N, 4 * threads)))
+    if any(rcs):
+        raise RuntimeError("oracle_lcp_kasai_range failed")
+    return 0, lcp
 
 
 def check_pairs(text, sa, lcp, idx) -> int:

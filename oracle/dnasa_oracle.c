@@ -24,6 +24,9 @@
  *   oracle_lcp_kasai        LCP of adjacent SA entries, Kasai et al. 2001
  *   oracle_lcp_direct       the same, measured pair by pair (a pin for Kasai)
  *   oracle_sa_check         Burkhardt & Kaerkkaeinen (CPM 2003) linear SA checker
+ *   oracle_inverse_sa, oracle_sa_check_range, oracle_lcp_kasai_range
+ *                           the checker and Kasai split into independent ranges
+ *                           (for billion-entry arrays, one range per thread)
  *   oracle_check_pairs      sampled SA neighbours (order and LCP) checked one by one
  *   oracle_split_sort_u64   Sec. IV / Algorithm 1: LSD radix sort made of 1-bit
  *                           stable "split" passes (flag, exclusive scan, scatter)
@@ -167,6 +170,65 @@ int64_t oracle_sa_check(const uint8_t *T, int64_t N, const int64_t *sa)
     return bad;
 }
 
+/* The same checker and Kasai's LCP split into independent pieces, for arrays
+ * of a billion entries and more (the large single-genome case): the caller
+ * builds the inverse once, then checks pair ranges and computes LCP position
+ * ranges in as many threads as it likes.  Each piece is the algorithm above
+ * restricted to its range; nothing is shared but read-only inputs.
+ *
+ * oracle_inverse_sa: isa[sa[j]] = j.  Returns 0, or 1 if sa is not a
+ * permutation of 0..N-1 (the first test of the checker). */
+int64_t oracle_inverse_sa(const int64_t *sa, int64_t N, int64_t *isa)
+{
+    if (!sa || !isa || N <= 0) return -1;
+    for (int64_t i = 0; i < N; ++i) isa[i] = -1;
+    for (int64_t j = 0; j < N; ++j) {
+        int64_t p = sa[j];
+        if (p < 0 || p >= N || isa[p] != -1) return 1;
+        isa[p] = j;
+    }
+    return 0;
+}
+
+/* The order tests of oracle_sa_check for the adjacent pairs (j-1, j), j in
+ * [j0, j1), given the inverse.  Returns 0 or 2 + the first j that fails. */
+int64_t oracle_sa_check_range(const uint8_t *T, int64_t N, const int64_t *sa, const int64_t *isa,
+                              int64_t j0, int64_t j1)
+{
+    if (!text_ok(T, N) || !sa || !isa || j0 < 1 || j1 > N || j0 > j1) return -1;
+    for (int64_t j = j0; j < j1; ++j) {
+        int64_t p = sa[j - 1], q = sa[j];
+        uint8_t a = T[p], b = T[q];
+        if (a == SEP && b == SEP) { if (!(p < q)) return 2 + j; }
+        else if (a == SEP) { /* '$' before a symbol: in order */ }
+        else if (b == SEP) return 2 + j;
+        else if (a < b) { /* in order */ }
+        else if (a > b) return 2 + j;
+        else if (!(isa[p + 1] < isa[q + 1])) return 2 + j;
+    }
+    return 0;
+}
+
+/* Kasai's walk over text positions [p0, p1) only: lcp[isa[i]] for those i.
+ * It starts with h = 0 at p0 instead of the bound carried from p0 - 1, which
+ * costs extra comparisons at the start of the range but never changes a value
+ * (the bound only skips symbols already known to match). */
+int oracle_lcp_kasai_range(const uint8_t *T, int64_t N, const int64_t *sa, const int64_t *isa,
+                           int64_t p0, int64_t p1, int32_t *lcp)
+{
+    if (!text_ok(T, N) || !sa || !isa || !lcp || p0 < 0 || p1 > N || p0 > p1) return -1;
+    int64_t h = 0;
+    for (int64_t i = p0; i < p1; ++i) {
+        int64_t r = isa[i];
+        if (r == 0) { lcp[0] = 0; h = 0; continue; }
+        int64_t j = sa[r - 1];
+        while (T[i + h] == T[j + h] && T[i + h] != SEP) ++h;
+        lcp[r] = (int32_t)h;
+        if (h > 0) --h;
+    }
+    return 0;
+}
+
 /* Checks sampled neighbours of a (possibly huge) suffix array one by one: for
  * each j in idx[0..m), suffix sa[j-1] must be smaller than suffix sa[j] and, if
  * lcp is non-NULL, lcp[j] must be their common prefix.  Returns the number of
@@ -273,8 +335,8 @@ int64_t oracle_overlaps_brute(const uint8_t *T, const int64_t *toff, int64_t nr,
 }
 
 /* Order of fragments by their strings ('$' smallest), ties by index. */
-static const uint8_t *g_T;
-static const int64_t *g_toff;
+static _Thread_local const uint8_t *g_T;   /* per thread: callers may run in parallel */
+static _Thread_local const int64_t *g_toff;
 static int read_cmp(const void *pa, const void *pb)
 {
     int64_t a = *(const int64_t *)pa, b = *(const int64_t *)pb;

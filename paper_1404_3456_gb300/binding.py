@@ -95,6 +95,7 @@ _SIGS = {
     "dnasa_server_submit": (_INT, [_P, ctypes.POINTER(Job), ctypes.c_uint64]),
     "dnasa_server_poll": (_INT, [_P, ctypes.POINTER(Result), _I32, _I32, ctypes.POINTER(_I32)]),
     "dnasa_server_pending": (_INT, [_P]),
+    "dnasa_server_job_bytes": (_I64, [_I64, _I64]),
     "dnasa_server_destroy": (None, [_P]),
     "sa_build_batched": (_INT, [_P, _P, _P, _I64, _I64, _P, _I32, _P, ctypes.POINTER(Opts), _P]),
     "assemble_batched": (_INT, [_P, _P, _P, _I32, _I32, ctypes.POINTER(Opts), _P, _I64, _P, _I64,
@@ -204,9 +205,22 @@ def packed_words(N: int) -> int:
     return int(lib().dnasa_packed_words(N))
 
 
+def _check_sort_args(keys, vals):
+    """The C side reads 8 bytes per key and 4 per value over keys.numel() items."""
+    if keys.dtype != torch.int64 or not keys.is_contiguous() or keys.device.type != "cuda":
+        raise ValueError("keys must be a contiguous int64 CUDA tensor")
+    if vals is not None:
+        if vals.dtype not in (torch.int32, getattr(torch, "uint32", torch.int32)) \
+                or not vals.is_contiguous() or vals.device != keys.device:
+            raise ValueError("vals must be a contiguous int32 tensor on the keys' device")
+        if vals.numel() != keys.numel():
+            raise ValueError("vals must have as many items as keys")
+
+
 def dnasa_sort_pairs(ctx: Context, keys, vals=None, key_bits: int = 64, tile_items: int = 0,
                      lookback: int = 0, stream=None):
     """Stable radix sort in place: keys int64 (bit pattern of uint64), vals int32/uint32."""
+    _check_sort_args(keys, vals)
     ctx.check(lib().dnasa_sort_pairs(ctx.handle, _ptr(keys), _ptr(vals) if vals is not None else None,
                                      keys.numel(), key_bits, tile_items, lookback, _stream(stream)))
 
@@ -222,8 +236,10 @@ NOALLOC_MAX_ITEMS = 1 << 20   # DNASA_NOALLOC_MAX_ITEMS in dnasa.h
 def dnasa_sort_pairs_noalloc(keys, vals=None, key_bits: int = 64, stream=None):
     """dnasa_sort_pairs without a context or any allocation (n <= NOALLOC_MAX_ITEMS);
     raises DnasaError with the C status on failure."""
-    rc = lib().dnasa_sort_pairs_noalloc(_ptr(keys), _ptr(vals) if vals is not None else None,
-                                        keys.numel(), key_bits, _stream(stream))
+    _check_sort_args(keys, vals)
+    with torch.cuda.device(keys.device):   # the C side sorts on the current device
+        rc = lib().dnasa_sort_pairs_noalloc(_ptr(keys), _ptr(vals) if vals is not None else None,
+                                            keys.numel(), key_bits, _stream(stream))
     if rc != 0:
         raise DnasaError(rc, "dnasa_sort_pairs_noalloc failed")
 
@@ -361,6 +377,11 @@ def assemble_texts_batched(ctx: Context, texts_np, min_overlap: int, opts=None, 
 
 class Server:
     """Continuous-batching assembly server (dnasa_server_* in the C ABI)."""
+
+    @staticmethod
+    def job_bytes(N: int, n_reads: int) -> int:
+        """Device bytes the server reserves for one job (dnasa_server_job_bytes)."""
+        return int(lib().dnasa_server_job_bytes(N, n_reads))
 
     def __init__(self, device: int = 0, hbm_budget: int = 0, slots: int = 2, max_batch: int = 64):
         torch.cuda.init()

@@ -97,6 +97,13 @@ bool is_device_ptr(dnasa_ctx *ctx, const void *p);
 // Reads the device error flags (synchronizes s) and maps them to a status;
 // clears them.
 int check_device_status(dnasa_ctx *ctx, cudaStream_t s, const char *where);
+// Raises kernel `fn`'s dynamic shared-memory limit to `bytes` on the CURRENT
+// device.  The attribute belongs to a (kernel, device) pair, so it is set the
+// first time each pair is seen (a process may use several devices) and
+// remembered under a lock; later calls only look it up.
+cudaError_t smem_attr_fn(const void *fn, size_t bytes);
+template <typename F>
+inline cudaError_t smem_attr(F *fn, size_t bytes) { return smem_attr_fn((const void *)fn, bytes); }
 
 // Counts one kernel launch of class `kind` and, when profiling is on, brackets
 // it with CUDA events on its stream; `bytes` is the launch's algorithmic
@@ -168,6 +175,9 @@ struct TextDesc {
     const uint32_t *fid;       // device, N: fragment of each text position (nullptr: search toff)
 };
 
+// Device workspace sa_build_u32 takes for an N-symbol text (bytes, before the
+// context's growth margin).
+size_t sa_workspace_bytes(int64_t N, int tile_items);
 // Builds the SA into sa32 (uint32, N entries, text coordinates).  If isa_out is
 // non-null it also receives the inverse SA (the final rank array), N uint32.
 int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_opts *opts,

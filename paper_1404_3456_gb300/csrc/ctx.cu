@@ -3,6 +3,9 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
+#include <set>
+#include <utility>
 
 #include "block.cuh"
 #include "common.cuh"
@@ -19,6 +22,19 @@ int cuda_fail(dnasa_ctx *ctx, cudaError_t e, const char *where) {
     cudaGetLastError();  // clear a sticky-free error so the context stays usable
     if (e == cudaErrorMemoryAllocation) return fail(ctx, DNASA_OOM, msg);
     return fail(ctx, DNASA_CUDA_ERROR, msg);
+}
+
+cudaError_t smem_attr_fn(const void *fn, size_t bytes) {
+    static std::mutex mu;
+    static std::set<std::pair<const void *, int>> done;   // (kernel, device) pairs configured
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done.count({fn, dev})) return cudaSuccess;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) done.insert({fn, dev});
+    return e;
 }
 
 int ws_reserve(dnasa_ctx *ctx, size_t bytes, cudaStream_t s) {

@@ -309,9 +309,7 @@ int layout_impl(dnasa_ctx *ctx, const TextDesc &t, int64_t max_reads_per_inst,
                                                            ib + lb + 2 * kbl, false, tile, &which, s));
         }
     }
-    static const cudaError_t greedy_smem =
-        cudaFuncSetAttribute(k_greedy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGreedySmem);
-    DNASA_CUDA(ctx, greedy_smem);
+    DNASA_CUDA(ctx, smem_attr(k_greedy, kGreedySmem));   // once per (kernel, device)
     {
         LaunchScope ls_(ctx, PK_LAYOUT, s, 0);
         int g = (int)std::min<int64_t>(t.n_inst, (int64_t)ctx->num_sms * 8);

@@ -350,9 +350,7 @@ cudaError_t launch_pass(int tiles, cudaStream_t s, const K *kin, const uint32_t 
                         int shift, uint32_t epoch, uint32_t *err, uint32_t spin_limit = kSpinLimit) {
     size_t smem = onesweep_smem<K, ITEMS, HAS_VALS>();
     auto kern = k_onesweep<K, ITEMS, HAS_VALS, LBW>;
-    // once per instantiation (thread-safe static initialisation)
-    static const cudaError_t configured =
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const cudaError_t configured = smem_attr(kern, smem);   // once per (kernel, device)
     if (configured != cudaSuccess) return configured;
     kern<<<tiles, kThreads, smem, s>>>(kin, vin, kout, vout, bucket, status, tile_ctr, n_host,
                                        d_n, shift, epoch, err, spin_limit);
@@ -595,6 +593,16 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoAllocS
 // Device address of g_noalloc_scratch per device ordinal, found once per device.
 static NoAllocScratch *g_noalloc_addr[64];
 
+// True if p is device or managed memory that belongs to device `dev`.
+static bool noalloc_device_ptr(const void *p, int dev) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();   // an unknown pointer leaves no sticky error behind
+        return false;
+    }
+    return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) && at.device == dev;
+}
+
 __global__ void k_noalloc_clear(NoAllocScratch *S, int tiles) {
     const int64_t words = (int64_t)tiles * kRadix;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < words;
@@ -655,6 +663,10 @@ extern "C" int dnasa_sort_pairs_noalloc(uint64_t *keys, uint32_t *vals, int64_t 
     if (!keys) return DNASA_INVALID_ARG;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return DNASA_CUDA_ERROR;
+    // keys and vals must be device (or managed) memory of the current device:
+    // anything else would reach the kernels as a bad address
+    if (!noalloc_device_ptr(keys, dev) || (vals && !noalloc_device_ptr(vals, dev)))
+        return DNASA_INVALID_ARG;
     if (!g_noalloc_addr[dev]) {
         // First call on this device: look up the array's device address (with
         // this device current).  Make this first call before any stream capture.

@@ -967,6 +967,25 @@ int h0_for(int64_t N, int n_inst, int *inst_bits, int *pack_bits) {
     return hp >= hmin ? hp : h0;
 }
 
+size_t sa_workspace_bytes(int64_t N, int tile_items) {
+    const size_t n = (size_t)N;
+    const int rr_tiles = ceil_div(N, kRrTile);
+    size_t need = 0;
+    auto add = [&](size_t bytes) { need += (bytes + 255) & ~size_t(255); };
+    add(n * 8); add(n * 8);                 // keys x2
+    add(n * 4); add(n * 4);                 // vals x2
+    add(n * 4);                             // rank
+    for (int i = 0; i < 6; ++i) add(n * 4); // lists A, B
+    add((n / 2 + 1) * 8);                   // groups
+    add((size_t)rr_tiles * 8);              // rerank status
+    add((size_t)kMaxBuckets * 4);           // rank-write bucket fill counts
+    add(n); add(n * 4); add(n * 8); add(n * 4);   // large-group flags, indices, sort buffers
+    for (int i = 0; i < 5; ++i) add((n / 2 + 1) * 8);   // group lists by size class
+    add(compact_scratch_bytes(N));
+    add(radix_scratch_bytes(N, 64, tile_items));
+    return need;
+}
+
 int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_opts *opts_in,
                  cudaStream_t s, uint32_t *isa_out) {
     dnasa_opts opts{};
@@ -992,19 +1011,7 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
     // ---- workspace
     const size_t n = (size_t)N;
     const int rr_tiles = ceil_div(N, kRrTile);
-    size_t need = 0;
-    auto add = [&](size_t bytes) { need += (bytes + 255) & ~size_t(255); };
-    add(n * 8); add(n * 8);                 // keys x2
-    add(n * 4); add(n * 4);                 // vals x2
-    add(n * 4);                             // rank
-    for (int i = 0; i < 6; ++i) add(n * 4); // lists A, B
-    add((n / 2 + 1) * 8);                   // groups
-    add((size_t)rr_tiles * 8);              // rerank status
-    add((size_t)kMaxBuckets * 4);           // rank-write bucket fill counts
-    add(n); add(n * 4); add(n * 8); add(n * 4);   // large-group flags, indices, sort buffers
-    for (int i = 0; i < 5; ++i) add((n / 2 + 1) * 8);   // group lists by size class
-    add(compact_scratch_bytes(N));
-    add(radix_scratch_bytes(N, 64, tile_items));
+    const size_t need = sa_workspace_bytes(N, tile_items);
     DNASA_TRY(ws_reserve(ctx, need + 4096, s));
     Arena a = ws_arena(ctx);
     unsigned long long *keys[2] = {a.take<unsigned long long>(n), a.take<unsigned long long>(n)};
@@ -1026,24 +1033,12 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
     RadixScratch rs = radix_scratch_take(a, N, 64, tile_items);
     if (!rs.hist || !rr_status) return fail(ctx, DNASA_OOM, "sa_build workspace");
 
-    // once per process (thread-safe static initialisation)
-    static const cudaError_t smem_set = [] {
-        cudaError_t e = cudaFuncSetAttribute(k_rerank<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)sizeof(RerankSmem<true>));
-        if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(k_seg_radix<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)seg_radix_smem<4>());
-        if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(k_seg_radix<12>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)seg_radix_smem<12>());
-        if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(k_seg_radix<24>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)seg_radix_smem<24>());
-        if (e != cudaSuccess) return e;
-        return cudaFuncSetAttribute(k_rerank<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)sizeof(RerankSmem<false>));
-    }();
-    DNASA_CUDA(ctx, smem_set);
+    // dynamic shared-memory limits of this call's kernels, once per (kernel, device)
+    DNASA_CUDA(ctx, smem_attr(k_rerank<true>, sizeof(RerankSmem<true>)));
+    DNASA_CUDA(ctx, smem_attr(k_rerank<false>, sizeof(RerankSmem<false>)));
+    DNASA_CUDA(ctx, smem_attr(k_seg_radix<4>, seg_radix_smem<4>()));
+    DNASA_CUDA(ctx, smem_attr(k_seg_radix<12>, seg_radix_smem<12>()));
+    DNASA_CUDA(ctx, smem_attr(k_seg_radix<24>, seg_radix_smem<24>()));
     DevCtrl *c = ctx->ctrl;
     unsigned long long *cnt = c->count;
     dnasa_trace &tr = ctx->trace;

@@ -48,11 +48,31 @@ struct Done {
     double t_submit, t_start, t_done;
 };
 
-// Device bytes one job of N symbols may need while it is assembled (the suffix
-// array workspace dominates: ~56 B per symbol, plus the text-sized buffers).
-size_t job_bytes(int64_t N) { return (size_t)N * 80 + (32u << 20); }
+// Device bytes one job of N symbols and n_reads fragments may hold at its peak
+// while it is assembled: the context workspace of the suffix-array build (the
+// largest step; the context grows it with a 1/8 margin and never shrinks it),
+// plus the buffers assemble keeps alongside (packed text, fragment offsets,
+// SA, LCP, inverse SA, fragment ids, containment flags, the edge list), plus
+// the slot's own text, contig and offset buffers, plus a fixed allowance for
+// the context's small buffers.
+size_t job_bytes(int64_t N, int64_t n_reads) {
+    const size_t n = (size_t)N, r = (size_t)std::max<int64_t>(n_reads, 1);
+    const size_t ws = dnasa::sa_workspace_bytes(N, 0 /* default tile */) + 4096;
+    const size_t ws_held = ws + ws / 8 + (1u << 20);
+    const size_t assemble_bufs = (n / 32 + 3) * 8          // packed text
+                                 + (n / 2 + 2) * 8         // fragment offsets (capacity)
+                                 + 4 * n * 4               // SA, LCP, inverse SA, fragment ids
+                                 + r                       // containment flags
+                                 + std::max<size_t>(8 * r, 1024) * sizeof(dnasa_edge);
+    const size_t slot_bufs = 2 * n + (n / 2 + 2) * 8;      // text, contigs, contig offsets
+    return ws_held + assemble_bufs + slot_bufs + (32u << 20);
+}
 
 struct Slot {
+    size_t held() const {   // device bytes this slot keeps between batches
+        return (ctx ? ctx->ws_size + ctx->lb_words * 8 : 0) + text_cap + contig_cap +
+               off_cap * 8 + ioff_cap * 8;
+    }
     dnasa_ctx *ctx = nullptr;
     cudaStream_t stream = nullptr;
     // device and pinned host buffers, grown on demand
@@ -194,31 +214,46 @@ void run_batch(dnasa_server *srv, Slot &sl, std::vector<Pending> &batch, std::ve
     }
 }
 
+// What admission may fill: the server's budget, but never more than the device
+// memory that is free right now plus what the batches in flight have reserved
+// (their memory is counted in `reserved`, allocated or not) plus what this slot
+// already holds (its buffers are reused).  Called with srv->mu held.
+size_t effective_budget(dnasa_server *srv, const Slot &sl) {
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+        cudaGetLastError();
+        return srv->budget;
+    }
+    const size_t live = (size_t)((double)(free_b + sl.held()) * 0.95) + srv->reserved;
+    return std::min(srv->budget, live);
+}
+
 void worker(dnasa_server *srv, int k) {
     cudaSetDevice(srv->device);
     Slot &sl = srv->slots[k];
     std::vector<Pending> batch;
     std::vector<Done> out;
     for (;;) {
-        size_t est = 0;
+        size_t est = 0, budget = 0;
         {
             std::unique_lock<std::mutex> lk(srv->mu);
             for (;;) {
                 if (srv->stop && srv->queue.empty()) return;
                 if (!srv->queue.empty()) {
                     // admit the FIFO head (alone if it exceeds the budget and nothing else runs)
+                    budget = effective_budget(srv, sl);
                     const Pending &h = srv->queue.front();
-                    bool fits = srv->reserved + h.est <= srv->budget;
+                    bool fits = srv->reserved + h.est <= budget;
                     if (fits || srv->in_flight == 0) break;
                 }
-                srv->cv_work.wait(lk);
+                srv->cv_work.wait_for(lk, std::chrono::milliseconds(50));   // free HBM may change
             }
             batch.clear();
             const int32_t lmin = srv->queue.front().min_overlap;
             while (!srv->queue.empty() && (int)batch.size() < srv->max_batch) {
                 Pending &h = srv->queue.front();
                 if (h.min_overlap != lmin) break;
-                if (!batch.empty() && srv->reserved + est + h.est > srv->budget) break;
+                if (!batch.empty() && srv->reserved + est + h.est > budget) break;
                 est += h.est;
                 batch.push_back(std::move(h));
                 srv->queue.pop_front();
@@ -302,7 +337,9 @@ int dnasa_server_submit(dnasa_server *srv, const dnasa_job *job, uint64_t id) {
     p.id = id;
     p.text.assign(job->text, job->text + job->N);
     p.min_overlap = job->min_overlap;
-    p.est = job_bytes(job->N);
+    int64_t n_reads = 0;
+    for (int64_t i = 0; i < job->N; ++i) n_reads += job->text[i] == '$';
+    p.est = job_bytes(job->N, n_reads);
     {
         std::lock_guard<std::mutex> lk(srv->mu);
         if (srv->stop) return DNASA_INVALID_ARG;
@@ -343,6 +380,11 @@ int dnasa_server_poll(dnasa_server *srv, dnasa_result *out, int32_t max_results,
     }
     *n_out = n;
     return DNASA_OK;
+}
+
+int64_t dnasa_server_job_bytes(int64_t N, int64_t n_reads) {
+    if (N <= 0 || n_reads < 1 || n_reads > N) return -1;
+    return (int64_t)job_bytes(N, n_reads);
 }
 
 int dnasa_server_pending(dnasa_server *srv) {

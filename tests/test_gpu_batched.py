@@ -93,3 +93,20 @@ def test_autotune_picks_valid_options(ctx, tmp_path):
     for i in (0, 5, 11):
         t = texts[i]
         assert np.array_equal(got[inst_off[i]: inst_off[i + 1]].astype(np.int64), oracle.suffix_array(t))
+
+
+def test_assemble_batched_c3_512_instances(ctx):
+    """512 instances of the batched workload's own generator (genome log-uniform
+    2-200 kbp, reads 100-1000 bp at 8x, min overlap 31), one batched call; every
+    instance's contigs equal the oracle's.  The oracle runs on host threads (its
+    C calls release the GIL)."""
+    from concurrent.futures import ThreadPoolExecutor
+    import os
+
+    texts = [synth.batched_instance(21, i)["text"] for i in range(512)]
+    with ThreadPoolExecutor(os.cpu_count() or 4) as ex:
+        want = list(ex.map(lambda t: oracle.contigs_as_list(*oracle.assemble(t, 31)), texts))
+    got = B().assemble_texts_batched(ctx, texts, 31)
+    assert len(got) == 512
+    bad = [i for i in range(512) if got[i] != want[i]]
+    assert not bad, f"{len(bad)} instances differ, first {bad[:5]}"

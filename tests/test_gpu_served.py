@@ -109,3 +109,39 @@ def test_server_refuses_malformed_jobs_and_keeps_serving():
         assert got[i]["status"] == 0
         buf, off = oracle.assemble(js[i]["text"], js[i]["min_overlap"])
         assert got[i]["contigs"] == oracle.contigs_as_list(buf, off)
+
+
+def test_server_budget_for_two_jobs_never_runs_three():
+    """With a budget that holds exactly two jobs' estimates (and 3 slots that
+    could run more), at no moment are three jobs on the GPU: admission counts
+    each job at dnasa_server_job_bytes."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    js = [synth.served_job(8, i, g_lo=40_000, g_hi=40_000) for i in range(9)]
+    sizes = {(j["text"].size, int((j["text"] == ord("$")).sum())) for j in js}
+    assert len(sizes) == 1
+    N, nr = sizes.pop()
+    jb = B().Server.job_bytes(N, nr)
+    assert jb > 95 * N   # the suffix-array workspace alone is ~95 bytes per symbol
+    srv = B().Server(0, hbm_budget=2 * jb + jb // 2, slots=3, max_batch=8)
+    for i, j in enumerate(js):
+        srv.submit(j["text"], j["min_overlap"], i)
+    got = {}
+    deadline = time.time() + 120
+    while len(got) < len(js) and time.time() < deadline:
+        for r in srv.poll(64, wait_ms=200):
+            assert r["status"] == 0
+            got[r["id"]] = r
+    srv.close()
+    assert sorted(got) == list(range(len(js)))
+    events = sorted([(r["t_start_ms"], 1) for r in got.values()] +
+                    [(r["t_done_ms"], -1) for r in got.values()])   # ends sort before starts
+    live = peak = 0
+    for _, d in events:
+        live += d
+        peak = max(peak, live)
+    assert peak <= 2, f"{peak} jobs in flight at once"
+    assert peak == 2   # and the budget is used: two run together
+    for i in (0, 4):
+        buf, off = oracle.assemble(js[i]["text"], js[i]["min_overlap"])
+        assert got[i]["contigs"] == oracle.contigs_as_list(buf, off)

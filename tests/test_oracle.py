@@ -169,6 +169,35 @@ def test_checker_rejects_perturbations():
     assert oracle.sa_check(text, np.roll(sa, 1)) != 0
 
 
+@pytest.mark.parametrize("seed", range(4))
+def test_threaded_checker_and_kasai_equal_whole(seed):
+    """The range-split checker and Kasai (one range per thread, each range of
+    Kasai restarting at h = 0) give exactly the whole-array results: the LCP of
+    the pinned Kasai, acceptance of the true SA, and rejection of planted swaps
+    (naming the same first failing pair as the whole checker), duplicates and
+    rotations."""
+    rng = np.random.default_rng(40 + seed)
+    text, _ = random_reads_text(rng, int(rng.integers(1, 30)), 1, 300, periodic=True)
+    sa = oracle.suffix_array(text)
+    code, lcp = oracle.sa_check_and_lcp_threaded(text, sa, threads=1 + seed)
+    assert code == 0
+    assert np.array_equal(lcp, oracle.lcp_kasai(text, sa))
+    n = len(sa)
+    for _ in range(20):
+        i, j = rng.choice(n, size=2, replace=False)
+        bad = sa.copy()
+        bad[i], bad[j] = bad[j], bad[i]
+        c, l2 = oracle.sa_check_and_lcp_threaded(text, bad, threads=3)
+        assert c >= 2 and l2 is None
+        # each range reports its first failing pair, so the smallest is the
+        # whole checker's first failing pair
+        assert c == oracle.sa_check(text, bad)
+    dup = sa.copy()
+    dup[0] = dup[1]
+    assert oracle.sa_check_and_lcp_threaded(text, dup)[0] == 1
+    assert oracle.sa_check_and_lcp_threaded(text, np.roll(sa, 1))[0] != 0
+
+
 def test_check_pairs_finds_planted_errors():
     """The sampled checker accepts the true SA and LCP and flags a planted swap
     and a planted LCP error (mistakes planted in oracle data, on the CPU)."""

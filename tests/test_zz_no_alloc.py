@@ -70,3 +70,52 @@ def test_noalloc_sort_keys_only_and_limit():
         assert e.value.status == B.CAPACITY
     finally:
         ctx.close()
+
+
+def test_noalloc_sort_odd_pass_counts():
+    """An odd number of 8-bit digit passes leaves the result in the library's own
+    scratch array, from which it is copied back into the caller's buffers; the
+    second, smaller call must not see the first call's contents."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1404_3456_gb300 import binding as B
+
+    ctx = B.Context(0)
+    try:
+        cases = [(500_000, 8, True), (123_457, 20, False), (65_537, 20, True), (4_099, 8, False)]
+        for call, (n, bits, with_vals) in enumerate(cases):
+            rng = np.random.default_rng(300 + call)
+            keys = _keys(rng, n, bits)
+            vals = rng.permutation(n).astype(np.uint32) if with_vals else None
+            k_ref = torch.from_numpy(keys.view(np.int64).copy()).cuda()
+            v_ref = torch.from_numpy(vals.view(np.int32).copy()).cuda() if with_vals else None
+            B.dnasa_sort_pairs(ctx, k_ref, v_ref, key_bits=bits)
+            k_na = torch.from_numpy(keys.view(np.int64).copy()).cuda()
+            v_na = torch.from_numpy(vals.view(np.int32).copy()).cuda() if with_vals else None
+            B.dnasa_sort_pairs_noalloc(k_na, v_na, key_bits=bits)
+            torch.cuda.synchronize()
+            assert torch.equal(k_na, k_ref), f"keys differ on call {call}"
+            if with_vals:
+                assert torch.equal(v_na, v_ref), f"values differ on call {call}"
+    finally:
+        ctx.close()
+
+
+def test_noalloc_sort_refuses_host_pointers():
+    """A host buffer handed to the C entry point is refused before any launch."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import ctypes
+    from paper_1404_3456_gb300 import binding as B
+
+    torch.cuda.init()
+    host_keys = np.zeros(1024, dtype=np.uint64)
+    host_vals = np.zeros(1024, dtype=np.uint32)
+    dev_keys = torch.zeros(1024, dtype=torch.int64, device="cuda")
+    rc = B.lib().dnasa_sort_pairs_noalloc(ctypes.c_void_p(host_keys.ctypes.data), None, 1024, 8, None)
+    assert rc == B.INVALID_ARG
+    rc = B.lib().dnasa_sort_pairs_noalloc(ctypes.c_void_p(dev_keys.data_ptr()),
+                                          ctypes.c_void_p(host_vals.ctypes.data), 1024, 8, None)
+    assert rc == B.INVALID_ARG
+    with pytest.raises(ValueError):
+        B.dnasa_sort_pairs_noalloc(torch.zeros(16, dtype=torch.int32, device="cuda"))
