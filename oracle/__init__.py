@@ -21,6 +21,9 @@ Every function follows one passage of the paper (arxiv 1404.3456):
 * :func:`contained`        -- Sec. III, fragments lying inside another fragment.
 * :func:`layout`, :func:`assemble` -- Sec. III, Fig. 3 (path -> superstring) and the
   RS concatenation: greedy unique-overlap layout and spelling.
+* :func:`fir_reconstruct` -- Sec. III, Figs. 2 and 5-8: a sequence cut by two
+  shotguns rebuilt from "fir" (prefix) relations by depth-first search with
+  back-tracking.
 
 Readings of the paper that these functions fix (the paper is silent on them):
 every fragment ends with its own '$' sentinel, smaller than A < C < G < T, and
@@ -91,6 +94,8 @@ def _load():
             lib.oracle_contained.restype = ctypes.c_int
             lib.oracle_layout.argtypes = [P, P, I64, P, P, P, I64, P, P, I64, P, I64, P, P]
             lib.oracle_layout.restype = ctypes.c_int
+            lib.oracle_fir_reconstruct.argtypes = [P, P, I64, I64, P, P, P]
+            lib.oracle_fir_reconstruct.restype = I64
             _lib = lib
     return _lib
 
@@ -287,3 +292,31 @@ def assemble(text, lmin: int, overlap_fn=overlaps_sorted):
 
 def contigs_as_list(buf: np.ndarray, off: np.ndarray):
     return [bytes(buf[off[i]: off[i + 1]]) for i in range(off.size - 1)]
+
+
+FIR_SOLVED, FIR_NONE, FIR_GAVE_UP = 0, 1, 2
+
+
+def fir_reconstruct(text, max_steps: int = 1 << 40):
+    """Sec. III two-cut reconstruction.  Returns (status, frag_start, rs, steps):
+    status 0 solved / 1 none exists / 2 gave up after max_steps placed fragments;
+    frag_start[r] = offset of fragment r in the result RS (-1 unless solved);
+    rs = the reconstructed sequence (bytes, empty unless solved)."""
+    t = _text(text)
+    toff = read_offsets(t)
+    nr = toff.size - 1
+    start = np.empty(max(nr, 1), dtype=np.int64)
+    st = ctypes.c_int32(0)
+    rl = ctypes.c_int64(0)
+    steps = _load().oracle_fir_reconstruct(_ptr(t), _ptr(toff), nr, int(max_steps), _ptr(start),
+                                           ctypes.byref(st), ctypes.byref(rl))
+    if steps < 0:
+        raise RuntimeError(f"oracle_fir_reconstruct failed ({steps})")
+    start = start[:nr].copy()
+    rs = b""
+    if st.value == FIR_SOLVED:
+        buf = np.zeros(rl.value, dtype=np.uint8)
+        for r in range(nr):
+            buf[start[r]: start[r] + toff[r + 1] - 1 - toff[r]] = t[toff[r]: toff[r + 1] - 1]
+        rs = buf.tobytes()
+    return int(st.value), start, rs, int(steps)

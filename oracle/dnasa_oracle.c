@@ -37,6 +37,9 @@
  *   oracle_contained        Sec. III: fragments that occur inside another one
  *   oracle_layout           Sec. III (Fig. 3 path -> superstring, RS concatenation):
  *                           greedy unique-overlap layout, then spelling
+ *   oracle_fir_reconstruct  Sec. III (Figs. 2, 5-8): a sequence cut by two shotguns
+ *                           rebuilt from fir relations by depth-first search with
+ *                           back-tracking
  *
  * Return codes: >= 0 success (or a count), -1 bad argument, -2 capacity,
  * -3 allocation failure.
@@ -524,4 +527,114 @@ int oracle_layout(const uint8_t *T, const int64_t *toff, int64_t nr,
     free(E); free(succ); free(succL); free(pred); free(parent);
     if (nb > cap || nc + 1 > off_cap) return -2;
     return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. III, Figs. 2 and 5-8: reconstruction of a sequence cut by two          */
+/* shotguns from "fir" relations, with back-tracking.                          */
+/*                                                                            */
+/* The fragments are the pieces of two cuttings of one sequence S, shuffled   */
+/* (Fig. 2: m + n fragments), every break position different (Fig. 4).  Both */
+/* cuttings start at the beginning of S, so the first piece of one is a      */
+/* prefix of the first piece of the other: a "fir" pair.  Cutting the shorter */
+/* from the longer leaves a remainder X (Fig. 6), and the next piece of the   */
+/* shorter one's cutting starts where X starts: either it is a prefix of X    */
+/* (cut it off X and continue with the rest of X) or X is a prefix of it      */
+/* (continue with the part of it past X).  When a choice leads to a state     */
+/* with no fir fragment, or to a result that leaves fragments unselected,    */
+/* the search backs up and takes the next choice (Figs. 7-8).                */
+/*                                                                            */
+/* Readings (the paper gives no listing):                                     */
+/*  - start pairs (i, k): d_i a proper prefix of d_k, tried for k ascending,   */
+/*    then i ascending; the remainder is d_k past |d_i|;                      */
+/*  - with remainder X (length l), the unused fragments c are tried in        */
+/*    ascending index: |c| < l and c a prefix of X -> remainder X past |c|;   */
+/*    |c| > l and X a prefix of c -> remainder c past l; |c| == l and c == X  */
+/*    only as the very last fragment (both cuttings end together: done);     */
+/*  - every placed fragment starts where its remainder starts in the result  */
+/*    RS (the start pair at 0), and RS ends where the last fragment ends;    */
+/*  - a step is one placed fragment (the start pair counts as one); after    */
+/*    max_steps steps the search gives up.                                    */
+/* Writes frag_start[r] (offset of fragment r in RS, -1 when not solved),     */
+/* *status (0 solved, 1 no reconstruction exists, 2 gave up) and *rs_len.    */
+/* Returns the number of steps taken, or < 0 on a bad argument.              */
+/* ------------------------------------------------------------------------ */
+typedef struct { int64_t k, o, c; } fir_frame_t;   /* remainder (k, o); c: fragment placed from it */
+
+/* 1 if the first la symbols of a equal those of b (la <= available length of b). */
+static int same_prefix(const uint8_t *a, const uint8_t *b, int64_t la)
+{
+    return memcmp(a, b, (size_t)la) == 0;
+}
+
+int64_t oracle_fir_reconstruct(const uint8_t *T, const int64_t *toff, int64_t nr, int64_t max_steps,
+                               int64_t *frag_start, int32_t *status, int64_t *rs_len)
+{
+    if (!reads_ok(T, toff, nr) || !frag_start || !status || !rs_len || max_steps < 1) return -1;
+    uint8_t *used = (uint8_t *)calloc((size_t)(nr ? nr : 1), 1);
+    fir_frame_t *F = (fir_frame_t *)malloc((size_t)(nr ? nr : 1) * sizeof(fir_frame_t));
+    if (!used || !F) { free(used); free(F); return -3; }
+    for (int64_t r = 0; r < nr; ++r) frag_start[r] = -1;
+    *status = 1;
+    *rs_len = 0;
+    int64_t steps = 0;
+    int done = 0;
+    for (int64_t k = 0; k < nr && !done && *status != 2; ++k) {
+        const int64_t lk = read_len(toff, k);
+        for (int64_t i = 0; i < nr && !done; ++i) {
+            const int64_t li = read_len(toff, i);
+            if (i == k || li >= lk || !same_prefix(T + toff[i], T + toff[k], li)) continue;
+            if (++steps > max_steps) { *status = 2; break; }
+            used[i] = used[k] = 1;
+            frag_start[i] = frag_start[k] = 0;
+            int64_t top = 0;
+            F[0].k = k; F[0].o = li; F[0].c = -1;
+            while (top >= 0 && !done) {
+                fir_frame_t *f = &F[top];
+                int64_t from = 0;
+                if (f->c >= 0) {               /* back from the child: undo its fragment */
+                    used[f->c] = 0;
+                    frag_start[f->c] = -1;
+                    from = f->c + 1;
+                    f->c = -1;
+                }
+                const int64_t l = read_len(toff, f->k) - f->o;     /* remainder length */
+                const uint8_t *X = T + toff[f->k] + f->o;
+                const int64_t pos = frag_start[f->k] + f->o;
+                const int64_t nused = 2 + top;
+                int64_t c = from;
+                int64_t nk = -1, no = 0;
+                for (; c < nr; ++c) {
+                    if (used[c]) continue;
+                    const int64_t lc = read_len(toff, c);
+                    const uint8_t *C = T + toff[c];
+                    if (lc < l && same_prefix(C, X, lc)) { nk = f->k; no = f->o + lc; break; }
+                    if (lc > l && same_prefix(X, C, l)) { nk = c; no = l; break; }
+                    if (lc == l && nused + 1 == nr && same_prefix(C, X, l)) { nk = -2; break; }
+                }
+                if (c >= nr) { --top; continue; }   /* no fir fragment: back-track */
+                if (++steps > max_steps) { *status = 2; break; }
+                used[c] = 1;
+                frag_start[c] = pos;
+                f->c = c;
+                if (nk == -2) {                    /* both cuttings end here */
+                    done = 1;
+                    *status = 0;
+                    *rs_len = pos + l;
+                    break;
+                }
+                ++top;
+                F[top].k = nk; F[top].o = no; F[top].c = -1;
+            }
+            if (!done) {
+                for (int64_t r = 0; r < nr; ++r) { used[r] = 0; frag_start[r] = -1; }
+            }
+            if (*status == 2) break;
+        }
+    }
+    if (*status != 0)
+        for (int64_t r = 0; r < nr; ++r) frag_start[r] = -1;
+    free(used);
+    free(F);
+    return steps;
 }

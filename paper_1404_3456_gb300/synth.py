@@ -27,6 +27,11 @@ Workloads
 ``large``    1.5 Gbp genome: 85 % i.i.d., 10 % tandem (period U{2..100},
              copies U{10..200}), 5 % copies of a 6 kbp element with 0.5 %
              substitutions; plus 10 M reads of 150 bp at 1x.
+``two_cut``  the paper's own model (Sec. III, Fig. 2): one genome cut by two
+             shotguns into two sets of consecutive pieces, all break positions
+             different (Fig. 4) and at least ``min_gap`` apart; the pieces of
+             both cuttings shuffled into one fragment set.  Optionally with
+             tandem arrays or repeated elements (ambiguous fir relations).
 """
 from __future__ import annotations
 
@@ -218,3 +223,40 @@ def large_reads(seed: int, genome: np.ndarray, n_reads: int = 10_000_000, read_l
         text[c0:c1, :read_len] = genome[starts[c0:c1, None] + cols]
     text[:, read_len] = SEP
     return text.ravel(), starts
+
+
+def two_cut(seed: int, G: int, mean_len: int = 500, min_gap: int = 24, frac_tandem: float = 0.0,
+            period: tuple = (2, 50), copies: tuple = (10, 200), frac_elem: float = 0.0,
+            elem_len: int = 0, elem_subst: float = 0.0, genome: np.ndarray | None = None):
+    """A genome cut twice (Sec. III, Fig. 2).  About G / mean_len pieces per
+    cutting; the union of both cuttings' break positions is drawn with every two
+    breaks at least min_gap apart (so every piece and every remainder is at
+    least min_gap long), and each break goes to one of the two cuttings at
+    random.  Returns dict(genome, text, frag_start (true offset of each fragment
+    in the genome, in text order), cut (0/1 per fragment))."""
+    rng = rng_for(seed, 7)
+    if genome is None:
+        genome = (genome_with_repeats(rng, G, frac_tandem, period, copies, frac_elem, elem_len,
+                                      elem_subst)
+                  if (frac_tandem > 0 or frac_elem > 0) else iid(rng, G))
+    G = int(genome.size)
+    K = max(2, 2 * int(round(G / mean_len)) - 2)        # breaks of both cuttings together
+    K = min(K, G // min_gap - 1)
+    free = G - (K + 1) * min_gap
+    if K < 2 or free < 0:
+        raise ValueError("genome too short for two cuttings with this min_gap")
+    u = np.sort(rng.integers(0, free + 1, size=K))
+    breaks = u + min_gap * np.arange(1, K + 1)           # strictly increasing, gaps >= min_gap
+    side = rng.integers(0, 2, size=K)
+    side[0], side[1] = 0, 1                              # each cutting breaks at least once
+    frags, starts, cuts = [], [], []
+    for c in (0, 1):
+        b = np.concatenate([[0], breaks[side == c], [G]])
+        for a, e in zip(b[:-1], b[1:]):
+            frags.append(genome[a:e])
+            starts.append(int(a))
+            cuts.append(c)
+    order = rng.permutation(len(frags))
+    frags = [frags[i] for i in order]
+    return dict(genome=genome, text=join_reads(frags), frag_start=np.array(starts)[order],
+                cut=np.array(cuts)[order])
