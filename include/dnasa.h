@@ -267,6 +267,54 @@ int assemble(dnasa_ctx *ctx, const uint8_t *text, int64_t N, int32_t min_overlap
              uint8_t *contigs, int64_t cap, int64_t *contig_off, int64_t off_cap,
              int64_t *n_contigs, int64_t *needed, void *stream);
 
+/* ---- two-cut reconstruction from fir relations (Sec. III, Figs. 2, 5-8) --- */
+
+/* Status of a fir reconstruction. */
+enum { DNASA_FIR_SOLVED = 0, DNASA_FIR_NONE = 1, DNASA_FIR_GAVE_UP = 2 };
+
+/* Rebuilds a sequence cut by two shotguns (Sec. III, Fig. 2: the fragments are
+ * the pieces of two cuttings of one sequence, shuffled, every break position
+ * different) from "fir" relations, by depth-first search with back-tracking:
+ * a start pair is a fragment d_i that is a proper prefix of a fragment d_k
+ * (tried for k ascending, then i ascending); with remainder X (what is left of
+ * the longer fragment past the shorter), the unused fragments in fir relation
+ * with X are tried in ascending index -- a fragment c that is a proper prefix of
+ * X leaves X past |c|; X a proper prefix of c leaves c past |X|; c equal to X
+ * ends the search when it is the last fragment.  A choice that leaves no fir
+ * fragment is undone and the next one tried (Figs. 7-8).  The fir relations of
+ * every suffix of every fragment come from one pass over the suffix array of
+ * the fragment text (Sec. IV: binary search of a suffix among the fragment
+ * starts, then the LCP of consecutive fragment starts).
+ *   text        device, N bytes: '$'-terminated fragments (as for dnasa_pack)
+ *   max_steps   >= 1: placed fragments (a start pair counts as one) after which
+ *               the search gives up (DNASA_FIR_GAVE_UP)
+ *   frag_start  device, frag_cap int64: offset of each fragment in the result
+ *               (-1 for all when not solved)
+ *   rs          device, rs_cap bytes: the reconstructed sequence (ASCII ACGT)
+ *   rs_len      host out: its length (0 when not solved)
+ *   status      host out: DNASA_FIR_SOLVED, _NONE (no reconstruction exists) or
+ *               _GAVE_UP;  steps  host out: steps taken
+ * Synchronizes the stream.  DNASA_CAPACITY when frag_cap is below the number
+ * of fragments or rs_cap below rs_len (*rs_len is set). */
+int fir_reconstruct(dnasa_ctx *ctx, const uint8_t *text, int64_t N, int64_t max_steps,
+                    int64_t *frag_start, int64_t frag_cap, uint8_t *rs, int64_t rs_cap,
+                    int64_t *rs_len, int32_t *status, int64_t *steps, void *stream);
+
+/* fir_reconstruct of n_inst independent fragment texts stored one after another
+ * (inst_off: host, n_inst + 1 offsets, each a fragment start), in one pass: one
+ * suffix array, one fir-relation pass and one search thread per instance.
+ *   frag_start  device int64[frag_cap]: per fragment (global index), offset in
+ *               its own instance's result
+ *   rs_off      device int64[n_inst + 1]: instance i's result is
+ *               rs[rs_off[i] .. rs_off[i+1]) (empty when not solved)
+ *   status      device int32[n_inst];  steps  device int64[n_inst]
+ *   rs_total    host out: bytes of all results
+ * Synchronizes the stream.  DNASA_CAPACITY as for fir_reconstruct. */
+int fir_reconstruct_batched(dnasa_ctx *ctx, const uint8_t *texts, const int64_t *inst_off, int32_t n_inst,
+                            int64_t max_steps, int64_t *frag_start, int64_t frag_cap, uint8_t *rs,
+                            int64_t rs_cap, int64_t *rs_off, int32_t *status, int64_t *steps,
+                            int64_t *rs_total, void *stream);
+
 /* ---- batched -- many independent fragment sets in one pass ------------- */
 
 /* Suffix arrays of n_inst independent fragment texts stored one after another

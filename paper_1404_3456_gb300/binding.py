@@ -97,6 +97,10 @@ _SIGS = {
     "dnasa_server_pending": (_INT, [_P]),
     "dnasa_server_job_bytes": (_I64, [_I64, _I64]),
     "dnasa_server_destroy": (None, [_P]),
+    "fir_reconstruct": (_INT, [_P, _P, _I64, _I64, _P, _I64, _P, _I64, ctypes.POINTER(_I64),
+                               ctypes.POINTER(_I32), ctypes.POINTER(_I64), _P]),
+    "fir_reconstruct_batched": (_INT, [_P, _P, _P, _I32, _I64, _P, _I64, _P, _I64, _P, _P, _P,
+                                       ctypes.POINTER(_I64), _P]),
     "sa_build_batched": (_INT, [_P, _P, _P, _I64, _I64, _P, _I32, _P, ctypes.POINTER(Opts), _P]),
     "assemble_batched": (_INT, [_P, _P, _P, _I32, _I32, ctypes.POINTER(Opts), _P, _I64, _P, _I64,
                                 _P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), _P]),
@@ -373,6 +377,53 @@ def assemble_texts_batched(ctx: Context, texts_np, min_overlap: int, opts=None, 
     o = off[: nc + 1].cpu().tolist()
     io = ioff.cpu().tolist()
     return [[buf[o[c]: o[c + 1]] for c in range(io[i], io[i + 1])] for i in range(len(texts_np))]
+
+
+FIR_SOLVED, FIR_NONE, FIR_GAVE_UP = 0, 1, 2   # DNASA_FIR_* in dnasa.h
+
+
+def fir_reconstruct(ctx: Context, text: torch.Tensor, max_steps: int = 1 << 40, stream=None):
+    """Two-cut reconstruction of one fragment text (device uint8).  Returns
+    (status, frag_start int64 tensor, result bytes, steps)."""
+    N = text.numel()
+    nf = int((text == ord("$")).sum().item())
+    start = torch.empty(max(nf, 1), dtype=torch.int64, device=text.device)
+    rs = torch.empty(max(N, 1), dtype=torch.uint8, device=text.device)
+    rl, st, steps = ctypes.c_int64(0), ctypes.c_int32(0), ctypes.c_int64(0)
+    ctx.check(lib().fir_reconstruct(ctx.handle, _ptr(text), N, max_steps, _ptr(start), start.numel(),
+                                    _ptr(rs), rs.numel(), ctypes.byref(rl), ctypes.byref(st),
+                                    ctypes.byref(steps), _stream(stream)))
+    return int(st.value), start[:nf], rs[: rl.value].cpu().numpy().tobytes(), int(steps.value)
+
+
+def fir_reconstruct_batched(ctx: Context, texts_np, max_steps: int = 1 << 40, stream=None):
+    """Two-cut reconstruction of several fragment texts (numpy uint8) in one call.
+    Returns one (status, frag_start numpy int64, result bytes, steps) per text."""
+    import numpy as np
+
+    sizes = [int(t.size) for t in texts_np]
+    inst_off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    joined_np = np.concatenate(texts_np)
+    nf = int((joined_np == ord("$")).sum())
+    joined = torch.from_numpy(joined_np).cuda()
+    n = len(texts_np)
+    N = int(inst_off[-1])
+    start = torch.empty(max(nf, 1), dtype=torch.int64, device="cuda")
+    rs = torch.empty(max(N, 1), dtype=torch.uint8, device="cuda")
+    rs_off = torch.empty(n + 1, dtype=torch.int64, device="cuda")
+    status = torch.empty(n, dtype=torch.int32, device="cuda")
+    steps = torch.empty(n, dtype=torch.int64, device="cuda")
+    total = ctypes.c_int64(0)
+    arr, p = _host_i64(inst_off)
+    ctx.check(lib().fir_reconstruct_batched(ctx.handle, _ptr(joined), p, n, max_steps, _ptr(start),
+                                            start.numel(), _ptr(rs), rs.numel(), _ptr(rs_off),
+                                            _ptr(status), _ptr(steps), ctypes.byref(total),
+                                            _stream(stream)))
+    st, so, sp = status.cpu().numpy(), rs_off.cpu().numpy(), steps.cpu().numpy()
+    buf = rs[: total.value].cpu().numpy().tobytes()
+    fs = start[:nf].cpu().numpy()
+    foff = np.concatenate([[0], np.cumsum([int((t == ord("$")).sum()) for t in texts_np])])
+    return [(int(st[i]), fs[foff[i]: foff[i + 1]], buf[so[i]: so[i + 1]], int(sp[i])) for i in range(n)]
 
 
 class Server:

@@ -49,25 +49,6 @@ struct SaView {
     uint32_t *owned = nullptr;
 };
 
-// stream-ordered device buffer
-struct DevBuf {
-    void *p = nullptr;
-    cudaStream_t s = nullptr;
-    ~DevBuf() {
-        if (p) cudaFreeAsync(p, s);
-    }
-};
-
-int dev_alloc(dnasa_ctx *ctx, DevBuf &b, size_t bytes, cudaStream_t s) {
-    b.s = s;
-    cudaError_t e = cudaMallocAsync(&b.p, std::max<size_t>(bytes, 256), s);
-    if (e != cudaSuccess) {
-        b.p = nullptr;
-        return cuda_fail(ctx, e, "cudaMallocAsync");
-    }
-    return DNASA_OK;
-}
-
 __global__ void k_narrow(const int64_t *__restrict__ a, int64_t n, uint32_t *__restrict__ b) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
@@ -121,6 +102,18 @@ __global__ void k_localize(uint32_t *__restrict__ sa, int64_t N, const int64_t *
     }
 }
 
+}  // namespace
+
+int dev_alloc(dnasa_ctx *ctx, DevBuf &b, size_t bytes, cudaStream_t s) {
+    b.s = s;
+    cudaError_t e = cudaMallocAsync(&b.p, std::max<size_t>(bytes, 256), s);
+    if (e != cudaSuccess) {
+        b.p = nullptr;
+        return cuda_fail(ctx, e, "cudaMallocAsync");
+    }
+    return DNASA_OK;
+}
+
 // Device copies of the instance offsets (text and fragment), with checks.
 int make_instances(dnasa_ctx *ctx, const int64_t *toff, int64_t n_reads, int64_t N,
                    const int64_t *inst_toff_host, int32_t n_inst, DevBuf &inst_toff, DevBuf &inst_roff,
@@ -149,8 +142,6 @@ int make_instances(dnasa_ctx *ctx, const int64_t *toff, int64_t n_reads, int64_t
     for (int i = 0; i < n_inst; ++i) *max_reads = std::max(*max_reads, roff[i + 1] - roff[i]);
     return DNASA_OK;
 }
-
-}  // namespace
 
 // Whole pipeline on a text already on the device, possibly several instances.
 int assemble_impl(dnasa_ctx *ctx, const uint8_t *text, int64_t N, const int64_t *inst_toff_host,

@@ -175,6 +175,21 @@ struct TextDesc {
     const uint32_t *fid;       // device, N: fragment of each text position (nullptr: search toff)
 };
 
+// Stream-ordered device buffer, freed on the stream when it goes out of scope.
+struct DevBuf {
+    void *p = nullptr;
+    cudaStream_t s = nullptr;
+    ~DevBuf() {
+        if (p) cudaFreeAsync(p, s);
+    }
+};
+int dev_alloc(dnasa_ctx *ctx, DevBuf &b, size_t bytes, cudaStream_t s);
+// Device copies of the instance offsets of a batch: text offsets (from the host
+// array inst_toff_host, n_inst + 1 entries) and the first fragment of each
+// instance; *max_reads = most fragments in one instance.  Synchronizes s.
+int make_instances(dnasa_ctx *ctx, const int64_t *toff, int64_t n_reads, int64_t N,
+                   const int64_t *inst_toff_host, int32_t n_inst, DevBuf &inst_toff, DevBuf &inst_roff,
+                   int64_t *max_reads, cudaStream_t s);
 // Device workspace sa_build_u32 takes for an N-symbol text (bytes, before the
 // context's growth margin).
 size_t sa_workspace_bytes(int64_t N, int tile_items);
