@@ -56,7 +56,8 @@ def parse():
     ap.add_argument("--genome", type=int, default=G, help="genome length (default 64,000,000)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="sa64m", choices=["sa64m", "large", "batched", "served"])
+    ap.add_argument("--workload", default="sa64m",
+                    choices=["sa64m", "large", "batched", "served", "fir", "approx"])
     ap.add_argument("--instances", type=int, default=4096, help="batched: fragment sets per batch")
     ap.add_argument("--solo-sample", type=int, default=256,
                     help="batched: instances timed one job per launch")
@@ -461,6 +462,245 @@ def run_batched(args):
     return 0
 
 
+def run_fir(args):
+    """Two-cut workload (Sec. III, Fig. 2): independent genomes log-uniform
+    2-200 kbp, each cut by two shotguns into pieces of mean 500 bp (every break
+    different, at least 24 bp apart), the pieces of both shuffled; one
+    fir_reconstruct_batched call per step rebuilds every genome by the fir
+    search with back-tracking."""
+    import torch
+
+    import oracle
+    from paper_1404_3456_gb300 import binding, synth
+
+    rank, local_rank, world = dist_env()
+    rank_setup(local_rank, world)
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    n_inst = args.instances
+    texts, genomes = [], []
+    for i in range(n_inst):   # instances shard by rank: each rank draws its own
+        rng = synth.rng_for(args.seed * 1_000_003 + 1000 * rank + i, 8)
+        G = synth.log_uniform(rng, 2_000, 200_000)
+        d = synth.two_cut(args.seed * 1_000_003 + 1000 * rank + i, G, mean_len=500)
+        texts.append(d["text"])
+        genomes.append(d["genome"])
+    inst_off = np.concatenate([[0], np.cumsum([t.size for t in texts])]).astype(np.int64)
+    N = int(inst_off[-1])
+    nf = int(sum(int((t == ord("$")).sum()) for t in texts))
+    ctx = binding.Context(local_rank)
+    h_text = torch.from_numpy(np.concatenate(texts)).pin_memory()
+    d_text = h_text.cuda()
+    start = torch.empty(nf, dtype=torch.int64, device=dev)
+    rs = torch.empty(N, dtype=torch.uint8, device=dev)
+    rs_off = torch.empty(n_inst + 1, dtype=torch.int64, device=dev)
+    status = torch.empty(n_inst, dtype=torch.int32, device=dev)
+    steps_d = torch.empty(n_inst, dtype=torch.int64, device=dev)
+    max_steps = 1 << 20
+    stream = torch.cuda.current_stream()
+
+    def step(t=d_text):
+        return binding.fir_reconstruct_batched_into(ctx, t, inst_off, max_steps, start, rs, rs_off,
+                                                    status, steps_d)
+
+    for _ in range(args.warmup):
+        total = step()
+    torch.cuda.synchronize()
+    st = status.cpu().numpy()
+    so = rs_off.cpu().numpy()
+    buf = rs[:total].cpu().numpy()
+    solved = int((st == 0).sum())
+    exact = sum(1 for i in range(n_inst)
+                if st[i] == 0 and np.array_equal(buf[so[i]: so[i + 1]], genomes[i]))
+    l0 = ctx.launch_count()
+    clocks = ClockSampler(local_rank)
+    rank_barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        total = step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    rank_barrier(world)
+    clk = clocks.stop()
+    launches = ctx.launch_count() - l0
+    ms = e0.elapsed_time(e1) / args.steps
+    ctx.profile(True)
+    for _ in range(args.steps):
+        step()
+    torch.cuda.synchronize()
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    h_rs = torch.empty(N, dtype=torch.uint8).pin_memory()
+    d2 = torch.empty_like(d_text)
+    x0, x1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    x0.record(stream)
+    for _ in range(args.steps):
+        d2.copy_(h_text, non_blocking=True)
+        total = step(d2)
+        h_rs[:total].copy_(rs[:total], non_blocking=True)
+        h_off = rs_off.cpu()
+    x1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = x0.elapsed_time(x1) / args.steps
+    ms, e2e_ms = over_ranks([ms, e2e_ms], world, "max", dev)
+    launches = int(over_ranks([launches], world, "sum", dev)[0])
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        sample = texts[: min(256, n_inst)]
+        t0 = time.perf_counter()
+        for t in sample:
+            oracle.fir_reconstruct(t, max_steps)
+        dt = time.perf_counter() - t0
+        cpu = {"value": len(sample) / dt, "unit": "reconstructions/s", "cores": 1, "kind": "oracle",
+               "sample": f"oracle fir search (direct string comparison, no suffix array) on the "
+                         f"first {len(sample)} instances, {dt:.1f} s"}
+    peak, src = measured_peak()
+    roof, kernels = roofline_of(prof, peak, src, args.steps)
+    line = {
+        "metric": f"two-cut fir reconstructions/s (fir_reconstruct_batched, {n_inst} genomes)",
+        "value": n_inst * world / (ms / 1000.0), "unit": "reconstructions/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8/int32", "data": "synthetic",
+        "config": {"workload": f"fir: {n_inst} genomes log-uniform 2-200 kbp, each cut twice into "
+                               f"pieces of mean 500 bp ({nf:,} fragments, {N:,} symbols)",
+                   "solved": solved, "recovered_exactly": exact,
+                   "msuffix_per_s": N * world / (ms / 1000.0) / 1e6},
+        "roofline": roof, "cpu_baseline": cpu,
+        "e2e": {"value": n_inst * world / (e2e_ms / 1000.0), "unit": "reconstructions/s",
+                "h2d_bytes_per_step": N, "d2h_bytes_per_step": int(total) + 8 * (n_inst + 1),
+                "ms_per_step": e2e_ms},
+        "gpu_launches": launches, "clocks": clk, "kernels": kernels,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    rank_teardown(world)
+    return 0
+
+
+def approx_reads(seed: int, G: int, coverage: float = 10.0, read_len: int = 150, subs: float = 0.01):
+    """Reads of a G-base i.i.d. genome at uniform starts, each from a random strand
+    (reverse complemented with probability 1/2) and with each base substituted
+    with probability subs."""
+    from paper_1404_3456_gb300 import synth
+
+    rng = synth.rng_for(seed, 10)
+    genome = synth.iid(rng, G)
+    text, starts = synth.shotgun_fixed_text(rng, genome, coverage, read_len)
+    m = text.reshape(-1, read_len + 1)[:, :read_len]
+    codes = np.searchsorted(synth.BASES, m).astype(np.uint8)
+    hit = rng.random(m.shape) < subs
+    codes = np.where(hit, (codes + rng.integers(1, 4, size=m.shape, dtype=np.uint8)) % 4, codes)
+    rev = rng.random(m.shape[0]) < 0.5
+    codes[rev] = (3 - codes[rev])[:, ::-1]            # reverse complement (A<->T, C<->G)
+    m[:] = synth.BASES[codes]
+    return text
+
+
+def run_approx(args):
+    """Overlaps on both strands with substitutions (Sec. III DEFINITION): reads of
+    150 bp at 10x from a 1 Mbp genome, half of them reverse complemented, 1 %
+    substitutions; overlap_search_approx with both strands, min overlap 40, at
+    most one mismatch per 30 bases."""
+    import torch
+
+    import oracle
+    from paper_1404_3456_gb300 import binding
+
+    rank, local_rank, world = dist_env()
+    rank_setup(local_rank, world)
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    G = 1_000_000
+    text_np = approx_reads(args.seed + 1000 * rank, G)
+    N = int(text_np.size)
+    nr = int((text_np == ord("$")).sum())
+    ctx = binding.Context(local_rank)
+    h_text = torch.from_numpy(text_np).pin_memory()
+    d_text = h_text.cuda()
+    edges, _ = binding.overlap_search_approx(ctx, d_text, 40, 1, 30, True)   # sizes the edge buffer
+    cap = int(edges.shape[0]) + 1024
+    buf = torch.empty((cap, 4), dtype=torch.int32, device=dev)
+    import ctypes
+
+    n_e, n_o = ctypes.c_int64(0), ctypes.c_int64(0)
+    stream = torch.cuda.current_stream()
+
+    def step(t=d_text):
+        ctx.check(binding.lib().overlap_search_approx(ctx.handle, ctypes.c_void_p(t.data_ptr()), N, 40, 1, 30,
+                                                      1, ctypes.c_void_p(buf.data_ptr()), cap,
+                                                      ctypes.byref(n_e), ctypes.byref(n_o), None))
+        return n_e.value
+
+    for _ in range(args.warmup):
+        ne = step()
+    l0 = ctx.launch_count()
+    clocks = ClockSampler(local_rank)
+    rank_barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        ne = step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    rank_barrier(world)
+    clk = clocks.stop()
+    launches = ctx.launch_count() - l0
+    ms = e0.elapsed_time(e1) / args.steps
+    ctx.profile(True)
+    for _ in range(args.steps):
+        step()
+    torch.cuda.synchronize()
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    h_edges = torch.empty((cap, 4), dtype=torch.int32).pin_memory()
+    d2 = torch.empty_like(d_text)
+    x0, x1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    x0.record(stream)
+    for _ in range(args.steps):
+        d2.copy_(h_text, non_blocking=True)
+        ne = step(d2)
+        h_edges[:ne].copy_(buf[:ne], non_blocking=True)
+    x1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = x0.elapsed_time(x1) / args.steps
+    ms, e2e_ms = over_ranks([ms, e2e_ms], world, "max", dev)
+    launches = int(over_ranks([launches], world, "sum", dev)[0])
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        sample = approx_reads(args.seed, 15_000)
+        t0 = time.perf_counter()
+        oracle.overlaps_approx(sample, 40, 1, 30, True)
+        dt = time.perf_counter() - t0
+        cpu = {"value": sample.size / dt / 1e6, "unit": "Msymbol/s", "cores": 1, "kind": "oracle",
+               "sample": f"oracle all-pairs approximate overlaps of the reads of a 15 kbp genome "
+                         f"({sample.size:,} symbols), {dt:.1f} s; all pairs: its rate falls as the "
+                         "read set grows"}
+    peak, src = measured_peak()
+    roof, kernels = roofline_of(prof, peak, src, args.steps)
+    line = {
+        "metric": "approximate two-strand overlap search Msymbol/s (overlap_search_approx)",
+        "value": N * world / (ms / 1000.0) / 1e6, "unit": "Msymbol/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8/int32", "data": "synthetic",
+        "config": {"workload": f"approx: {nr:,} reads x 150 bp at 10x of a {G:,} bp genome, half reverse "
+                               "complemented, 1 % substitutions; both strands, min overlap 40, mu = 1/30",
+                   "edges": int(ne)},
+        "roofline": roof, "cpu_baseline": cpu,
+        "e2e": {"value": N * world / (e2e_ms / 1000.0) / 1e6, "unit": "Msymbol/s", "h2d_bytes_per_step": N,
+                "d2h_bytes_per_step": 16 * int(ne), "ms_per_step": e2e_ms},
+        "gpu_launches": launches, "clocks": clk, "kernels": kernels,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    rank_teardown(world)
+    return 0
+
+
 def run_served(args):
     """Served workload: jobs with genome log-uniform 5 kbp - 5 Mbp (2 % tandem
     arrays), 150 bp reads at 10x, min overlap 41, arriving as a Poisson process at
@@ -560,6 +800,10 @@ def main():
         return run_reference(args)
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "fir":
+        return run_fir(args)
+    if args.workload == "approx":
+        return run_approx(args)
     if args.workload == "served":
         return run_served(args)
     import torch

@@ -73,7 +73,9 @@ typedef struct {
     int64_t finish_threshold;  /* when the suffixes still unsorted after a doubling round
                                   number at most this many, and every unsorted group has at
                                   most 1024 members, the rest is sorted by direct comparison
-                                  of packed words; -1 = never; 0 = default */
+                                  of packed words; -1 = never; 0 = default (never: on the
+                                  repeat-rich genomes measured, the doubling rounds were
+                                  faster; the autotuner tries the switch) */
     int32_t max_rounds;        /* safety bound on doubling rounds (default 63) */
     int32_t lookback;          /* look-back loads in flight per digit in a onesweep pass:
                                   8 (default) or 1 */
@@ -91,6 +93,12 @@ typedef struct {
 typedef struct {
     int32_t j, k, L;
 } dnasa_edge;
+
+/* An overlap between oriented fragments allowing substitutions: the last L
+ * bases of a and the first L bases of b differ in `mismatches` places. */
+typedef struct {
+    int32_t a, b, L, mismatches;
+} dnasa_aedge;
 
 /* Per-round trace of the last sa_build on a context (host-readable). */
 typedef struct {
@@ -250,6 +258,28 @@ int overlap_search(dnasa_ctx *ctx, const uint64_t *packed, const int64_t *toff, 
                    int64_t N, const void *sa, const int32_t *lcp, int idx_width,
                    int32_t min_overlap, dnasa_edge *edges, int64_t cap, int64_t *n_edges,
                    uint8_t *contained, void *stream);
+
+/* ---- overlaps on both strands with errors (Sec. III DEFINITION) ------- */
+
+/* The paper's problem allows each fragment to come from either strand and to
+ * carry a rate mu of errors.  Read here as substitutions (Hamming distance) with
+ * mu = mu_num / mu_den (0 <= mu < 1): oriented fragments are 2r (fragment r) and
+ * 2r + 1 (its reverse complement) when both_strands is 1, else r; (a, b, L) is an
+ * overlap when a and b are different fragments, min_overlap <= L < |a|, |b|, and
+ * the last L bases of a and the first L bases of b differ in at most
+ * floor(L * mu_num / mu_den) places.  The largest L per ordered pair is written,
+ * in (a, b) order, with its mismatch count.  Every such overlap contains a run
+ * of at least L / (e + 1) equal bases (e = allowed mismatches); the runs are
+ * found as LCP intervals of the suffix array of the oriented text (Sec. IV) and
+ * each candidate alignment is verified on packed words.
+ *   text        device, N bytes ('$'-terminated fragments, as for dnasa_pack)
+ *   edges       device, cap entries;  n_edges  host out (also when > cap)
+ *   n_oriented  host out: oriented fragments (2 * fragments or fragments)
+ * Synchronizes the stream.  DNASA_CAPACITY when the edges exceed cap.  Cost:
+ * g^2 seed pairs per position shared by g copies of a repeat. */
+int overlap_search_approx(dnasa_ctx *ctx, const uint8_t *text, int64_t N, int32_t min_overlap,
+                          int32_t mu_num, int32_t mu_den, int32_t both_strands, dnasa_aedge *edges,
+                          int64_t cap, int64_t *n_edges, int64_t *n_oriented, void *stream);
 
 /* ---- whole method on one fragment set (Sec. III, Fig. 3 -> superstring) -- */
 

@@ -21,6 +21,8 @@ Every function follows one passage of the paper (arxiv 1404.3456):
 * :func:`contained`        -- Sec. III, fragments lying inside another fragment.
 * :func:`layout`, :func:`assemble` -- Sec. III, Fig. 3 (path -> superstring) and the
   RS concatenation: greedy unique-overlap layout and spelling.
+* :func:`overlaps_approx` -- Sec. III DEFINITION: overlaps of fragments read on
+  either strand (reverse complements) with at most a rate mu of substitutions.
 * :func:`fir_reconstruct` -- Sec. III, Figs. 2 and 5-8: a sequence cut by two
   shotguns rebuilt from "fir" (prefix) relations by depth-first search with
   back-tracking.
@@ -94,6 +96,8 @@ def _load():
             lib.oracle_contained.restype = ctypes.c_int
             lib.oracle_layout.argtypes = [P, P, I64, P, P, P, I64, P, P, I64, P, I64, P, P]
             lib.oracle_layout.restype = ctypes.c_int
+            lib.oracle_overlaps_approx.argtypes = [P, P, I64, I32, I32, I32, ctypes.c_int, P, P, P, P, I64]
+            lib.oracle_overlaps_approx.restype = I64
             lib.oracle_fir_reconstruct.argtypes = [P, P, I64, I64, P, P, P]
             lib.oracle_fir_reconstruct.restype = I64
             _lib = lib
@@ -320,3 +324,20 @@ def fir_reconstruct(text, max_steps: int = 1 << 40):
             buf[start[r]: start[r] + toff[r + 1] - 1 - toff[r]] = t[toff[r]: toff[r + 1] - 1]
         rs = buf.tobytes()
     return int(st.value), start, rs, int(steps)
+
+
+def overlaps_approx(text, lmin: int, mu_num: int = 0, mu_den: int = 1, rc: bool = False):
+    """Edges (a, b, L, mismatches) between oriented fragments (2r = fragment r,
+    2r + 1 = its reverse complement when rc), the largest L per ordered pair with
+    at most floor(L * mu_num / mu_den) substitutions; (a, b) order."""
+    t = _text(text)
+    toff = read_offsets(t)
+    nr = toff.size - 1
+    f = _load().oracle_overlaps_approx
+    n = f(_ptr(t), _ptr(toff), nr, lmin, mu_num, mu_den, int(rc), None, None, None, None, 0)
+    if n < 0:
+        raise RuntimeError(f"oracle_overlaps_approx failed ({n})")
+    out = [np.empty(max(n, 1), dtype=np.int32) for _ in range(4)]
+    n2 = f(_ptr(t), _ptr(toff), nr, lmin, mu_num, mu_den, int(rc), *(_ptr(o) for o in out), n)
+    assert n2 == n
+    return tuple(o[:n].copy() for o in out)

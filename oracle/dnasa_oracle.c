@@ -37,6 +37,8 @@
  *   oracle_contained        Sec. III: fragments that occur inside another one
  *   oracle_layout           Sec. III (Fig. 3 path -> superstring, RS concatenation):
  *                           greedy unique-overlap layout, then spelling
+ *   oracle_overlaps_approx  Sec. III DEFINITION: overlaps between fragments read on
+ *                           either strand, with at most a rate mu of substitutions
  *   oracle_fir_reconstruct  Sec. III (Figs. 2, 5-8): a sequence cut by two shotguns
  *                           rebuilt from fir relations by depth-first search with
  *                           back-tracking
@@ -637,4 +639,79 @@ int64_t oracle_fir_reconstruct(const uint8_t *T, const int64_t *toff, int64_t nr
     free(used);
     free(F);
     return steps;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. III DEFINITION: fragments may come from either strand and carry      */
+/* errors -- every fragment A must lie within an error rate mu of a piece of */
+/* the result, read directly or as its reverse complement.  The overlap      */
+/* relation under that definition, as this repository reads it:             */
+/*  - errors are substitutions: the distance is the Hamming distance;        */
+/*  - mu is the rational mu_num / mu_den; an overlap of length L may have at */
+/*    most floor(L * mu_num / mu_den) mismatches;                            */
+/*  - with rc != 0 the fragments are oriented: oriented fragment 2r is        */
+/*    fragment r as given and 2r + 1 its reverse complement (A<->T, C<->G,   */
+/*    read backwards); otherwise oriented fragment r is fragment r.          */
+/* Edge set: every ordered pair (a, b) of oriented fragments of different    */
+/* fragments with the largest L, lmin <= L <= min(|a|, |b|) - 1, whose last  */
+/* L symbols of a and first L symbols of b differ in at most the allowed     */
+/* number of places; written in (a, b) order with the mismatch count.        */
+/* Returns the number of edges (only the first cap written), < 0 on error.   */
+/* ------------------------------------------------------------------------ */
+static uint8_t complement(uint8_t c)
+{
+    switch (c) {
+    case 'A': return 'T';
+    case 'C': return 'G';
+    case 'G': return 'C';
+    default: return 'A';
+    }
+}
+
+int64_t oracle_overlaps_approx(const uint8_t *T, const int64_t *toff, int64_t nr, int32_t lmin,
+                               int32_t mu_num, int32_t mu_den, int rc, int32_t *ea, int32_t *eb,
+                               int32_t *eL, int32_t *emm, int64_t cap)
+{
+    if (!reads_ok(T, toff, nr) || lmin < 1 || mu_num < 0 || mu_den < 1 || cap < 0) return -1;
+    const int64_t m = rc ? 2 * nr : nr;
+    /* oriented fragment strings, one after another */
+    int64_t *off = (int64_t *)malloc((size_t)(m + 1) * sizeof(int64_t));
+    uint8_t *S = (uint8_t *)malloc((size_t)(2 * toff[nr] + 1));
+    if (!off || !S) { free(off); free(S); return -3; }
+    int64_t w = 0;
+    for (int64_t a = 0; a < m; ++a) {
+        const int64_t r = rc ? a / 2 : a;
+        const int64_t len = read_len(toff, r);
+        off[a] = w;
+        if (!rc || a % 2 == 0) {
+            memcpy(S + w, T + toff[r], (size_t)len);
+        } else {
+            for (int64_t i = 0; i < len; ++i) S[w + i] = complement(T[toff[r] + len - 1 - i]);
+        }
+        w += len;
+    }
+    off[m] = w;
+    int64_t ne = 0;
+    for (int64_t a = 0; a < m; ++a) {
+        const int64_t la = off[a + 1] - off[a];
+        for (int64_t b = 0; b < m; ++b) {
+            if ((rc ? a / 2 : a) == (rc ? b / 2 : b)) continue;   /* same fragment */
+            const int64_t lb = off[b + 1] - off[b];
+            const int64_t top = (la < lb ? la : lb) - 1;
+            for (int64_t L = top; L >= lmin; --L) {
+                const int64_t allow = (L * (int64_t)mu_num) / mu_den;
+                const uint8_t *x = S + off[a] + la - L, *y = S + off[b];
+                int64_t mm = 0;
+                for (int64_t i = 0; i < L && mm <= allow; ++i) mm += x[i] != y[i];
+                if (mm <= allow) {
+                    if (ne < cap) { ea[ne] = (int32_t)a; eb[ne] = (int32_t)b; eL[ne] = (int32_t)L; emm[ne] = (int32_t)mm; }
+                    ++ne;
+                    break;
+                }
+            }
+        }
+    }
+    free(off);
+    free(S);
+    return ne;
 }

@@ -97,6 +97,8 @@ _SIGS = {
     "dnasa_server_pending": (_INT, [_P]),
     "dnasa_server_job_bytes": (_I64, [_I64, _I64]),
     "dnasa_server_destroy": (None, [_P]),
+    "overlap_search_approx": (_INT, [_P, _P, _I64, _I32, _I32, _I32, _I32, _P, _I64,
+                                     ctypes.POINTER(_I64), ctypes.POINTER(_I64), _P]),
     "fir_reconstruct": (_INT, [_P, _P, _I64, _I64, _P, _I64, _P, _I64, ctypes.POINTER(_I64),
                                ctypes.POINTER(_I32), ctypes.POINTER(_I64), _P]),
     "fir_reconstruct_batched": (_INT, [_P, _P, _P, _I32, _I64, _P, _I64, _P, _I64, _P, _P, _P,
@@ -379,6 +381,26 @@ def assemble_texts_batched(ctx: Context, texts_np, min_overlap: int, opts=None, 
     return [[buf[o[c]: o[c + 1]] for c in range(io[i], io[i + 1])] for i in range(len(texts_np))]
 
 
+def overlap_search_approx(ctx: Context, text: torch.Tensor, min_overlap: int, mu_num: int = 0,
+                          mu_den: int = 1, both_strands: bool = False, cap: int = 0, stream=None):
+    """Overlaps between oriented fragments with at most floor(L * mu) substitutions.
+    Returns (edges int32 tensor (n, 4) of (a, b, L, mismatches), n_oriented)."""
+    n = ctypes.c_int64(0)
+    m = ctypes.c_int64(0)
+    cap = cap or max(1024, 8 * int((text == ord("$")).sum().item()) * (2 if both_strands else 1))
+    for _ in range(2):
+        edges = torch.empty((cap, 4), dtype=torch.int32, device=text.device)
+        rc = lib().overlap_search_approx(ctx.handle, _ptr(text), text.numel(), min_overlap, mu_num, mu_den,
+                                         int(both_strands), _ptr(edges), cap, ctypes.byref(n),
+                                         ctypes.byref(m), _stream(stream))
+        if rc == CAPACITY and n.value > cap:
+            cap = n.value
+            continue
+        ctx.check(rc)
+        break
+    return edges[: n.value], int(m.value)
+
+
 FIR_SOLVED, FIR_NONE, FIR_GAVE_UP = 0, 1, 2   # DNASA_FIR_* in dnasa.h
 
 
@@ -394,6 +416,19 @@ def fir_reconstruct(ctx: Context, text: torch.Tensor, max_steps: int = 1 << 40, 
                                     _ptr(rs), rs.numel(), ctypes.byref(rl), ctypes.byref(st),
                                     ctypes.byref(steps), _stream(stream)))
     return int(st.value), start[:nf], rs[: rl.value].cpu().numpy().tobytes(), int(steps.value)
+
+
+def fir_reconstruct_batched_into(ctx: Context, joined, inst_off, max_steps, start, rs, rs_off,
+                                 status, steps, stream=None) -> int:
+    """fir_reconstruct_batched into caller buffers (device tensors); returns the
+    result bytes of all instances."""
+    total = ctypes.c_int64(0)
+    arr, p = _host_i64(inst_off)
+    ctx.check(lib().fir_reconstruct_batched(ctx.handle, _ptr(joined), p, arr.size - 1, max_steps,
+                                            _ptr(start), start.numel(), _ptr(rs), rs.numel(),
+                                            _ptr(rs_off), _ptr(status), _ptr(steps),
+                                            ctypes.byref(total), _stream(stream)))
+    return int(total.value)
 
 
 def fir_reconstruct_batched(ctx: Context, texts_np, max_steps: int = 1 << 40, stream=None):

@@ -194,8 +194,8 @@ struct FirState {
     int64_t *rs_len;                      // [n_inst]
 };
 
-__device__ __forceinline__ int64_t pairs_lower(const FirState &S, unsigned long long key) {
-    int64_t lo = 0, hi = S.npairs;
+__device__ __forceinline__ int64_t pairs_lower(const FirState &S, unsigned long long key, int64_t lo,
+                                               int64_t hi) {
     while (lo < hi) {
         const int64_t m = (lo + hi) >> 1;
         if (S.pairs[m] < key) lo = m + 1; else hi = m;
@@ -216,6 +216,11 @@ __global__ void k_fir_dfs(TextDesc t, FirState S) {
     const unsigned long long cmask = (1ull << S.kb) - 1ull;
     for (int64_t r = r0; r < r1; ++r) { S.used[r] = 0; S.start[r] = -1; }
     uint2 *F = S.frames + r0;
+    // the instance's pairs: its text positions are [x0, x1), so its pairs are one
+    // run of the sorted list; every later search stays inside it (a few cache lines)
+    const uint64_t x0 = (uint64_t)__ldg(t.toff + r0), x1 = (uint64_t)__ldg(t.toff + r1);
+    const int64_t plo = pairs_lower(S, x0 << S.kb, 0, S.npairs);
+    const int64_t phi = pairs_lower(S, x1 << S.kb, plo, S.npairs);
     int64_t steps = 0;
     int status = 1;
     int64_t rs_len = 0;
@@ -223,8 +228,8 @@ __global__ void k_fir_dfs(TextDesc t, FirState S) {
     for (int64_t k = r0; k < r1 && !done && status != 2; ++k) {
         const int64_t lk = flen(t.toff, k);
         const uint64_t xk = (uint64_t)__ldg(t.toff + k);
-        for (int64_t pi = pairs_lower(S, xk << S.kb);
-             pi < S.npairs && (S.pairs[pi] >> S.kb) == xk && !done && status != 2; ++pi) {
+        for (int64_t pi = pairs_lower(S, xk << S.kb, plo, phi);
+             pi < phi && (S.pairs[pi] >> S.kb) == xk && !done && status != 2; ++pi) {
             const int64_t i = (int64_t)(S.pairs[pi] & cmask);
             const int64_t li = flen(t.toff, i);
             if (i == k || li >= lk) continue;       // start pairs: proper prefixes of d_k
@@ -244,7 +249,7 @@ __global__ void k_fir_dfs(TextDesc t, FirState S) {
                     from = prev + 1;
                     F[top].y = 0u;
                 } else {
-                    from = pairs_lower(S, x << S.kb);
+                    from = pairs_lower(S, x << S.kb, plo, phi);
                 }
                 const int64_t ko = frag_of(t, (int64_t)x);
                 const int64_t o = (int64_t)x - __ldg(t.toff + ko);
@@ -253,7 +258,7 @@ __global__ void k_fir_dfs(TextDesc t, FirState S) {
                 const int64_t nused = 2 + top;
                 int64_t pick = -1, nx = 0;
                 bool last = false;
-                for (int64_t p = from; p < S.npairs && (S.pairs[p] >> S.kb) == x; ++p) {
+                for (int64_t p = from; p < phi && (S.pairs[p] >> S.kb) == x; ++p) {
                     const int64_t c = (int64_t)(S.pairs[p] & cmask);
                     if (S.used[c]) continue;
                     const int64_t lc = flen(t.toff, c);

@@ -108,8 +108,11 @@ __global__ void __launch_bounds__(256) k_lcp(TextDesc t, const uint32_t *__restr
 // predecessor is at least that of p minus one, so along a run of consecutive
 // positions each comparison starts where the previous one ended instead of at
 // base 64.  One thread walks kChain consecutive entries, four words (128 bases)
-// per round trip.
-constexpr int kChain = 128;
+// per round trip.  The walk is a chain of dependent loads, so short chains (many
+// threads in flight) beat the comparisons the bound saves inside a long one: a
+// 16 Mbp genome queued ~1.3 M pairs, which at 128 entries per thread left the GPU
+// 6 % occupied.
+constexpr int kChain = 16;
 
 __global__ void __launch_bounds__(256) k_lcp_chain(TextDesc t, const uint32_t *__restrict__ sa,
                                                    int32_t *__restrict__ lcp,
@@ -248,7 +251,7 @@ int lcp_build_impl(dnasa_ctx *ctx, const TextDesc &t, const uint32_t *sa32, int3
     {
         LaunchScope ls_(ctx, PK_LCP, s, 16.0 * nq);
         int g2 = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(ceil_div(nq, kChain), 128),
-                                                           (int64_t)ctx->num_sms * 32));
+                                                           (int64_t)ctx->num_sms * 64));
         k_lcp_chain<<<g2, 128, 0, s>>>(t, sa32, lcp, qk[which], qv[which], nq);
     }
     DNASA_CUDA(ctx, cudaGetLastError());

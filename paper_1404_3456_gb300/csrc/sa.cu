@@ -39,7 +39,7 @@ constexpr int kInitItems = 8;
 // read the keys once more for them.  Grid-stride over chunks of 32 * kInitItems
 // positions per warp.
 __global__ void __launch_bounds__(kInitThreads) k_init_keys(TextDesc t, int h0, int inst_shift,
-                                                            int pb, int passes, int lo_bit,
+                                                            int pb, int single, int passes, int lo_bit,
                                                             uint32_t *__restrict__ ghist,
                                                             unsigned long long *__restrict__ keys,
                                                             uint32_t *__restrict__ vals) {
@@ -69,7 +69,10 @@ __global__ void __launch_bounds__(kInitThreads) k_init_keys(TextDesc t, int h0, 
             unsigned long long key = ((unsigned long long)kmer << 5) | (unsigned long long)lc;
             if (t.n_inst > 1) key |= (unsigned long long)inst << inst_shift;
             unsigned long long w;
-            if (pb) {
+            if (single) {   // one sequence: bases only, the ended suffixes first (h0_single)
+                const unsigned long long f = lc < h0 ? (unsigned long long)lc : (unsigned long long)(p + h0);
+                w = ((unsigned long long)kmer << pb) | f;
+            } else if (pb) {
                 w = (key << pb) | (unsigned long long)p;
             } else {
                 w = key;
@@ -118,6 +121,7 @@ struct RerankOut {
     uint32_t *bucket_fill;   // [kMaxBuckets]
     int bshift;
     int pb;             // round 0 only: keys hold (key << pb) | position, no value array
+    int single;         // round 0 only: (bases << pb) | f, f as in h0_single
 };
 
 // Shared memory of one rerank tile (dynamic, > 48 KB).  Round 0 needs neither
@@ -173,6 +177,15 @@ __global__ void __launch_bounds__(kRrThreads) k_rerank(
     for (int i = tid; i < tile_n + 2; i += kRrThreads) {
         int64_t j = base - 1 + i;
         unsigned long long w = (j >= 0 && j < n) ? keys[j] : 0ull;
+        if (ROUND0 && o.single) {
+            // bit 0 of the compared key: 0 for an ended suffix (f < h0), which
+            // is its own group, and so is the suffix after it
+            const uint32_t f = (uint32_t)(w & ((1ull << pb) - 1ull));
+            const bool ended = f < (uint32_t)h0;
+            S.u.k[i] = ((w >> pb) << 1) | (ended ? 0ull : 1ull);
+            if (i >= 1 && i <= tile_n) S.v[i - 1] = ended ? (uint32_t)(o.N - 1 - f) : f - (uint32_t)h0;
+            continue;
+        }
         S.u.k[i] = w >> pb;
         if (pb && i >= 1 && i <= tile_n) S.v[i - 1] = (uint32_t)(w & ((1ull << pb) - 1ull));
         if (!ROUND0 && i >= 1 && i <= tile_n) S.oh[i - 1] = (uint32_t)(w >> o.kb);
@@ -186,6 +199,10 @@ __global__ void __launch_bounds__(kRrThreads) k_rerank(
     auto is_head = [&](int64_t j) -> bool {   // j in [base, base + tile_n]
         if (j == 0) return true;
         unsigned long long k = S.u.k[j - base + 1];
+        if (ROUND0 && o.single) {
+            const unsigned long long kp = S.u.k[j - base];
+            return (k & 1ull) == 0 || (kp & 1ull) == 0 || k != kp;   // ended: alone
+        }
         if (ROUND0 && (int)(k & 31ull) < h0) return true;   // own '$' inside: final
         return k != S.u.k[j - base];
     };
@@ -390,6 +407,294 @@ __global__ void __launch_bounds__(kRrThreads) k_rerank(
             o.npos[kp] = pos;
             o.nhead[kp] = hs;
         }
+    }
+}
+
+// ------------------------------------------------------------------ round 0 without a look-back
+// After the initial sort, round 0 needs no cross-tile prefix: every group (equal
+// initial keys) is handled whole by the tile that holds its head.  A tile writes
+// SA for its own slots; for the groups whose heads it holds it writes the ranks
+// (staged by position bucket), and reserves room for their kept members in the
+// active list with one atomic, so each group stays contiguous there (the order
+// of the groups in the list is free: every later step works group by group).
+// A last group that runs past the tile is followed into the next tiles in global
+// memory; a tile with no head leaves its items to the tile of their head.
+constexpr int kR0Threads = 256;
+constexpr int kR0Items = 8;
+constexpr int kR0Tile = kR0Threads * kR0Items;
+
+// Round 0's sorted word -> the key heads are compared on, and the position.
+__device__ __forceinline__ void r0_decode(unsigned long long w, uint32_t val, const RerankOut &o, int h0,
+                                          unsigned long long *key, uint32_t *pos) {
+    if (o.single) {   // bit 0: 0 for an ended suffix (f < h0), which is its own group
+        const uint32_t f = (uint32_t)(w & ((1ull << o.pb) - 1ull));
+        const bool ended = f < (uint32_t)h0;
+        *key = ((w >> o.pb) << 1) | (ended ? 0ull : 1ull);
+        *pos = ended ? (uint32_t)(o.N - 1 - f) : f - (uint32_t)h0;
+    } else if (o.pb) {
+        *key = w >> o.pb;
+        *pos = (uint32_t)(w & ((1ull << o.pb) - 1ull));
+    } else {
+        *key = w;
+        *pos = val;
+    }
+}
+
+// Does the item with compared key k start a group (kp: the key before it)?
+__device__ __forceinline__ bool r0_head(unsigned long long k, unsigned long long kp, const RerankOut &o,
+                                        int h0) {
+    if (o.single) return (k & 1ull) == 0 || (kp & 1ull) == 0 || k != kp;
+    if ((int)(k & 31ull) < h0) return true;   // its own '$' lies inside the key: final
+    return k != kp;
+}
+
+struct R0Smem {
+    unsigned long long k[kR0Tile + 2];   // compared keys, one halo key on each side
+    uint32_t v[kR0Tile];                 // positions
+    uint32_t hb[kR0Tile / 32];           // bit l of word w: item 32w + l starts a group
+    uint32_t nb[kR0Tile / 32];           // ... the item after it starts one (or the data end)
+    int64_t tmp[kR0Threads / 32 + 1];
+    uint32_t bcnt[kMaxBuckets];          // per-bucket counts of a chunk, then global bases
+    int64_t own_end;                     // end of the last group whose head is in the tile
+    unsigned long long kp_base;          // active-list index of the tile's first kept item
+    int first_head;                      // tile-local index of the first head (tile_n: none)
+};
+
+// Stages rank writes (pos -> head slot) of a chunk of items: counts per position
+// bucket in shared memory, one global atomic per bucket, then the writes.
+// Every thread calls; item i of the chunk is (pos[i], head[i]) for i < cnt when
+// take(i) is true.
+template <typename Pos, typename Head, typename Take>
+__device__ __forceinline__ void r0_stage(R0Smem &S, const RerankOut &o, int cnt, Pos pos, Head head,
+                                         Take take, uint32_t *err) {
+    const int nb = (int)((o.N + (1ll << o.bshift) - 1) >> o.bshift);
+    for (int b = threadIdx.x; b < nb; b += kR0Threads) S.bcnt[b] = 0;
+    __syncthreads();
+    uint32_t idx[kR0Items];
+#pragma unroll
+    for (int q = 0; q < kR0Items; ++q) {
+        const int i = threadIdx.x + q * kR0Threads;
+        idx[q] = (i < cnt && take(i)) ? atomicAdd(&S.bcnt[pos(i) >> o.bshift], 1u) : 0u;
+    }
+    __syncthreads();
+    for (int b = threadIdx.x; b < nb; b += kR0Threads) {
+        const uint32_t c = S.bcnt[b];
+        if (c) S.bcnt[b] = atomicAdd(&o.bucket_fill[b], c);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kR0Items; ++q) {
+        const int i = threadIdx.x + q * kR0Threads;
+        if (i >= cnt || !take(i)) continue;
+        const uint32_t p = pos(i);
+        const uint32_t b = p >> o.bshift;
+        const uint64_t st = ((uint64_t)b << o.bshift) + S.bcnt[b] + idx[q];
+        if ((int64_t)p >= o.N || (int64_t)st >= o.N) {
+            atomicOr(err, DERR_BOUNDS);
+            continue;
+        }
+        o.stage[st] = make_uint2(p, head(i));
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kR0Threads) k_rerank0(const unsigned long long *__restrict__ keys,
+                                                        const uint32_t *__restrict__ vals, int64_t n,
+                                                        int h0, RerankOut o, uint32_t *err) {
+    __shared__ R0Smem S;
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int64_t base = (int64_t)blockIdx.x * kR0Tile;
+    if (base >= n) return;
+    const int tile_n = (int)min((int64_t)kR0Tile, n - base);
+
+    // ---- keys (one halo each side) and positions; SA for the tile's own slots
+    for (int i = tid; i < tile_n + 2; i += kR0Threads) {
+        const int64_t j = base - 1 + i;
+        unsigned long long w = 0, key = 0;
+        uint32_t val = 0, pos = 0;
+        if (j >= 0 && j < n) {
+            w = keys[j];
+            if (!o.pb) val = vals[j];
+        }
+        r0_decode(w, val, o, h0, &key, &pos);
+        S.k[i] = key;
+        if (i >= 1 && i <= tile_n) {
+            S.v[i - 1] = pos;
+            if ((int64_t)pos < o.N) o.sa[base + i - 1] = pos;
+            else atomicOr(err, DERR_BOUNDS);
+        }
+    }
+    __syncthreads();
+    // ---- head flags, one ballot per 32 consecutive items
+    for (int b0 = tid - lane; b0 < tile_n; b0 += kR0Threads) {   // warp-uniform
+        const int li = b0 + lane;
+        const int64_t j = base + li;
+        const bool in = li < tile_n;
+        const bool h = in && (j == 0 || r0_head(S.k[li + 1], S.k[li], o, h0));
+        const uint32_t hm = __ballot_sync(0xffffffffu, h);
+        bool nh = false;
+        if (in) {
+            if (j == n - 1) nh = true;
+            else if (lane < 31 && li + 1 < tile_n) nh = ((hm >> (lane + 1)) & 1u) != 0u;
+            else nh = r0_head(S.k[li + 2], S.k[li + 1], o, h0);
+        }
+        const uint32_t nm = __ballot_sync(0xffffffffu, nh);
+        if (lane == 0) {
+            S.hb[b0 >> 5] = hm;
+            S.nb[b0 >> 5] = nm;
+        }
+    }
+    __syncthreads();
+    // ---- first head of the tile; end of its last group (past the tile if needed)
+    if (tid < 32) {
+        int fh = tile_n;
+        for (int w0 = 0; w0 < (tile_n + 31) / 32; w0 += 32) {
+            const int w = w0 + lane;
+            const uint32_t hm = w < (tile_n + 31) / 32 ? S.hb[w] : 0u;
+            const uint32_t any = __ballot_sync(0xffffffffu, hm != 0u);
+            if (any) {
+                const int wl = __ffs(any) - 1;
+                const uint32_t hw = __shfl_sync(0xffffffffu, hm, wl);
+                fh = (w0 + wl) * 32 + __ffs(hw) - 1;
+                break;
+            }
+        }
+        int64_t end = base + tile_n;
+        const int last = tile_n - 1;
+        const bool closed = (S.nb[last >> 5] >> (last & 31)) & 1u;
+        if (fh < tile_n && !closed) {
+            // follow the last group into the next tiles: 32 keys per probe
+            unsigned long long prev = S.k[tile_n];   // key of the tile's last item
+            for (int64_t j0 = base + tile_n;; j0 += 32) {
+                const int64_t j = j0 + lane;
+                unsigned long long key = 0;
+                uint32_t pos;
+                if (j < n) r0_decode(keys[j], o.pb ? 0u : vals[j], o, h0, &key, &pos);
+                unsigned long long kprev = __shfl_up_sync(0xffffffffu, key, 1);
+                if (lane == 0) kprev = prev;
+                const bool stop = j >= n || r0_head(key, kprev, o, h0);
+                const uint32_t sm = __ballot_sync(0xffffffffu, stop);
+                if (sm) {
+                    end = j0 + __ffs(sm) - 1;
+                    break;
+                }
+                prev = __shfl_sync(0xffffffffu, key, 31);
+            }
+        }
+        if (lane == 0) {
+            S.first_head = fh;
+            S.own_end = end;
+        }
+    }
+    __syncthreads();
+    const int fh = S.first_head;
+    if (fh >= tile_n) return;   // every item belongs to a group whose head is in an earlier tile
+    const int64_t spill = S.own_end - (base + tile_n);
+
+    // ---- blocked: head slot and kept index of every owned item
+    static_assert(kR0Items == 8, "a thread's items are one byte of a flag word");
+    const int sh = (tid * kR0Items) & 31;
+    uint32_t vm = tid * kR0Items >= tile_n ? 0u : (1u << min(kR0Items, tile_n - tid * kR0Items)) - 1u;
+    {   // items before the first head belong to an earlier tile
+        const int lo = fh - tid * kR0Items;
+        if (lo > 0) vm &= lo >= kR0Items ? 0u : ~((1u << lo) - 1u);
+    }
+    const uint32_t headbits = (S.hb[(tid * kR0Items) >> 5] >> sh) & vm;
+    const uint32_t lastbits = (S.nb[(tid * kR0Items) >> 5] >> sh) & vm;
+    const uint32_t keepbits = ~(headbits & lastbits) & vm;
+    const int64_t my_max = headbits ? base + tid * kR0Items + 31 - __clz(headbits) : -1;
+    int64_t tile_max, tile_keep;
+    const int64_t inc_max = block_inclusive_max<kR0Threads>(my_max, S.tmp, &tile_max, (int64_t)-1);
+    const int64_t ex_max = __shfl_up_sync(0xffffffffu, inc_max, 1);
+    const int64_t ex_keep = block_exclusive_sum<kR0Threads>((int64_t)__popc(keepbits), S.tmp, &tile_keep);
+    if (tid == 0) S.kp_base = atomicAdd(o.kept, (unsigned long long)(tile_keep + spill));
+    // exclusive max over threads: the lane before in this warp, or the warps before
+    int64_t cur;
+    {
+        const int w = tid >> 5;
+        __syncthreads();
+        if (lane == 31) S.tmp[w] = inc_max;
+        __syncthreads();
+        int64_t before = -1;
+        for (int x = 0; x < w; ++x) before = max(before, S.tmp[x]);
+        cur = lane > 0 ? max(before, ex_max) : before;
+    }
+    __syncthreads();
+    const unsigned long long kp0 = S.kp_base;
+    {
+        uint32_t gend = keepbits & lastbits;
+        const uint32_t ng = __popc(gend);
+        uint32_t ng_inc = ng;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, ng_inc, off);
+            if (lane >= off) ng_inc += y;
+        }
+        unsigned long long gbase = 0;
+        if (lane == 31 && ng_inc) gbase = atomicAdd(o.ngroups, (unsigned long long)ng_inc);
+        gbase = __shfl_sync(0xffffffffu, gbase, 31) + (ng_inc - ng);
+        uint32_t my_maxsize = 0;
+        unsigned long long kp = kp0 + (unsigned long long)ex_keep;
+#pragma unroll
+        for (int i = 0; i < kR0Items; ++i) {
+            const int li = tid * kR0Items + i;
+            if (!((vm >> i) & 1u)) continue;
+            const int64_t j = base + li;
+            if ((headbits >> i) & 1u) cur = j;
+            S.k[li] = (unsigned long long)cur;        // keys are done with: head slot of item li
+            if ((keepbits >> i) & 1u) {
+                if (kp >= (unsigned long long)n) {
+                    atomicOr(err, DERR_BOUNDS);
+                } else {
+                    o.nslots[kp] = (uint32_t)j;
+                    o.npos[kp] = S.v[li];
+                    o.nhead[kp] = (uint32_t)cur;
+                }
+                if ((lastbits >> i) & 1u) {
+                    const uint32_t size = (uint32_t)(j - cur + 1);
+                    o.groups[gbase++] = make_uint2((uint32_t)(kp - size + 1), size);
+                    my_maxsize = max(my_maxsize, size);
+                }
+                ++kp;
+            }
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1)
+            my_maxsize = max(my_maxsize, __shfl_xor_sync(0xffffffffu, my_maxsize, off));
+        if (lane == 0 && my_maxsize) atomicMax(o.maxgroup, (unsigned long long)my_maxsize);
+    }
+    __syncthreads();
+    // ---- ranks of the owned items in the tile
+    r0_stage(S, o, tile_n, [&](int i) { return S.v[i]; }, [&](int i) { return (uint32_t)S.k[i]; },
+             [&](int i) { return i >= fh; }, err);
+    if (spill <= 0) return;
+    // ---- the last group continues past the tile: all of it kept, one head
+    const uint32_t head = (uint32_t)tile_max;
+    const unsigned long long kps = kp0 + (unsigned long long)tile_keep;
+    for (int64_t c0 = base + tile_n; c0 < S.own_end; c0 += kR0Tile) {
+        const int cnt = (int)min((int64_t)kR0Tile, S.own_end - c0);
+        for (int i = tid; i < cnt; i += kR0Threads) {
+            unsigned long long key;
+            uint32_t pos;
+            r0_decode(keys[c0 + i], o.pb ? 0u : vals[c0 + i], o, h0, &key, &pos);
+            S.v[i] = pos;
+            const unsigned long long kp = kps + (unsigned long long)(c0 - base - tile_n + i);
+            if (kp >= (unsigned long long)n || (int64_t)pos >= o.N) {
+                atomicOr(err, DERR_BOUNDS);
+                continue;
+            }
+            o.nslots[kp] = (uint32_t)(c0 + i);
+            o.npos[kp] = pos;
+            o.nhead[kp] = head;
+        }
+        __syncthreads();
+        r0_stage(S, o, cnt, [&](int i) { return S.v[i]; }, [&](int) { return head; },
+                 [&](int) { return true; }, err);
+    }
+    if (tid == 0) {
+        const uint32_t size = (uint32_t)(S.own_end - (int64_t)head);
+        o.groups[atomicAdd(o.ngroups, 1ull)] = make_uint2((uint32_t)(kp0 + tile_keep + spill - size), size);
+        atomicMax(o.maxgroup, (unsigned long long)size);
     }
 }
 
@@ -951,6 +1256,25 @@ __global__ void k_widen(const uint32_t *__restrict__ a, int64_t n, int64_t *__re
 // unsorted (4^h0 >= 32 * symbols per instance: expected colliding pairs at most
 // N/64), then as many as fit in the same number of 8-bit passes: the key is
 // [instance | 2*h0 bits of bases | 5 bits of lc], and its passes are the cost.
+// A single sequence (one fragment, one instance) has only h0 suffixes that reach
+// its '$' within h0 symbols, so the initial word can drop the bases-left field:
+// word = (2*h0 bits of bases << pb) | f with f = bases left (0..h0-1) for those
+// few "ended" suffixes and f = position + h0 for every other one.  Among equal
+// bases the ended suffixes then come first, shorter first, as their '$' makes
+// them smaller, and the rest by position; f < N, so pb = bits of N - 1.  The
+// key is 5 bits shorter: one 8-bit pass fewer for a 16-base key.  Returns 0 when
+// no packed word holds a key of at least the collision bound.
+int h0_single(int64_t N, int *pack_bits) {
+    int hmin = (int)std::ceil((std::log2(std::max((double)N, 2.0)) + 5.0) / 2.0);
+    hmin = std::max(8, std::min(hmin, 29));
+    const int passes = (2 * hmin + 7) / 8;
+    const int pb = bits_for((uint64_t)(N - 1));
+    const int h0 = std::min(std::min(4 * passes, 29), (64 - pb) / 2);
+    if (h0 < hmin) return 0;
+    *pack_bits = pb;
+    return h0;
+}
+
 int h0_for(int64_t N, int n_inst, int *inst_bits, int *pack_bits) {
     int ib = n_inst > 1 ? bits_for((uint64_t)(n_inst - 1)) : 0;
     *inst_bits = ib;
@@ -992,7 +1316,7 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
     if (opts_in) opts = *opts_in;
     const int tile_items = opts.tile_items ? opts.tile_items : radix_tile_default();
     const int64_t finish_threshold =
-        opts.finish_threshold == 0 ? (int64_t)1 << 20 : opts.finish_threshold;
+        opts.finish_threshold == 0 ? (int64_t)-1 : opts.finish_threshold;   // default: never
     const int max_rounds = opts.max_rounds > 0 ? std::min(opts.max_rounds, 63) : 63;
     const int lbw = opts.lookback == 1 ? 1 : 8;
     // largest group a doubling round sorts on chip (larger ones: radix passes)
@@ -1004,8 +1328,20 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
         pb = 0;
         h0 = h0_for(N, t.n_inst, &ib, nullptr);
     }
+    // one sequence: the shorter key without the bases-left field (h0_single)
+    bool single = false;
+    if (t.n_reads == 1 && t.n_inst <= 1 && opts.pack_position >= 0) {
+        int pbs = 0;
+        const int hs = h0_single(N, &pbs);
+        if (hs > 0) {
+            single = true;
+            h0 = hs;
+            pb = pbs;
+            ib = 0;
+        }
+    }
     const int inst_shift = 2 * h0 + 5;
-    const int key_bits0 = inst_shift + ib;
+    const int key_bits0 = single ? 2 * h0 : inst_shift + ib;
     const int b = bits_for((uint64_t)(N - 1));
 
     // ---- workspace
@@ -1034,7 +1370,6 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
     if (!rs.hist || !rr_status) return fail(ctx, DNASA_OOM, "sa_build workspace");
 
     // dynamic shared-memory limits of this call's kernels, once per (kernel, device)
-    DNASA_CUDA(ctx, smem_attr(k_rerank<true>, sizeof(RerankSmem<true>)));
     DNASA_CUDA(ctx, smem_attr(k_rerank<false>, sizeof(RerankSmem<false>)));
     DNASA_CUDA(ctx, smem_attr(k_seg_radix<4>, seg_radix_smem<4>()));
     DNASA_CUDA(ctx, smem_attr(k_seg_radix<12>, seg_radix_smem<12>()));
@@ -1086,6 +1421,7 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
     ro.bshift = bshift;
     ro.kb = b;
     ro.pb = pb;
+    ro.single = single ? 1 : 0;
 
     // ---- round 0: initial keys, sort, rerank
     {
@@ -1096,7 +1432,8 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
             const int warps = ceil_div(N, 32 * kInitItems);
             const int grid = (int)std::min<int64_t>(ceil_div(warps, kInitThreads / 32),
                                                     (int64_t)ctx->num_sms * 8);
-            k_init_keys<<<std::max(grid, 1), kInitThreads, 0, s>>>(t, h0, inst_shift, pb, passes0, pb,
+            k_init_keys<<<std::max(grid, 1), kInitThreads, 0, s>>>(t, h0, inst_shift, pb, single ? 1 : 0,
+                                                                   passes0, pb,
                                                                    rs.hist, keys[0], vals[0]);
         }
         DNASA_CUDA(ctx, cudaGetLastError());
@@ -1109,8 +1446,7 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
         ro.stage = reinterpret_cast<uint2 *>(keys[which ^ 1]);   // the free key buffer
         {
             LaunchScope ls_(ctx, PK_RERANK, s, 20.0 * N);
-            k_rerank<true><<<rr_tiles, kRrThreads, sizeof(RerankSmem<true>), s>>>(keys[which], vals[which], nullptr, N, nullptr,
-                                                           h0, ro, rr_status, c->tile_ctr + 32, &c->err);
+            k_rerank0<<<ceil_div(N, kR0Tile), kR0Threads, 0, s>>>(keys[which], vals[which], N, h0, ro, &c->err);
         }
         DNASA_CUDA(ctx, cudaGetLastError());
         DNASA_TRY(apply_ranks(N, which ^ 1));

@@ -182,6 +182,27 @@ def test_sa_int64(ctx):
     assert np.array_equal(sa.cpu().numpy(), oracle.suffix_array(t))
 
 
+@pytest.mark.parametrize("seed", range(6))
+def test_sa_single_sequence_endings(ctx, seed):
+    """One sequence: its last h0 suffixes reach the '$' inside the initial key and
+    sort before every suffix that shares their bases (shorter first).  Endings made
+    of A's (whose bases equal the zero padding), runs of one base, periodic tails
+    and random lengths around the key and tile sizes."""
+    rng = np.random.default_rng(400 + seed)
+    A = np.frombuffer(b"ACGT", np.uint8)
+    cases = [np.full(int(rng.integers(1, 40)), ord("A"), np.uint8),
+             np.concatenate([A[rng.integers(0, 4, int(rng.integers(1, 3000)))],
+                             np.full(int(rng.integers(1, 40)), ord("A"), np.uint8)]),
+             np.tile(A[rng.integers(0, 4, int(rng.integers(1, 5)))], int(rng.integers(1, 400))),
+             A[rng.integers(0, 4, int(rng.integers(1, 20)))],
+             np.concatenate([np.tile(np.frombuffer(b"CA", np.uint8), 2000),
+                             A[rng.integers(0, 4, int(rng.integers(0, 17)))]])]
+    for g in cases:
+        t = synth.genome_text(g)
+        sa = gpu_sa(ctx, t)[0]
+        assert np.array_equal(sa.cpu().numpy().astype(np.int64), oracle.suffix_array(t)), g[-40:].tobytes()
+
+
 def test_sa_all_same_base(ctx):
     t = synth.genome_text(np.full(50_000, ord("A"), np.uint8))
     sa = gpu_sa(ctx, t)[0]
