@@ -61,7 +61,9 @@ def parse():
     ap.add_argument("--instances", type=int, default=4096, help="batched: fragment sets per batch")
     ap.add_argument("--solo-sample", type=int, default=256,
                     help="batched: instances timed one job per launch")
-    ap.add_argument("--jobs", type=int, default=48, help="served: distinct jobs in the trace")
+    ap.add_argument("--jobs", type=int, default=48, help="served: jobs in the trace")
+    ap.add_argument("--distinct", type=int, default=0,
+                    help="served: distinct generated jobs the trace cycles through (0 = all distinct)")
     ap.add_argument("--lambdas", default="0.25,0.5,0.75,0.9,1.0,1.25",
                     help="served: arrival rates as multiples of one-job-per-launch capacity")
     ap.add_argument("--no-tune", action="store_true", help="skip the build-option autotuner")
@@ -237,6 +239,25 @@ def pctl(xs, q):
 
 
 ROOF_TIMING = "per-launch CUDA events on the launching stream, second pass of the same K steps"
+
+
+def traffic_ratio(kind: str):
+    """DRAM bytes (ncu dram__bytes_read + write) per algorithmic byte of a kernel
+    class, from profiles/traffic.json -- only while the class's kernel source is the
+    one the counters were taken on (sha1 pinned there), else None."""
+    import hashlib
+
+    tfile = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        tj = json.load(open(tfile)).get(kind)
+        if not tj or not tj.get("valid"):
+            return None
+        src = os.path.join(ROOT, tj["source"])
+        if hashlib.sha1(open(src, "rb").read()).hexdigest() != tj["source_sha1"]:
+            return None
+        return float(tj["dram_per_algorithmic_byte"])
+    except Exception:
+        return None
 
 
 def roofline_of(prof, peak, peak_src, steps):
@@ -714,9 +735,12 @@ def run_served(args):
 
     rank, local_rank, world = dist_env()
     torch.cuda.set_device(local_rank)
-    jobs = [synth.served_job(args.seed + 1000 * rank, i) for i in range(args.jobs)]
+    n_pool = args.distinct if 0 < args.distinct < args.jobs else args.jobs
+    pool = [synth.served_job(args.seed + 1000 * rank, i) for i in range(n_pool)]
+    pool_pinned = [torch.from_numpy(j["text"]).pin_memory() for j in pool]
+    jobs = [pool[i % n_pool] for i in range(args.jobs)]          # the trace's jobs
+    pinned = [pool_pinned[i % n_pool] for i in range(args.jobs)]
     ctx = binding.Context(local_rank)
-    pinned = [torch.from_numpy(j["text"]).pin_memory() for j in jobs]
 
     def solo(i):  # one job per launch: upload, assemble, contigs back
         t = pinned[i].cuda(non_blocking=True)
@@ -725,10 +749,10 @@ def run_served(args):
     for i in range(min(3, len(jobs))):
         solo(i)
     t0 = time.perf_counter()
-    for i in range(len(jobs)):
+    for i in range(n_pool):   # capacity: every distinct job once
         solo(i)
     cap_s = time.perf_counter() - t0
-    capacity = len(jobs) / cap_s
+    capacity = n_pool / cap_s
     rng = np.random.default_rng(args.seed)
     results = []
     srv = binding.Server(local_rank, slots=args.slots, max_batch=args.max_batch)
@@ -780,9 +804,12 @@ def run_served(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8/int32",
         "data": "synthetic",
         "config": {"workload": f"served: {len(jobs)} jobs (genome log-uniform 5 kbp-5 Mbp, 2% tandem, "
-                               "150 bp reads at 10x, min overlap 41), Poisson arrivals",
+                               "150 bp reads at 10x, min overlap 41), Poisson arrivals"
+                               + (f"; the trace cycles through {n_pool} distinct generated jobs"
+                                  if n_pool < len(jobs) else ""),
                    "one_job_per_launch_capacity_jobs_per_s": capacity,
                    "mean_job_symbols": float(np.mean([j["text"].size for j in jobs])),
+                   "distinct_jobs": n_pool,
                    "slots": args.slots, "max_batch": args.max_batch, "sweep": results},
         "e2e": {"value": top["served"]["jobs_per_s"], "unit": "jobs/s",
                 "h2d_bytes_per_step": float(np.mean([j["text"].size for j in jobs])),
@@ -944,20 +971,8 @@ def main():
     if dom:
         name, d = dom
         achieved = d["bytes"] / (d["ms"] / 1000.0) / 1e9
-        traffic = None
-        tfile = os.path.join(ROOT, "profiles", "traffic.json")
-        if os.path.exists(tfile):
-            try:
-                import hashlib
-
-                tj = json.load(open(tfile)).get(name)
-                src = os.path.join(ROOT, tj["source"]) if tj else None
-                if tj and tj.get("valid") and src and os.path.exists(src):
-                    # the counters hold only while the kernel source is the captured one
-                    if hashlib.sha1(open(src, "rb").read()).hexdigest() == tj["source_sha1"]:
-                        traffic = tj["dram_per_algorithmic_byte"] * d["bytes"] / d["launches"]
-            except Exception:
-                traffic = None
+        ratio = traffic_ratio(name)
+        traffic = ratio * d["bytes"] / d["launches"] if ratio is not None else None
         all_bytes = sum(v["bytes"] for v in prof.values())
         all_ms = sum(v["ms"] for v in prof.values())
         roofline = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak,
@@ -967,7 +982,9 @@ def main():
                     "algorithmic_bytes_per_launch": d["bytes"] / d["launches"],
                     "avg_launch_ms": d["ms"] / d["launches"], "timing": ROOF_TIMING}
     breakdown = {k: {"launches": v["launches"], "ms_per_step": v["ms"] / args.steps,
-                     "share": v["ms"] / max(1e-9, sum(x["ms"] for x in prof.values()))}
+                     "share": v["ms"] / max(1e-9, sum(x["ms"] for x in prof.values())),
+                     "algorithmic_gbs": v["bytes"] / (v["ms"] / 1000.0) / 1e9 if v["ms"] else None,
+                     "dram_per_algorithmic_byte": traffic_ratio(k)}
                  for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])}
     cpu = None
     if not args.no_cpu_baseline and world == 1:   # the oracle's baseline: rank 0 at N = 1 only

@@ -68,7 +68,11 @@ typedef struct dnasa_ctx dnasa_ctx;
 
 /* Options of the suffix-array build.  Zero in any field selects the default. */
 typedef struct {
-    int32_t digit_bits;        /* radix digit width of the LSD passes: 8 (default; the only one) */
+    int32_t reserved0;         /* must be 0.  The radix digit is fixed at 8 bits: a onesweep
+                                  pass keeps one look-back word per digit and tile, so a
+                                  wider digit multiplies that traffic and the per-tile scans
+                                  while saving at most one pass of the initial sort (for
+                                  which the key is already cut to whole bytes) */
     int32_t tile_items;        /* items per onesweep tile: 3840 (default), 2048 or 5120 */
     int64_t finish_threshold;  /* when the suffixes still unsorted after a doubling round
                                   number at most this many, and every unsorted group has at
@@ -86,6 +90,15 @@ typedef struct {
                                   the key and sorts one 64-bit word per suffix when the
                                   key can still hold enough symbols; -1 never packs and
                                   sorts (key, position) pairs */
+    int32_t builder;           /* 0 (default): prefix doubling as described at sa_build;
+                                  1: the difference-cover (DC3, skew) algorithm of
+                                  Kaerkkaeinen and Sanders, after which the paper names its
+                                  GPU kernel (Sec. IV) -- sample positions i mod 3 != 0
+                                  radix sorted by triples and named, recursion while names
+                                  repeat, then the mod-0 positions by (symbol, rank of
+                                  i+1) and a merge; same suffix array; one instance only
+                                  (sa_build_batched refuses it); the other options are
+                                  ignored */
 } dnasa_opts;
 
 /* One suffix-prefix overlap: the last L bases of fragment j equal the first L

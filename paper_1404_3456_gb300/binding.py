@@ -31,10 +31,10 @@ class DnasaError(RuntimeError):
 
 
 class Opts(ctypes.Structure):
-    _fields_ = [("digit_bits", ctypes.c_int32), ("tile_items", ctypes.c_int32),
+    _fields_ = [("reserved0", ctypes.c_int32), ("tile_items", ctypes.c_int32),
                 ("finish_threshold", ctypes.c_int64), ("max_rounds", ctypes.c_int32),
                 ("lookback", ctypes.c_int32), ("seg_max", ctypes.c_int32),
-                ("pack_position", ctypes.c_int32)]
+                ("pack_position", ctypes.c_int32), ("builder", ctypes.c_int32)]
 
 
 class Trace(ctypes.Structure):
@@ -198,10 +198,10 @@ class Context:
             pass
 
 
-def make_opts(digit_bits=0, tile_items=0, finish_threshold=0, max_rounds=0, lookback=0, seg_max=0,
-              pack_position=0):
-    return Opts(digit_bits, tile_items, finish_threshold, max_rounds, lookback, seg_max,
-                pack_position)
+def make_opts(reserved0=0, tile_items=0, finish_threshold=0, max_rounds=0, lookback=0, seg_max=0,
+              pack_position=0, builder=0):
+    return Opts(reserved0, tile_items, finish_threshold, max_rounds, lookback, seg_max,
+                pack_position, builder)
 
 
 # ---------------------------------------------------------------- entry points

@@ -208,14 +208,16 @@ int sa_build(dnasa_ctx *ctx, const uint64_t *packed, const int64_t *toff, int64_
     if (opts && (opts->tile_items != 0 && opts->tile_items != 2048 && opts->tile_items != 3840 &&
                  opts->tile_items != 5120))
         return fail(ctx, DNASA_INVALID_ARG, "sa_build: tile_items must be 0, 2048, 3840 or 5120");
-    if (opts && opts->digit_bits != 0 && opts->digit_bits != 8)
-        return fail(ctx, DNASA_INVALID_ARG, "sa_build: digit_bits must be 0 or 8");
+    if (opts && opts->reserved0 != 0)
+        return fail(ctx, DNASA_INVALID_ARG, "sa_build: reserved0 must be 0");
     if (opts && opts->lookback != 0 && opts->lookback != 1 && opts->lookback != 8)
         return fail(ctx, DNASA_INVALID_ARG, "sa_build: lookback must be 0, 1 or 8");
     if (opts && opts->seg_max != 0 && (opts->seg_max < 8 || opts->seg_max > 12288))
         return fail(ctx, DNASA_INVALID_ARG, "sa_build: seg_max must be 0 or in [8, 12288]");
     if (opts && opts->pack_position != 0 && opts->pack_position != -1)
         return fail(ctx, DNASA_INVALID_ARG, "sa_build: pack_position must be 0 or -1");
+    if (opts && opts->builder != 0 && opts->builder != 1)
+        return fail(ctx, DNASA_INVALID_ARG, "sa_build: builder must be 0 (doubling) or 1 (DC3)");
     cudaSetDevice(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
     TextDesc t = one_instance(packed, toff, n_reads, N);

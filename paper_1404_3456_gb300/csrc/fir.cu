@@ -183,6 +183,7 @@ __global__ void __launch_bounds__(256) k_fir_query(TextDesc t, FirIndex fi) {
 
 struct FirState {
     const unsigned long long *pairs;      // sorted (x << kb) | c
+    const uint32_t *xoff;                 // [N + 1]: pairs of position x are [xoff[x], xoff[x+1])
     int64_t npairs;
     int kb;
     int64_t max_steps;
@@ -194,13 +195,18 @@ struct FirState {
     int64_t *rs_len;                      // [n_inst]
 };
 
-__device__ __forceinline__ int64_t pairs_lower(const FirState &S, unsigned long long key, int64_t lo,
-                                               int64_t hi) {
-    while (lo < hi) {
-        const int64_t m = (lo + hi) >> 1;
-        if (S.pairs[m] < key) lo = m + 1; else hi = m;
+
+// xoff[x] = first pair of position x (pairs sorted by x): each pair that starts a
+// run of its position fills the offsets of the positions since the previous run.
+__global__ void k_fir_xoff(const unsigned long long *__restrict__ pairs, int64_t np, int kb, int64_t N,
+                           uint32_t *__restrict__ xoff) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p <= np;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t x = p < np ? (int64_t)(pairs[p] >> kb) : N;
+        const int64_t xp = p > 0 ? (int64_t)(pairs[p - 1] >> kb) : -1;
+        if (p < np && x == xp) continue;
+        for (int64_t y = xp + 1; y <= x; ++y) xoff[y] = (uint32_t)p;
     }
-    return lo;
 }
 
 // Depth-first search of one instance (one thread per instance).  Frame f holds
@@ -216,11 +222,6 @@ __global__ void k_fir_dfs(TextDesc t, FirState S) {
     const unsigned long long cmask = (1ull << S.kb) - 1ull;
     for (int64_t r = r0; r < r1; ++r) { S.used[r] = 0; S.start[r] = -1; }
     uint2 *F = S.frames + r0;
-    // the instance's pairs: its text positions are [x0, x1), so its pairs are one
-    // run of the sorted list; every later search stays inside it (a few cache lines)
-    const uint64_t x0 = (uint64_t)__ldg(t.toff + r0), x1 = (uint64_t)__ldg(t.toff + r1);
-    const int64_t plo = pairs_lower(S, x0 << S.kb, 0, S.npairs);
-    const int64_t phi = pairs_lower(S, x1 << S.kb, plo, S.npairs);
     int64_t steps = 0;
     int status = 1;
     int64_t rs_len = 0;
@@ -228,8 +229,8 @@ __global__ void k_fir_dfs(TextDesc t, FirState S) {
     for (int64_t k = r0; k < r1 && !done && status != 2; ++k) {
         const int64_t lk = flen(t.toff, k);
         const uint64_t xk = (uint64_t)__ldg(t.toff + k);
-        for (int64_t pi = pairs_lower(S, xk << S.kb, plo, phi);
-             pi < phi && (S.pairs[pi] >> S.kb) == xk && !done && status != 2; ++pi) {
+        const int64_t pe = (int64_t)__ldg(S.xoff + xk + 1);
+        for (int64_t pi = (int64_t)__ldg(S.xoff + xk); pi < pe && !done && status != 2; ++pi) {
             const int64_t i = (int64_t)(S.pairs[pi] & cmask);
             const int64_t li = flen(t.toff, i);
             if (i == k || li >= lk) continue;       // start pairs: proper prefixes of d_k
@@ -249,7 +250,7 @@ __global__ void k_fir_dfs(TextDesc t, FirState S) {
                     from = prev + 1;
                     F[top].y = 0u;
                 } else {
-                    from = pairs_lower(S, x << S.kb, plo, phi);
+                    from = (int64_t)__ldg(S.xoff + x);
                 }
                 const int64_t ko = frag_of(t, (int64_t)x);
                 const int64_t o = (int64_t)x - __ldg(t.toff + ko);
@@ -258,7 +259,8 @@ __global__ void k_fir_dfs(TextDesc t, FirState S) {
                 const int64_t nused = 2 + top;
                 int64_t pick = -1, nx = 0;
                 bool last = false;
-                for (int64_t p = from; p < phi && (S.pairs[p] >> S.kb) == x; ++p) {
+                const int64_t to = (int64_t)__ldg(S.xoff + x + 1);
+                for (int64_t p = from; p < to; ++p) {
                     const int64_t c = (int64_t)(S.pairs[p] & cmask);
                     if (S.used[c]) continue;
                     const int64_t lc = flen(t.toff, c);
@@ -445,8 +447,18 @@ int fir_impl(dnasa_ctx *ctx, const uint8_t *text, int64_t N, const int64_t *inst
             DNASA_TRY(radix_sort_pairs<unsigned long long>(ctx, rs2, pk, nov, np, nullptr, kb + xb, false,
                                                            tile, &which2, s));
         }
+        DevBuf xoffb;
+        DNASA_TRY(dev_alloc(ctx, xoffb, (size_t)(N + 1) * 4, s));
+        if (np == 0) {
+            DNASA_CUDA(ctx, cudaMemsetAsync(xoffb.p, 0, (size_t)(N + 1) * 4, s));
+        } else {
+            LaunchScope ls_(ctx, PK_OVERLAP, s, 4.0 * (N + 1) + 16.0 * np);
+            k_fir_xoff<<<grid_for(ctx, np + 1), 256, 0, s>>>(pk[which2], np, kb, N, (uint32_t *)xoffb.p);
+        }
+        DNASA_CUDA(ctx, cudaGetLastError());
         FirState S;
         S.pairs = pk[which2];
+        S.xoff = (const uint32_t *)xoffb.p;
         S.npairs = np;
         S.kb = kb;
         S.max_steps = max_steps;

@@ -69,16 +69,21 @@ __global__ void __launch_bounds__(kInitThreads) k_init_keys(TextDesc t, int h0, 
             unsigned long long key = ((unsigned long long)kmer << 5) | (unsigned long long)lc;
             if (t.n_inst > 1) key |= (unsigned long long)inst << inst_shift;
             unsigned long long w;
-            if (single) {   // one sequence: bases only, the ended suffixes first (h0_single)
+            int64_t at = p;
+            if (single) {
+                // one sequence: bases only, and the word stored at index f (h0_single):
+                // the sort orders key bits only and keeps equal keys in input order,
+                // which is then f order -- ended suffixes first, shorter first
                 const unsigned long long f = lc < h0 ? (unsigned long long)lc : (unsigned long long)(p + h0);
                 w = ((unsigned long long)kmer << pb) | f;
+                at = (int64_t)f;
             } else if (pb) {
                 w = (key << pb) | (unsigned long long)p;
             } else {
                 w = key;
                 vals[p] = (uint32_t)p;
             }
-            keys[p] = w;
+            keys[at] = w;
             for (int q = 0; q < passes; ++q)
                 atomicAdd(&sh[q * 256 + (uint32_t)((w >> (lo_bit + 8 * q)) & 255ull)], 1u);
         }
@@ -124,9 +129,7 @@ struct RerankOut {
     int single;         // round 0 only: (bases << pb) | f, f as in h0_single
 };
 
-// Shared memory of one rerank tile (dynamic, > 48 KB).  Round 0 needs neither
-// the slots (slot = item index) nor the old head ranks.
-template <bool ROUND0>
+// Shared memory of one rerank tile of a doubling round (dynamic, > 48 KB).
 struct RerankSmem {
     union {
         unsigned long long k[kRrTile + 2];   // keys with one halo key on each side
@@ -138,8 +141,8 @@ struct RerankSmem {
         } o;
     } u;
     uint32_t v[kRrTile];                 // positions
-    uint32_t sl[ROUND0 ? 1 : kRrTile];   // slots (rounds >= 1)
-    uint32_t oh[ROUND0 ? 1 : kRrTile];   // old head rank (rounds >= 1)
+    uint32_t sl[kRrTile];                // SA slots
+    uint32_t oh[kRrTile];                // old head rank
     uint32_t hb[kRrTile / 32];           // bit l of word w: item 32w + l starts a group
     uint32_t nb[kRrTile / 32];           // ... the item after it starts one (or the data end)
     int64_t tmp[kRrThreads / 32 + 1];
@@ -153,13 +156,12 @@ struct RerankSmem {
     int stop;
 };
 
-template <bool ROUND0>
 __global__ void __launch_bounds__(kRrThreads) k_rerank(
     const unsigned long long *__restrict__ keys, const uint32_t *__restrict__ vals,
     const uint32_t *__restrict__ slots, int64_t n_host, const unsigned long long *__restrict__ d_n,
     int h0, RerankOut o, unsigned long long *status, uint32_t *tile_ctr, uint32_t *err) {
     extern __shared__ __align__(16) unsigned char rr_raw[];
-    RerankSmem<ROUND0> &S = *reinterpret_cast<RerankSmem<ROUND0> *>(rr_raw);
+    RerankSmem &S = *reinterpret_cast<RerankSmem *>(rr_raw);
     const int tid = threadIdx.x;
     if (tid == 0) {
         S.tile = atomicAdd(tile_ctr, 1u);
@@ -173,38 +175,21 @@ __global__ void __launch_bounds__(kRrThreads) k_rerank(
     const int tile_n = (int)min((int64_t)kRrTile, n - base);
 
     // ---- striped, coalesced loads
-    const int pb = ROUND0 ? o.pb : 0;
     for (int i = tid; i < tile_n + 2; i += kRrThreads) {
         int64_t j = base - 1 + i;
         unsigned long long w = (j >= 0 && j < n) ? keys[j] : 0ull;
-        if (ROUND0 && o.single) {
-            // bit 0 of the compared key: 0 for an ended suffix (f < h0), which
-            // is its own group, and so is the suffix after it
-            const uint32_t f = (uint32_t)(w & ((1ull << pb) - 1ull));
-            const bool ended = f < (uint32_t)h0;
-            S.u.k[i] = ((w >> pb) << 1) | (ended ? 0ull : 1ull);
-            if (i >= 1 && i <= tile_n) S.v[i - 1] = ended ? (uint32_t)(o.N - 1 - f) : f - (uint32_t)h0;
-            continue;
-        }
-        S.u.k[i] = w >> pb;
-        if (pb && i >= 1 && i <= tile_n) S.v[i - 1] = (uint32_t)(w & ((1ull << pb) - 1ull));
-        if (!ROUND0 && i >= 1 && i <= tile_n) S.oh[i - 1] = (uint32_t)(w >> o.kb);
+        S.u.k[i] = w;
+        if (i >= 1 && i <= tile_n) S.oh[i - 1] = (uint32_t)(w >> o.kb);
     }
     for (int i = tid; i < tile_n; i += kRrThreads) {
-        if (!pb) S.v[i] = vals[base + i];
-        if (!ROUND0) S.sl[i] = slots[base + i];
+        S.v[i] = vals[base + i];
+        S.sl[i] = slots[base + i];
     }
     __syncthreads();
     // ---- head flags, striped (conflict-free shared reads)
     auto is_head = [&](int64_t j) -> bool {   // j in [base, base + tile_n]
         if (j == 0) return true;
-        unsigned long long k = S.u.k[j - base + 1];
-        if (ROUND0 && o.single) {
-            const unsigned long long kp = S.u.k[j - base];
-            return (k & 1ull) == 0 || (kp & 1ull) == 0 || k != kp;   // ended: alone
-        }
-        if (ROUND0 && (int)(k & 31ull) < h0) return true;   // own '$' inside: final
-        return k != S.u.k[j - base];
+        return S.u.k[j - base + 1] != S.u.k[j - base];
     };
     {   // one ballot per 32 consecutive items; the next item's flag is the next lane's
         const int lane = tid & 31;
@@ -347,8 +332,8 @@ __global__ void __launch_bounds__(kRrThreads) k_rerank(
             if (li >= tile_n) break;
             int64_t j = base + li;
             if (headbits >> i & 1u) cur = j;
-            uint32_t slot = ROUND0 ? (uint32_t)j : S.sl[li];
-            S.u.o.head[li + (li >> 5)] = ROUND0 ? (uint32_t)cur : slot - (uint32_t)(j - cur);
+            uint32_t slot = S.sl[li];
+            S.u.o.head[li + (li >> 5)] = slot - (uint32_t)(j - cur);
             if (keepbits >> i & 1u) {
                 S.u.o.kp[li + (li >> 5)] = (int32_t)kp;
                 if (lastbits >> i & 1u) {
@@ -372,7 +357,7 @@ __global__ void __launch_bounds__(kRrThreads) k_rerank(
     const int nb = (int)((o.N + (1ll << o.bshift) - 1) >> o.bshift);
     for (int b = tid; b < nb; b += kRrThreads) S.bcnt[b] = 0;
     __syncthreads();
-    auto restage = [&](int li) -> bool { return ROUND0 || S.u.o.head[li + (li >> 5)] != S.oh[li]; };
+    auto restage = [&](int li) -> bool { return S.u.o.head[li + (li >> 5)] != S.oh[li]; };
     uint32_t bidx[kRrItems];
 #pragma unroll
     for (int i = 0; i < kRrItems; ++i) {
@@ -390,7 +375,7 @@ __global__ void __launch_bounds__(kRrThreads) k_rerank(
     for (int i = 0; i < kRrItems; ++i) {
         int li = tid + i * kRrThreads;
         if (li >= tile_n) break;
-        uint32_t slot = ROUND0 ? (uint32_t)(base + li) : S.sl[li];
+        uint32_t slot = S.sl[li];
         uint32_t pos = S.v[li];
         uint32_t hs = S.u.o.head[li + (li >> 5)];
         int32_t kp = S.u.o.kp[li + (li >> 5)];
@@ -411,14 +396,17 @@ __global__ void __launch_bounds__(kRrThreads) k_rerank(
 }
 
 // ------------------------------------------------------------------ round 0 without a look-back
-// After the initial sort, round 0 needs no cross-tile prefix: every group (equal
-// initial keys) is handled whole by the tile that holds its head.  A tile writes
-// SA for its own slots; for the groups whose heads it holds it writes the ranks
-// (staged by position bucket), and reserves room for their kept members in the
-// active list with one atomic, so each group stays contiguous there (the order
-// of the groups in the list is free: every later step works group by group).
-// A last group that runs past the tile is followed into the next tiles in global
-// memory; a tile with no head leaves its items to the tile of their head.
+// Round 0 needs no cross-tile prefix: every group (items with equal initial
+// keys) is handled whole by the tile that holds its head.  A tile writes SA for
+// its own items; for the groups whose heads it holds it writes the ranks (rank =
+// SA slot of the group head, staged by position bucket), and reserves room for
+// their kept members in the active list with one atomic, so that each group
+// stays contiguous there (the order of the groups in the list is free: every
+// later step works group by group).  A last group that runs past the tile is
+// followed into the next tiles in global memory; a tile with no head leaves its
+// items to the tile of their head.  (Later rounds, where most groups are a few
+// dozen members and many cross a tile boundary, keep k_rerank's look-back: the
+// look-back-free form measured slower there.)
 constexpr int kR0Threads = 256;
 constexpr int kR0Items = 8;
 constexpr int kR0Tile = kR0Threads * kR0Items;
@@ -441,32 +429,33 @@ __device__ __forceinline__ void r0_decode(unsigned long long w, uint32_t val, co
 }
 
 // Does the item with compared key k start a group (kp: the key before it)?
-__device__ __forceinline__ bool r0_head(unsigned long long k, unsigned long long kp, const RerankOut &o,
-                                        int h0) {
+__device__ __forceinline__ bool own_head(unsigned long long k, unsigned long long kp, const RerankOut &o,
+                                         int h0) {
     if (o.single) return (k & 1ull) == 0 || (kp & 1ull) == 0 || k != kp;
     if ((int)(k & 31ull) < h0) return true;   // its own '$' lies inside the key: final
     return k != kp;
 }
 
-struct R0Smem {
+struct OwnSmem {
     unsigned long long k[kR0Tile + 2];   // compared keys, one halo key on each side
     uint32_t v[kR0Tile];                 // positions
+    uint32_t hd[kR0Tile];                // rank of each owned item
     uint32_t hb[kR0Tile / 32];           // bit l of word w: item 32w + l starts a group
     uint32_t nb[kR0Tile / 32];           // ... the item after it starts one (or the data end)
     int64_t tmp[kR0Threads / 32 + 1];
     uint32_t bcnt[kMaxBuckets];          // per-bucket counts of a chunk, then global bases
     int64_t own_end;                     // end of the last group whose head is in the tile
-    unsigned long long kp_base;          // active-list index of the tile's first kept item
+    unsigned long long kp_base;          // list index of the tile's first kept item
     int first_head;                      // tile-local index of the first head (tile_n: none)
 };
 
-// Stages rank writes (pos -> head slot) of a chunk of items: counts per position
+// Stages rank writes (pos -> rank) of a chunk of items: counts per position
 // bucket in shared memory, one global atomic per bucket, then the writes.
-// Every thread calls; item i of the chunk is (pos[i], head[i]) for i < cnt when
+// Every thread calls; item i of the chunk is (pos(i), rank(i)) for i < cnt when
 // take(i) is true.
-template <typename Pos, typename Head, typename Take>
-__device__ __forceinline__ void r0_stage(R0Smem &S, const RerankOut &o, int cnt, Pos pos, Head head,
-                                         Take take, uint32_t *err) {
+template <typename SM, typename Pos, typename Rank, typename Take>
+__device__ __forceinline__ void own_stage(SM &S, const RerankOut &o, int cnt, Pos pos, Rank rank, Take take,
+                                          uint32_t *err) {
     const int nb = (int)((o.N + (1ll << o.bshift) - 1) >> o.bshift);
     for (int b = threadIdx.x; b < nb; b += kR0Threads) S.bcnt[b] = 0;
     __syncthreads();
@@ -493,34 +482,37 @@ __device__ __forceinline__ void r0_stage(R0Smem &S, const RerankOut &o, int cnt,
             atomicOr(err, DERR_BOUNDS);
             continue;
         }
-        o.stage[st] = make_uint2(p, head(i));
+        o.stage[st] = make_uint2(p, rank(i));
     }
     __syncthreads();
 }
 
+__device__ __forceinline__ void own_load(const unsigned long long *__restrict__ keys,
+                                         const uint32_t *__restrict__ vals, int64_t j, const RerankOut &o,
+                                         int h0, unsigned long long *key, uint32_t *pos) {
+    r0_decode(keys[j], o.pb ? 0u : vals[j], o, h0, key, pos);
+}
+
 __global__ void __launch_bounds__(kR0Threads) k_rerank0(const unsigned long long *__restrict__ keys,
-                                                        const uint32_t *__restrict__ vals, int64_t n,
-                                                        int h0, RerankOut o, uint32_t *err) {
-    __shared__ R0Smem S;
+                                                        const uint32_t *__restrict__ vals, int64_t n, int h0,
+                                                        RerankOut o, uint32_t *err) {
+    __shared__ OwnSmem S;
     const int tid = threadIdx.x, lane = tid & 31;
     const int64_t base = (int64_t)blockIdx.x * kR0Tile;
     if (base >= n) return;
     const int tile_n = (int)min((int64_t)kR0Tile, n - base);
 
-    // ---- keys (one halo each side) and positions; SA for the tile's own slots
+    // ---- keys (one halo each side) and positions; SA of the tile's items
     for (int i = tid; i < tile_n + 2; i += kR0Threads) {
         const int64_t j = base - 1 + i;
-        unsigned long long w = 0, key = 0;
-        uint32_t val = 0, pos = 0;
-        if (j >= 0 && j < n) {
-            w = keys[j];
-            if (!o.pb) val = vals[j];
-        }
-        r0_decode(w, val, o, h0, &key, &pos);
+        unsigned long long key = 0;
+        uint32_t pos = 0;
+        if (j >= 0 && j < n) own_load(keys, vals, j, o, h0, &key, &pos);
+        else r0_decode(0ull, 0u, o, h0, &key, &pos);
         S.k[i] = key;
         if (i >= 1 && i <= tile_n) {
             S.v[i - 1] = pos;
-            if ((int64_t)pos < o.N) o.sa[base + i - 1] = pos;
+            if ((int64_t)pos < o.N) o.sa[j] = pos;
             else atomicOr(err, DERR_BOUNDS);
         }
     }
@@ -530,13 +522,13 @@ __global__ void __launch_bounds__(kR0Threads) k_rerank0(const unsigned long long
         const int li = b0 + lane;
         const int64_t j = base + li;
         const bool in = li < tile_n;
-        const bool h = in && (j == 0 || r0_head(S.k[li + 1], S.k[li], o, h0));
+        const bool h = in && (j == 0 || own_head(S.k[li + 1], S.k[li], o, h0));
         const uint32_t hm = __ballot_sync(0xffffffffu, h);
         bool nh = false;
         if (in) {
             if (j == n - 1) nh = true;
             else if (lane < 31 && li + 1 < tile_n) nh = ((hm >> (lane + 1)) & 1u) != 0u;
-            else nh = r0_head(S.k[li + 2], S.k[li + 1], o, h0);
+            else nh = own_head(S.k[li + 2], S.k[li + 1], o, h0);
         }
         const uint32_t nm = __ballot_sync(0xffffffffu, nh);
         if (lane == 0) {
@@ -548,9 +540,10 @@ __global__ void __launch_bounds__(kR0Threads) k_rerank0(const unsigned long long
     // ---- first head of the tile; end of its last group (past the tile if needed)
     if (tid < 32) {
         int fh = tile_n;
-        for (int w0 = 0; w0 < (tile_n + 31) / 32; w0 += 32) {
+        const int words = (tile_n + 31) / 32;
+        for (int w0 = 0; w0 < words; w0 += 32) {
             const int w = w0 + lane;
-            const uint32_t hm = w < (tile_n + 31) / 32 ? S.hb[w] : 0u;
+            const uint32_t hm = w < words ? S.hb[w] : 0u;
             const uint32_t any = __ballot_sync(0xffffffffu, hm != 0u);
             if (any) {
                 const int wl = __ffs(any) - 1;
@@ -569,10 +562,10 @@ __global__ void __launch_bounds__(kR0Threads) k_rerank0(const unsigned long long
                 const int64_t j = j0 + lane;
                 unsigned long long key = 0;
                 uint32_t pos;
-                if (j < n) r0_decode(keys[j], o.pb ? 0u : vals[j], o, h0, &key, &pos);
+                if (j < n) own_load(keys, vals, j, o, h0, &key, &pos);
                 unsigned long long kprev = __shfl_up_sync(0xffffffffu, key, 1);
                 if (lane == 0) kprev = prev;
-                const bool stop = j >= n || r0_head(key, kprev, o, h0);
+                const bool stop = j >= n || own_head(key, kprev, o, h0);
                 const uint32_t sm = __ballot_sync(0xffffffffu, stop);
                 if (sm) {
                     end = j0 + __ffs(sm) - 1;
@@ -591,7 +584,7 @@ __global__ void __launch_bounds__(kR0Threads) k_rerank0(const unsigned long long
     if (fh >= tile_n) return;   // every item belongs to a group whose head is in an earlier tile
     const int64_t spill = S.own_end - (base + tile_n);
 
-    // ---- blocked: head slot and kept index of every owned item
+    // ---- blocked: rank and kept index of every owned item
     static_assert(kR0Items == 8, "a thread's items are one byte of a flag word");
     const int sh = (tid * kR0Items) & 31;
     uint32_t vm = tid * kR0Items >= tile_n ? 0u : (1u << min(kR0Items, tile_n - tid * kR0Items)) - 1u;
@@ -608,8 +601,7 @@ __global__ void __launch_bounds__(kR0Threads) k_rerank0(const unsigned long long
     const int64_t ex_max = __shfl_up_sync(0xffffffffu, inc_max, 1);
     const int64_t ex_keep = block_exclusive_sum<kR0Threads>((int64_t)__popc(keepbits), S.tmp, &tile_keep);
     if (tid == 0) S.kp_base = atomicAdd(o.kept, (unsigned long long)(tile_keep + spill));
-    // exclusive max over threads: the lane before in this warp, or the warps before
-    int64_t cur;
+    int64_t cur;   // list index of the head before this thread's items
     {
         const int w = tid >> 5;
         __syncthreads();
@@ -622,7 +614,7 @@ __global__ void __launch_bounds__(kR0Threads) k_rerank0(const unsigned long long
     __syncthreads();
     const unsigned long long kp0 = S.kp_base;
     {
-        uint32_t gend = keepbits & lastbits;
+        const uint32_t gend = keepbits & lastbits;
         const uint32_t ng = __popc(gend);
         uint32_t ng_inc = ng;
 #pragma unroll
@@ -641,14 +633,15 @@ __global__ void __launch_bounds__(kR0Threads) k_rerank0(const unsigned long long
             if (!((vm >> i) & 1u)) continue;
             const int64_t j = base + li;
             if ((headbits >> i) & 1u) cur = j;
-            S.k[li] = (unsigned long long)cur;        // keys are done with: head slot of item li
+            const uint32_t rk = (uint32_t)cur;
+            S.hd[li] = rk;
             if ((keepbits >> i) & 1u) {
                 if (kp >= (unsigned long long)n) {
                     atomicOr(err, DERR_BOUNDS);
                 } else {
                     o.nslots[kp] = (uint32_t)j;
                     o.npos[kp] = S.v[li];
-                    o.nhead[kp] = (uint32_t)cur;
+                    o.nhead[kp] = rk;
                 }
                 if ((lastbits >> i) & 1u) {
                     const uint32_t size = (uint32_t)(j - cur + 1);
@@ -665,18 +658,18 @@ __global__ void __launch_bounds__(kR0Threads) k_rerank0(const unsigned long long
     }
     __syncthreads();
     // ---- ranks of the owned items in the tile
-    r0_stage(S, o, tile_n, [&](int i) { return S.v[i]; }, [&](int i) { return (uint32_t)S.k[i]; },
-             [&](int i) { return i >= fh; }, err);
+    own_stage(S, o, tile_n, [&](int i) { return S.v[i]; }, [&](int i) { return S.hd[i]; },
+              [&](int i) { return i >= fh; }, err);
     if (spill <= 0) return;
-    // ---- the last group continues past the tile: all of it kept, one head
-    const uint32_t head = (uint32_t)tile_max;
+    // ---- the last group continues past the tile: all of it kept, one rank
+    const uint32_t rk = S.hd[tile_n - 1];
     const unsigned long long kps = kp0 + (unsigned long long)tile_keep;
     for (int64_t c0 = base + tile_n; c0 < S.own_end; c0 += kR0Tile) {
         const int cnt = (int)min((int64_t)kR0Tile, S.own_end - c0);
         for (int i = tid; i < cnt; i += kR0Threads) {
             unsigned long long key;
             uint32_t pos;
-            r0_decode(keys[c0 + i], o.pb ? 0u : vals[c0 + i], o, h0, &key, &pos);
+            own_load(keys, vals, c0 + i, o, h0, &key, &pos);
             S.v[i] = pos;
             const unsigned long long kp = kps + (unsigned long long)(c0 - base - tile_n + i);
             if (kp >= (unsigned long long)n || (int64_t)pos >= o.N) {
@@ -685,14 +678,14 @@ __global__ void __launch_bounds__(kR0Threads) k_rerank0(const unsigned long long
             }
             o.nslots[kp] = (uint32_t)(c0 + i);
             o.npos[kp] = pos;
-            o.nhead[kp] = head;
+            o.nhead[kp] = rk;
         }
         __syncthreads();
-        r0_stage(S, o, cnt, [&](int i) { return S.v[i]; }, [&](int) { return head; },
-                 [&](int) { return true; }, err);
+        own_stage(S, o, cnt, [&](int i) { return S.v[i]; }, [&](int) { return rk; }, [&](int) { return true; },
+                  err);
     }
     if (tid == 0) {
-        const uint32_t size = (uint32_t)(S.own_end - (int64_t)head);
+        const uint32_t size = (uint32_t)(S.own_end - tile_max);
         o.groups[atomicAdd(o.ngroups, 1ull)] = make_uint2((uint32_t)(kp0 + tile_keep + spill - size), size);
         atomicMax(o.maxgroup, (unsigned long long)size);
     }
@@ -1171,38 +1164,52 @@ __global__ void __launch_bounds__(kSegThreads) k_seg_radix(const uint2 *__restri
 }
 
 // Marks the members of the groups larger than kSegMax (flags zeroed beforehand).
+// Members of the groups sorted by global radix passes: flagged, and each one
+// tagged with its group's start in the active list.
 __global__ void k_flag_large(const uint2 *__restrict__ groups,
-                             const unsigned long long *__restrict__ d_ng, uint8_t *__restrict__ flags) {
+                             const unsigned long long *__restrict__ d_ng, uint8_t *__restrict__ flags,
+                             uint32_t *__restrict__ gstart) {
     const int64_t ng = (int64_t)*d_ng;
     for (int64_t g = blockIdx.x; g < ng; g += gridDim.x) {
         const uint2 gs = groups[g];
-        for (uint32_t i = threadIdx.x; i < gs.y; i += blockDim.x) flags[(size_t)gs.x + i] = 1;
+        for (uint32_t i = threadIdx.x; i < gs.y; i += blockDim.x) {
+            flags[(size_t)gs.x + i] = 1;
+            gstart[(size_t)gs.x + i] = gs.x;
+        }
     }
 }
 
+// Sort keys of the large-group members: (group start << kb) | rank[i+h].  The
+// groups may lie in the active list in any order; keyed by their start, the
+// sorted members come back group by group in list order.
 __global__ void k_take(const uint32_t *__restrict__ idx, const unsigned long long *__restrict__ d_m,
                        const unsigned long long *__restrict__ keys, const uint32_t *__restrict__ vals,
-                       unsigned long long *__restrict__ ck, uint32_t *__restrict__ cv) {
+                       const uint32_t *__restrict__ gstart, int kb, unsigned long long *__restrict__ ck,
+                       uint32_t *__restrict__ cv) {
     const int64_t m = (int64_t)*d_m;
+    const unsigned long long lo = (1ull << kb) - 1ull;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
          i += (int64_t)gridDim.x * blockDim.x) {
         uint32_t t = idx[i];
-        ck[i] = keys[t];
+        ck[i] = ((unsigned long long)gstart[t] << kb) | (keys[t] & lo);
         cv[i] = vals[t];
     }
 }
 
 // Sorted large-group members back to their ranges: the i-th of the sorted list
-// belongs at the i-th large-group index (groups keep their order: ascending head
-// rank = ascending position in the active list).
+// belongs at the i-th large-group index, with its key restored to (old head
+// rank << kb) | rank[i+h] (the head rank of a group is that of its first member).
 __global__ void k_put(const uint32_t *__restrict__ idx, const unsigned long long *__restrict__ d_m,
                       const unsigned long long *__restrict__ ck, const uint32_t *__restrict__ cv,
+                      const uint32_t *__restrict__ nhead, int kb,
                       unsigned long long *__restrict__ keys, uint32_t *__restrict__ vals) {
     const int64_t m = (int64_t)*d_m;
+    const unsigned long long lo = (1ull << kb) - 1ull;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m;
          i += (int64_t)gridDim.x * blockDim.x) {
         uint32_t t = idx[i];
-        keys[t] = ck[i];
+        const uint32_t start = (uint32_t)(ck[i] >> kb);
+        keys[t] = ((unsigned long long)nhead[start] << kb) | (ck[i] & lo);
         vals[t] = cv[i];
     }
 }
@@ -1259,11 +1266,12 @@ __global__ void k_widen(const uint32_t *__restrict__ a, int64_t n, int64_t *__re
 // A single sequence (one fragment, one instance) has only h0 suffixes that reach
 // its '$' within h0 symbols, so the initial word can drop the bases-left field:
 // word = (2*h0 bits of bases << pb) | f with f = bases left (0..h0-1) for those
-// few "ended" suffixes and f = position + h0 for every other one.  Among equal
-// bases the ended suffixes then come first, shorter first, as their '$' makes
-// them smaller, and the rest by position; f < N, so pb = bits of N - 1.  The
-// key is 5 bits shorter: one 8-bit pass fewer for a 16-base key.  Returns 0 when
-// no packed word holds a key of at least the collision bound.
+// few "ended" suffixes and f = position + h0 for every other one, stored at
+// index f of the sort input.  The radix passes order the bases and keep equal
+// ones in input order, i.e. f order: the ended suffixes first, shorter first (as
+// their '$' makes them smaller), then the rest by position.  f < N, so pb = bits
+// of N - 1.  The key is 5 bits shorter: one 8-bit pass fewer for a 16-base key.
+// Returns 0 when no packed word holds a key of at least the collision bound.
 int h0_single(int64_t N, int *pack_bits) {
     int hmin = (int)std::ceil((std::log2(std::max((double)N, 2.0)) + 5.0) / 2.0);
     hmin = std::max(8, std::min(hmin, 29));
@@ -1314,6 +1322,7 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
                  cudaStream_t s, uint32_t *isa_out) {
     dnasa_opts opts{};
     if (opts_in) opts = *opts_in;
+    if (opts.builder == 1) return sa_build_dc3(ctx, t, sa32, s, isa_out);
     const int tile_items = opts.tile_items ? opts.tile_items : radix_tile_default();
     const int64_t finish_threshold =
         opts.finish_threshold == 0 ? (int64_t)-1 : opts.finish_threshold;   // default: never
@@ -1370,7 +1379,7 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
     if (!rs.hist || !rr_status) return fail(ctx, DNASA_OOM, "sa_build workspace");
 
     // dynamic shared-memory limits of this call's kernels, once per (kernel, device)
-    DNASA_CUDA(ctx, smem_attr(k_rerank<false>, sizeof(RerankSmem<false>)));
+    DNASA_CUDA(ctx, smem_attr(k_rerank, sizeof(RerankSmem)));
     DNASA_CUDA(ctx, smem_attr(k_seg_radix<4>, seg_radix_smem<4>()));
     DNASA_CUDA(ctx, smem_attr(k_seg_radix<12>, seg_radix_smem<12>()));
     DNASA_CUDA(ctx, smem_attr(k_seg_radix<24>, seg_radix_smem<24>()));
@@ -1524,7 +1533,8 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
             DNASA_CUDA(ctx, cudaMemsetAsync(lflags, 0, (size_t)kept, s));
             {
                 LaunchScope ls_(ctx, PK_SEGSORT, s, 0.0);
-                k_flag_large<<<ctx->num_sms * 2, 256, 0, s>>>(glarge, cnt + CNT_SEG + 4, lflags);
+                k_flag_large<<<ctx->num_sms * 2, 256, 0, s>>>(glarge, cnt + CNT_SEG + 4, lflags,
+                                                              reinterpret_cast<uint32_t *>(ck2));
             }
             Arena rest = a;
             DNASA_TRY(compact_flags(ctx, rest, lflags, kept, lidx, cnt + CNT_TMP, s));
@@ -1536,14 +1546,17 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
             int g2 = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(m, 256), (int64_t)ctx->num_sms * 16));
             {
                 LaunchScope ls_(ctx, PK_SEGSORT, s, 24.0 * m);
-                k_take<<<g2, 256, 0, s>>>(lidx, cnt + CNT_TMP, keys[0], vals[0], ck[0], cv[0]);
+                // ck2 (the radix sort's spare buffer, free until the sort) holds the group starts
+                k_take<<<g2, 256, 0, s>>>(lidx, cnt + CNT_TMP, keys[0], vals[0],
+                                          reinterpret_cast<const uint32_t *>(ck2), b, ck[0], cv[0]);
             }
             int which;
             DNASA_TRY(radix_sort_pairs<unsigned long long>(ctx, rs, ck, cv, m, nullptr, 2 * b,
                                                            false, tile_items, &which, s, lbw));
             {
                 LaunchScope ls_(ctx, PK_SEGSORT, s, 24.0 * m);
-                k_put<<<g2, 256, 0, s>>>(lidx, cnt + CNT_TMP, ck[which], cv[which], keys[0], vals[0]);
+                k_put<<<g2, 256, 0, s>>>(lidx, cnt + CNT_TMP, ck[which], cv[which], L[cur][2], b, keys[0],
+                                         vals[0]);
             }
             DNASA_CUDA(ctx, cudaGetLastError());
         }
@@ -1552,8 +1565,11 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
         ro.stage = reinterpret_cast<uint2 *>(keys[1]);   // free again: stage the rank writes
         int tiles = ceil_div(kept, kRrTile);
         {
+            // later rounds keep the decoupled look-back: measured faster here than the
+            // look-back-free form, whose tiles wait on following the many groups that
+            // cross a tile boundary once most groups are a few dozen members
             LaunchScope ls_(ctx, PK_RERANK, s, 24.0 * kept);
-            k_rerank<false><<<tiles, kRrThreads, sizeof(RerankSmem<false>), s>>>(keys[0], vals[0], L[cur][0], kept,
+            k_rerank<<<tiles, kRrThreads, sizeof(RerankSmem), s>>>(keys[0], vals[0], L[cur][0], kept,
                                                          nullptr, h0, ro, rr_status, c->tile_ctr + 32,
                                                          &c->err);
         }
