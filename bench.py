@@ -67,6 +67,8 @@ def parse():
     ap.add_argument("--lambdas", default="0.25,0.5,0.75,0.9,1.0,1.25",
                     help="served: arrival rates as multiples of one-job-per-launch capacity")
     ap.add_argument("--no-tune", action="store_true", help="skip the build-option autotuner")
+    ap.add_argument("--builder", default="doubling", choices=["doubling", "dc3"],
+                    help="sa64m / large: suffix-array builder (dc3: the difference-cover algorithm)")
     ap.add_argument("--slots", type=int, default=2)
     ap.add_argument("--max-batch", type=int, default=16)
     return ap.parse_args()
@@ -860,7 +862,9 @@ def main():
     sa = torch.empty(N, dtype=idx_dtype, device=dev)
     lcp = torch.empty(N, dtype=torch.int32, device=dev)
     opts, tuned = None, None
-    if not args.no_tune:
+    if args.builder == "dc3":
+        opts = binding.make_opts(builder=1)
+    elif not args.no_tune:
         opts, tms = binding.dnasa_autotune(ctx, packed, toff, nr, N, cache_path=TUNE_CACHE)
         tuned = {"tile_items": opts.tile_items, "finish_threshold": opts.finish_threshold,
                  "lookback": opts.lookback, "sa_ms": tms}
@@ -984,6 +988,7 @@ def main():
     breakdown = {k: {"launches": v["launches"], "ms_per_step": v["ms"] / args.steps,
                      "share": v["ms"] / max(1e-9, sum(x["ms"] for x in prof.values())),
                      "algorithmic_gbs": v["bytes"] / (v["ms"] / 1000.0) / 1e9 if v["ms"] else None,
+                     "algorithmic_bytes_per_step": v["bytes"] / args.steps,
                      "dram_per_algorithmic_byte": traffic_ratio(k)}
                  for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])}
     cpu = None
@@ -1013,7 +1018,9 @@ def main():
                    "l2": "working set >> L2 (no flush needed)",
                    "rounds": trace["rounds"], "finished_direct": trace["finished_direct"],
                    "active_per_round": trace["active"], "sa_only_ms": sa_only_ms,
-                   "autotuned": tuned, **({"reads": reads_info} if reads_info else {})},
+                   "autotuned": tuned, "builder": args.builder,
+                   **({"dc3_levels": trace["rounds"]} if args.builder == "dc3" else {}),
+                   **({"reads": reads_info} if reads_info else {})},
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": ({"value": N * world / (e2e["ms"] / 1000.0) / 1e6, "unit": UNIT,

@@ -34,7 +34,7 @@ namespace {
 constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;
 constexpr int kScanTile = kScanThreads * kScanItems;
-constexpr int kMergeRun = 16;   // outputs per thread of the merge
+constexpr int kMergeRun = 64;   // outputs per thread of the merge (one diagonal search per run)
 
 inline int grid_for(dnasa_ctx *ctx, int64_t n, int threads = 256) {
     return (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(std::max<int64_t>(n, 1), threads),
