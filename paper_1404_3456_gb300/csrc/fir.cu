@@ -181,20 +181,48 @@ __global__ void __launch_bounds__(256) k_fir_query(TextDesc t, FirIndex fi) {
     }
 }
 
+// One fir relation as a move of the search: from the remainder at position x,
+// place fragment c; the next remainder starts at text position nx, adv bases
+// further in the result.  kind 0: c inside the remainder (c a proper prefix of
+// it: the remainder continues in the same fragment past |c|); 1: the remainder
+// inside c (the remainder continues in c past |X|); 2: c equal to the
+// remainder (allowed only as the last fragment; the result ends adv bases on).
+struct FirMove {
+    uint32_t c, nx, adv, kind;
+};
+
 struct FirState {
-    const unsigned long long *pairs;      // sorted (x << kb) | c
-    const uint32_t *xoff;                 // [N + 1]: pairs of position x are [xoff[x], xoff[x+1])
+    const FirMove *moves;                 // one per pair, in pair order (x, then c ascending)
+    const uint32_t *xoff;                 // [N + 1]: moves of position x are [xoff[x], xoff[x+1])
     int64_t npairs;
-    int kb;
     int64_t max_steps;
     uint8_t *used;                        // [n_reads]
-    uint2 *frames;                        // [n_reads]: (x, index in pairs of the placed c + 1)
+    uint4 *frames;                        // [n_reads]: (x, index of the placed move + 1, result offset of x)
     int64_t *start;                       // [n_reads] output: offset in the instance's result
     int32_t *status;                      // [n_inst] 0 solved, 1 none, 2 gave up
     int64_t *steps;                       // [n_inst]
     int64_t *rs_len;                      // [n_inst]
 };
 
+// The move of every (x, c) pair: the lengths that decide it are read once here,
+// so that a step of the search is a few dependent loads.
+__global__ void k_fir_moves(TextDesc t, const unsigned long long *__restrict__ pairs, int64_t np, int kb,
+                            FirMove *__restrict__ moves) {
+    const unsigned long long cmask = (1ull << kb) - 1ull;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < np;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t x = (int64_t)(pairs[p] >> kb), c = (int64_t)(pairs[p] & cmask);
+        const int64_t k = frag_of(t, x);
+        const int64_t l = flen(t.toff, k) - (x - __ldg(t.toff + k));   // |X|
+        const int64_t lc = flen(t.toff, c);
+        FirMove m;
+        m.c = (uint32_t)c;
+        if (lc < l) { m.kind = 0u; m.nx = (uint32_t)(x + lc); m.adv = (uint32_t)lc; }
+        else if (lc > l) { m.kind = 1u; m.nx = (uint32_t)(__ldg(t.toff + c) + l); m.adv = (uint32_t)l; }
+        else { m.kind = 2u; m.nx = 0u; m.adv = (uint32_t)l; }
+        moves[p] = m;
+    }
+}
 
 // xoff[x] = first pair of position x (pairs sorted by x): each pair that starts a
 // run of its position fills the offsets of the positions since the previous run.
@@ -210,78 +238,70 @@ __global__ void k_fir_xoff(const unsigned long long *__restrict__ pairs, int64_t
 }
 
 // Depth-first search of one instance (one thread per instance).  Frame f holds
-// the remainder's text position x and 1 + the index (in pairs) of the candidate
-// placed from it (0: none yet).  Fragment indices of an instance are the
-// contiguous range [r0, r1).
+// the remainder's text position x, 1 + the index of the move placed from it (0:
+// none yet), and the remainder's offset in the result.  Fragment indices of an
+// instance are the contiguous range [r0, r1).
 __global__ void k_fir_dfs(TextDesc t, FirState S) {
     const int64_t inst = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (inst >= t.n_inst) return;
     const int64_t r0 = t.n_inst > 1 ? __ldg(t.inst_roff + inst) : 0;
     const int64_t r1 = t.n_inst > 1 ? __ldg(t.inst_roff + inst + 1) : t.n_reads;
     const int64_t n = r1 - r0;
-    const unsigned long long cmask = (1ull << S.kb) - 1ull;
     for (int64_t r = r0; r < r1; ++r) { S.used[r] = 0; S.start[r] = -1; }
-    uint2 *F = S.frames + r0;
+    uint4 *F = S.frames + r0;
     int64_t steps = 0;
     int status = 1;
     int64_t rs_len = 0;
     bool done = false;
     for (int64_t k = r0; k < r1 && !done && status != 2; ++k) {
-        const int64_t lk = flen(t.toff, k);
         const uint64_t xk = (uint64_t)__ldg(t.toff + k);
         const int64_t pe = (int64_t)__ldg(S.xoff + xk + 1);
         for (int64_t pi = (int64_t)__ldg(S.xoff + xk); pi < pe && !done && status != 2; ++pi) {
-            const int64_t i = (int64_t)(S.pairs[pi] & cmask);
-            const int64_t li = flen(t.toff, i);
-            if (i == k || li >= lk) continue;       // start pairs: proper prefixes of d_k
+            const FirMove st = S.moves[pi];
+            if (st.kind != 0u) continue;            // start pairs: proper prefixes of d_k
+            const int64_t i = (int64_t)st.c;
             if (++steps > S.max_steps) { status = 2; break; }
             S.used[i] = S.used[k] = 1;
             S.start[i] = S.start[k] = 0;
             int64_t top = 0;
-            F[0] = make_uint2((uint32_t)(xk + li), 0u);
+            F[0] = make_uint4(st.nx, 0u, st.adv, 0u);
             while (top >= 0 && !done) {
-                const uint64_t x = F[top].x;
+                const uint4 f = F[top];
                 int64_t from;
-                if (F[top].y) {                     // back from the child: undo its fragment
-                    const int64_t prev = (int64_t)F[top].y - 1;
-                    const int64_t c = (int64_t)(S.pairs[prev] & cmask);
+                if (f.y) {                          // back from the child: undo its fragment
+                    const int64_t prev = (int64_t)f.y - 1;
+                    const int64_t c = (int64_t)S.moves[prev].c;
                     S.used[c] = 0;
                     S.start[c] = -1;
                     from = prev + 1;
                     F[top].y = 0u;
                 } else {
-                    from = (int64_t)__ldg(S.xoff + x);
+                    from = (int64_t)__ldg(S.xoff + f.x);
                 }
-                const int64_t ko = frag_of(t, (int64_t)x);
-                const int64_t o = (int64_t)x - __ldg(t.toff + ko);
-                const int64_t l = flen(t.toff, ko) - o;
-                const int64_t pos = S.start[ko] + o;
                 const int64_t nused = 2 + top;
-                int64_t pick = -1, nx = 0;
-                bool last = false;
-                const int64_t to = (int64_t)__ldg(S.xoff + x + 1);
+                const int64_t to = (int64_t)__ldg(S.xoff + f.x + 1);
+                int64_t pick = -1;
+                FirMove m;
                 for (int64_t p = from; p < to; ++p) {
-                    const int64_t c = (int64_t)(S.pairs[p] & cmask);
-                    if (S.used[c]) continue;
-                    const int64_t lc = flen(t.toff, c);
-                    if (lc < l) { pick = p; nx = (int64_t)x + lc; break; }          // c inside X
-                    if (lc > l) { pick = p; nx = __ldg(t.toff + c) + l; break; }    // X inside c
-                    if (nused + 1 == n) { pick = p; last = true; break; }          // both end here
+                    m = S.moves[p];
+                    if (S.used[m.c]) continue;
+                    if (m.kind == 2u && nused + 1 != n) continue;   // equal: only as the last one
+                    pick = p;
+                    break;
                 }
                 if (pick < 0) { --top; continue; }  // no fir fragment: back-track
                 if (++steps > S.max_steps) { status = 2; break; }
-                const int64_t c = (int64_t)(S.pairs[pick] & cmask);
-                S.used[c] = 1;
-                S.start[c] = pos;
+                S.used[m.c] = 1;
+                S.start[m.c] = (int64_t)f.z;
                 F[top].y = (uint32_t)(pick + 1);
-                if (last) {
+                if (m.kind == 2u) {                 // both cuttings end here
                     done = true;
                     status = 0;
-                    rs_len = pos + l;
+                    rs_len = (int64_t)f.z + (int64_t)m.adv;
                     break;
                 }
                 ++top;
-                F[top] = make_uint2((uint32_t)nx, 0u);
+                F[top] = make_uint4(m.nx, 0u, f.z + m.adv, 0u);
             }
             if (!done)
                 for (int64_t r = r0; r < r1; ++r) { S.used[r] = 0; S.start[r] = -1; }
@@ -387,7 +407,7 @@ int fir_impl(dnasa_ctx *ctx, const uint8_t *text, int64_t N, const int64_t *inst
         add(radix_scratch_bytes(nr, 32, tile));
         add((size_t)cap * 8); add((size_t)cap * 8);        // pairs x2
         add(radix_scratch_bytes(cap, 64, tile));
-        add((size_t)nr); add((size_t)nr * 8);              // used flags, frames
+        add((size_t)nr); add((size_t)nr * 16);             // used flags, frames
         DNASA_TRY(ws_reserve(ctx, need + 8192, s));
         Arena a = ws_arena(ctx);
         uint32_t *rk[2] = {a.take<uint32_t>((size_t)nr), a.take<uint32_t>((size_t)nr)};
@@ -399,7 +419,7 @@ int fir_impl(dnasa_ctx *ctx, const uint8_t *text, int64_t N, const int64_t *inst
                                      a.take<unsigned long long>((size_t)cap)};
         RadixScratch rs2 = radix_scratch_take(a, cap, 64, tile);
         uint8_t *used = a.take<uint8_t>((size_t)nr);
-        uint2 *frames = a.take<uint2>((size_t)nr);
+        uint4 *frames = a.take<uint4>((size_t)nr);
         if (!frames) return fail(ctx, DNASA_OOM, "fir_reconstruct workspace");
         DNASA_CUDA(ctx, cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * 8, s));
         DNASA_CUDA(ctx, cudaMemsetAsync(cnt + CNT_TMP, 0xff, 8, s));   // running minimum
@@ -456,11 +476,17 @@ int fir_impl(dnasa_ctx *ctx, const uint8_t *text, int64_t N, const int64_t *inst
             k_fir_xoff<<<grid_for(ctx, np + 1), 256, 0, s>>>(pk[which2], np, kb, N, (uint32_t *)xoffb.p);
         }
         DNASA_CUDA(ctx, cudaGetLastError());
+        DevBuf movesb;
+        DNASA_TRY(dev_alloc(ctx, movesb, (size_t)std::max<int64_t>(np, 1) * sizeof(FirMove), s));
+        if (np > 0) {
+            LaunchScope ls_(ctx, PK_OVERLAP, s, 24.0 * np);
+            k_fir_moves<<<grid_for(ctx, np), 256, 0, s>>>(t, pk[which2], np, kb, (FirMove *)movesb.p);
+        }
+        DNASA_CUDA(ctx, cudaGetLastError());
         FirState S;
-        S.pairs = pk[which2];
+        S.moves = (const FirMove *)movesb.p;
         S.xoff = (const uint32_t *)xoffb.p;
         S.npairs = np;
-        S.kb = kb;
         S.max_steps = max_steps;
         S.used = used;
         S.frames = frames;

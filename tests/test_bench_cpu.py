@@ -76,3 +76,26 @@ def test_dist_env_defaults(monkeypatch):
     for k in ("RANK", "LOCAL_RANK", "WORLD_SIZE"):
         monkeypatch.delenv(k, raising=False)
     assert bench.dist_env() == (0, 0, 1)
+
+
+def test_traffic_ratio_only_for_the_captured_source(tmp_path, monkeypatch):
+    """A DRAM-per-algorithmic-byte ratio is reported only while the kernel source
+    hashes to the one the counters were taken on."""
+    import hashlib
+
+    src = tmp_path / "k.cu"
+    src.write_text("kernel v1\n")
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    good = hashlib.sha1(src.read_bytes()).hexdigest()
+    (prof / "traffic.json").write_text(json.dumps({
+        "onesweep": {"dram_per_algorithmic_byte": 0.9, "valid": True, "source": "k.cu", "source_sha1": good},
+        "rerank": {"dram_per_algorithmic_byte": 1.1, "valid": True, "source": "k.cu", "source_sha1": "0" * 40},
+        "lcp": {"dram_per_algorithmic_byte": 1.0, "valid": False, "source": "k.cu", "source_sha1": good}}))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.traffic_ratio("onesweep") == 0.9
+    assert bench.traffic_ratio("rerank") is None      # source changed since the capture
+    assert bench.traffic_ratio("lcp") is None         # marked invalid
+    assert bench.traffic_ratio("segsort") is None     # never captured
+    src.write_text("kernel v2\n")
+    assert bench.traffic_ratio("onesweep") is None
