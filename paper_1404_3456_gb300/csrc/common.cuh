@@ -197,6 +197,8 @@ size_t sa_workspace_bytes(int64_t N, int tile_items);
 // non-null it also receives the inverse SA (the final rank array), N uint32.
 int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_opts *opts,
                  cudaStream_t s, uint32_t *isa_out = nullptr);
+// x[i] = x[0] + ... + x[i] in place (dc3.cu; sums below 2^32).
+int scan_inclusive_u32(dnasa_ctx *ctx, uint32_t *x, int64_t n, cudaStream_t s);
 // The same suffix array by DC3 (dc3.cu), one instance; isa_out may be null.
 int sa_build_dc3(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, cudaStream_t s, uint32_t *isa_out);
 // fid[p] = fragment holding text position p, for p in [0, N).

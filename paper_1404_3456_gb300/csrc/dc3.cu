@@ -384,6 +384,20 @@ int dc3_level(dnasa_ctx *ctx, const uint32_t *s, int64_t n, uint64_t K, uint32_t
 
 }  // namespace
 
+// x[i] = x[0] + ... + x[i] in place (n uint32 values, sums below 2^32).
+int scan_inclusive_u32(dnasa_ctx *ctx, uint32_t *x, int64_t n, cudaStream_t st) {
+    if (n <= 0) return DNASA_OK;
+    const int64_t tiles = ceil_div(n, kScanTile);
+    DevBuf sums;
+    DNASA_TRY(dev_alloc(ctx, sums, (size_t)(tiles + 1) * 8, st));
+    LaunchScope ls_(ctx, PK_OTHER, st, 8.0 * n);
+    k_tile_sums<<<(int)tiles, kScanThreads, 0, st>>>(x, n, (uint64_t *)sums.p);
+    k_scan_sums<<<1, 1024, 0, st>>>((uint64_t *)sums.p, tiles);
+    k_tile_apply<<<(int)tiles, kScanThreads, 0, st>>>(x, n, (const uint64_t *)sums.p);
+    DNASA_CUDA(ctx, cudaGetLastError());
+    return DNASA_OK;
+}
+
 // Suffix array of the packed text by DC3 (one instance); isa_out (may be null)
 // receives the inverse.
 int sa_build_dc3(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, cudaStream_t st, uint32_t *isa_out) {

@@ -15,8 +15,10 @@
 // parallel pass over the text, before the search:
 //   * R = the fragment starts in SA order with LCP_R (common prefix of
 //     consecutive entries), per instance;
-//   * for X at text position x: binary search of x's SA slot among R's slots;
-//     walking forward while the common prefix with X stays >= |X| gives the
+//   * for X at text position x: its place among R's slots (the number of
+//     fragment starts at smaller slots, from one prefix count over the SA --
+//     Sec. IV's binary search answered for every slot at once); walking
+//     forward while the common prefix with X stays >= |X| gives the
 //     fragments X is a prefix of (or equal to); walking backward, a fragment c
 //     whose common prefix with X is all of c is a prefix of X;
 //   * the (x, c) pairs are radix sorted, so the candidates of each x are a run
@@ -92,8 +94,18 @@ __global__ void k_fir_lcpr(TextDesc t, const uint32_t *__restrict__ R, int32_t *
     }
 }
 
+// flag[s] = 1 when the suffix at SA slot s starts a fragment (then scanned).
+__global__ void k_fir_startflag(TextDesc t, const uint32_t *__restrict__ sa, uint32_t *__restrict__ flag) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < t.N;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = sa[j];
+        flag[j] = p == __ldg(t.toff + frag_of(t, p)) ? 1u : 0u;
+    }
+}
+
 struct FirIndex {
     const uint32_t *isa, *Rslot, *R;
+    const uint32_t *nstart;               // [N]: fragment-start suffixes at SA slots <= s
     const int32_t *lcpr;
     const uint2 *rrange;
     int64_t minlen;
@@ -115,13 +127,12 @@ __device__ __forceinline__ void fir_candidates(const TextDesc &t, const FirIndex
     if (l <= 0) return;                             // x is a '$'
     const uint32_t s = fi.isa[x];
     const uint2 rg = __ldg(fi.rrange + k);
-    int lo = (int)rg.x, hi = (int)rg.y;
-    while (lo < hi) {                               // first fragment start at or after X's slot
-        const int m = (lo + hi) >> 1;
-        if (__ldg(fi.Rslot + m) < s) lo = m + 1; else hi = m;
-    }
+    // first fragment start at or after X's slot: the fragment starts at smaller
+    // slots, counted once for every slot (instances occupy consecutive slots, so
+    // this index lies in the instance's range of R)
+    const bool self = o == 0;                       // X is itself a fragment
+    const int lo = (int)__ldg(fi.nstart + s) - (self ? 1 : 0);
     const uint64_t bx = (uint64_t)(x - k);          // base coordinate of X
-    const bool self = lo < (int)rg.y && __ldg(fi.Rslot + lo) == s;   // X is itself a fragment
     // forward: fragments having X as a prefix (|c| >= l)
     {
         int64_t h = -1;                             // common prefix of X with R[i]
@@ -390,6 +401,12 @@ int fir_impl(dnasa_ctx *ctx, const uint8_t *text, int64_t N, const int64_t *inst
         t.fid = (const uint32_t *)fid.p;
     }
     DNASA_TRY(sa_build_u32(ctx, t, (uint32_t *)sa.p, nullptr, s, (uint32_t *)isa.p));
+    {   // the SA itself is needed no further: it becomes the count of fragment starts per slot
+        LaunchScope ls_(ctx, PK_OVERLAP, s, 8.0 * N);
+        k_fir_startflag<<<grid_for(ctx, N), 256, 0, s>>>(t, (const uint32_t *)sa.p, (uint32_t *)sa.p);
+    }
+    DNASA_CUDA(ctx, cudaGetLastError());
+    DNASA_TRY(scan_inclusive_u32(ctx, (uint32_t *)sa.p, N, s));
 
     // ---- R, LCP_R, then the fir pairs of every text position
     const int tile = radix_tile_default();
@@ -440,6 +457,7 @@ int fir_impl(dnasa_ctx *ctx, const uint8_t *text, int64_t N, const int64_t *inst
         FirIndex fi;
         fi.isa = (const uint32_t *)isa.p;
         fi.Rslot = rk[which];
+        fi.nstart = (const uint32_t *)sa.p;
         fi.R = rv[which];
         fi.lcpr = lcpr;
         fi.rrange = rrange;

@@ -10,9 +10,11 @@
 //     with LCP_R[k] = common prefix of R[k-1] and R[k];
 //   * the fragments having X as a prefix are exactly the fragment starts that
 //     follow X's own SA slot within X's LCP interval (X ends in its '$', which
-//     sorts before any base); the first candidate is found by binary search of
-//     X's slot among R's slots, checked by one direct packed-word comparison,
-//     and the rest are read off LCP_R while it stays >= |X|.
+//     sorts before any base); the first candidate's index in R is the number of
+//     fragment starts at smaller SA slots (Sec. IV's binary search of X among
+//     the fragments, answered for every slot at once by one prefix count over
+//     the SA), checked by one direct packed-word comparison, and the rest are
+//     read off LCP_R while it stays >= |X|.
 // Candidates (j, k, L) are radix sorted by (j, k, L desc) and reduced to the
 // largest L per ordered pair.  Containment of fragment k: some other suffix
 // shares all |r_k| bases with r_k's start suffix (the SA neighbour just before
@@ -77,8 +79,18 @@ __global__ void k_lcp_r(TextDesc t, const uint32_t *__restrict__ R, int32_t *__r
     }
 }
 
+// flag[s] = 1 when the suffix at SA slot s starts a fragment (then scanned).
+__global__ void k_startflag(TextDesc t, const uint32_t *__restrict__ sa, uint32_t *__restrict__ flag) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < t.N;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t p = sa[j];
+        flag[j] = p == __ldg(t.toff + frag_of(t, p)) ? 1u : 0u;
+    }
+}
+
 struct QueryArgs {
     const uint32_t *isa, *Rslot, *R;
+    const uint32_t *nstart;           // [N]: fragment-start suffixes at SA slots <= s
     const int32_t *lcpr;
     const uint2 *rrange;              // per fragment: its instance's range in R (batches)
     int32_t lmin;
@@ -103,17 +115,10 @@ __device__ __forceinline__ bool query_locate(const TextDesc &t, const QueryArgs 
     const int64_t L = __ldg(t.toff + j + 1) - 1 - q;   // bases of X = r_j[o..]
     if (o < 1 || L < a.lmin) return false;
     const uint32_t s = a.isa[q];
-    int lo = 0, hi = (int)t.n_reads;
-    if (a.rrange) {
-        const uint2 rg = __ldg(a.rrange + j);
-        lo = (int)rg.x;
-        hi = (int)rg.y;
-    }
-    const int ri1 = hi;
-    while (lo < hi) {   // first fragment start after X's slot
-        const int m = (lo + hi) >> 1;
-        if (__ldg(a.Rslot + m) < s) lo = m + 1; else hi = m;
-    }
+    const int ri1 = a.rrange ? (int)__ldg(a.rrange + j).y : (int)t.n_reads;
+    // first fragment start after X's slot = the fragment starts at smaller slots
+    // (X itself is no fragment start: o >= 1); instances occupy consecutive slots
+    const int lo = (int)__ldg(a.nstart + s);
     if (lo >= ri1) return false;
     const int64_t k = __ldg(a.R + lo);
     if (frag_len(t.toff, k) < L) return false;
@@ -249,6 +254,7 @@ int overlap_impl(dnasa_ctx *ctx, const TextDesc &t, const uint32_t *sa32, const 
     size_t need = 0;
     auto add = [&](size_t bytes) { need += (bytes + 255) & ~size_t(255); };
     add((size_t)N * 4);                              // isa
+    add((size_t)N * 4);                              // fragment starts per SA slot (scanned)
     for (int i = 0; i < 4; ++i) add((size_t)nr * 4); // R keys/vals x2
     add((size_t)nr * 4);                             // lcp_r
     if (t.n_inst > 1) add((size_t)nr * 8);           // per-fragment instance range in R
@@ -265,6 +271,7 @@ int overlap_impl(dnasa_ctx *ctx, const TextDesc &t, const uint32_t *sa32, const 
     for (int attempt = 0; attempt < 2; ++attempt) {
         Arena a = ws_arena(ctx);
         uint32_t *isa_ws = a.take<uint32_t>((size_t)N);
+        uint32_t *nstart = a.take<uint32_t>((size_t)N);
         const uint32_t *isa = isa_in ? isa_in : isa_ws;
         uint32_t *rk[2] = {a.take<uint32_t>((size_t)nr), a.take<uint32_t>((size_t)nr)};
         uint32_t *rv[2] = {a.take<uint32_t>((size_t)nr), a.take<uint32_t>((size_t)nr)};
@@ -307,8 +314,14 @@ int overlap_impl(dnasa_ctx *ctx, const TextDesc &t, const uint32_t *sa32, const 
             LaunchScope ls_(ctx, PK_OVERLAP, s, 24.0 * nr);
             k_read_range<<<grid_for(ctx, nr), 256, 0, s>>>(t, rrange);
         }
+        {
+            LaunchScope ls_(ctx, PK_OVERLAP, s, 8.0 * N);
+            k_startflag<<<grid_for(ctx, N), 256, 0, s>>>(t, sa32, nstart);
+        }
+        DNASA_CUDA(ctx, cudaGetLastError());
+        DNASA_TRY(scan_inclusive_u32(ctx, nstart, N, s));
         QueryArgs qa;
-        qa.isa = isa; qa.Rslot = Rslot; qa.R = R; qa.lcpr = lcpr; qa.rrange = rrange;
+        qa.isa = isa; qa.Rslot = Rslot; qa.R = R; qa.lcpr = lcpr; qa.rrange = rrange; qa.nstart = nstart;
         qa.lmin = min_overlap;
         qa.kb = kb; qa.lb = lb; qa.cand = ck[0]; qa.cap = (unsigned long long)cand_cap;
         qa.count = cnt + CNT_CAND;

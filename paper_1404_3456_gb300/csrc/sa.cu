@@ -556,23 +556,38 @@ __global__ void __launch_bounds__(kR0Threads) k_rerank0(const unsigned long long
         const int last = tile_n - 1;
         const bool closed = (S.nb[last >> 5] >> (last & 31)) & 1u;
         if (fh < tile_n && !closed) {
-            // follow the last group into the next tiles: 32 keys per probe
-            unsigned long long prev = S.k[tile_n];   // key of the tile's last item
-            for (int64_t j0 = base + tile_n;; j0 += 32) {
-                const int64_t j = j0 + lane;
-                unsigned long long key = 0;
+            // follow the last group into the next tiles.  The keys are sorted and a
+            // group that runs past a tile has a key no ended suffix shares, so its
+            // end is the first slot whose key differs: found by galloping (lane l
+            // probes 2^l slots on), then by 32-way splits of the bracket
+            const unsigned long long gk = S.k[tile_n];   // key of the tile's last item
+            auto differs = [&](int64_t j) -> bool {
+                if (j >= n) return true;
+                unsigned long long key;
                 uint32_t pos;
-                if (j < n) own_load(keys, vals, j, o, h0, &key, &pos);
-                unsigned long long kprev = __shfl_up_sync(0xffffffffu, key, 1);
-                if (lane == 0) kprev = prev;
-                const bool stop = j >= n || own_head(key, kprev, o, h0);
-                const uint32_t sm = __ballot_sync(0xffffffffu, stop);
-                if (sm) {
-                    end = j0 + __ffs(sm) - 1;
-                    break;
-                }
-                prev = __shfl_sync(0xffffffffu, key, 31);
+                own_load(keys, vals, j, o, h0, &key, &pos);
+                return key != gk;
+            };
+            int64_t a = base + tile_n - 1;                  // last slot known in the group
+            int64_t b;                                      // a slot known past it
+            {
+                const int64_t j = a + ((int64_t)1 << lane);
+                const uint32_t dm = __ballot_sync(0xffffffffu, differs(j));
+                const int l = __ffs(dm) - 1;                // lane 31 reaches past n: dm != 0
+                b = a + ((int64_t)1 << l);
+                if (l > 0) a += (int64_t)1 << (l - 1);
             }
+            while (b - a > 1) {
+                const int64_t step = (b - a + 32) / 33;     // 32 probes inside (a, b)
+                const int64_t j = min(a + step * (lane + 1), b - 1);
+                const uint32_t dm = __ballot_sync(0xffffffffu, differs(j));
+                const int l = dm ? __ffs(dm) - 1 : 32;
+                const int64_t nb = l < 32 ? min(a + step * (l + 1), b - 1) : b;
+                const int64_t na = l > 0 ? min(a + step * l, b - 1) : a;
+                a = na;
+                b = nb;
+            }
+            end = b;
         }
         if (lane == 0) {
             S.first_head = fh;
