@@ -300,11 +300,17 @@ __device__ __forceinline__ void onesweep_tile(
     }
 }
 
-// Held to 80 registers so that three CTAs share an SM whatever the variant
-// (the pass is latency- and issue-bound).  Every tile but the last is full and
-// runs without per-item bounds tests.
+// CTAs per SM a variant is held to: the pass is latency- and issue-bound, so
+// small tiles (2048 items) take five CTAs per SM and the larger ones three (80
+// registers, no spills).  Every tile but the last is full and runs without
+// per-item bounds tests.
+template <int ITEMS>
+struct OnesweepOcc {
+    static constexpr int value = ITEMS <= 8 ? 5 : 3;
+};
+
 template <typename K, int ITEMS, bool HAS_VALS, int LBW>
-__global__ void __launch_bounds__(kThreads, 3) k_onesweep(
+__global__ void __launch_bounds__(kThreads, OnesweepOcc<ITEMS>::value) k_onesweep(
     const K *__restrict__ kin, const uint32_t *__restrict__ vin, K *__restrict__ kout,
     uint32_t *__restrict__ vout, const uint32_t *__restrict__ bucket, unsigned long long *status,
     uint32_t *tile_ctr, int64_t n_host, const unsigned long long *__restrict__ d_n, int shift,

@@ -102,3 +102,30 @@ def test_edges_past_cap_report_capacity(ctx):
                                          ctypes.c_void_p(edges.data_ptr()), 2, ctypes.byref(n),
                                          ctypes.byref(m), None)
     assert rc == B().CAPACITY and n.value == want
+
+
+def test_degenerate_and_bad_arguments(ctx):
+    """Fragments shorter than the minimum overlap give no edges; mu >= 1, a
+    non-positive minimum and host pointers are refused."""
+    import ctypes
+
+    t = np.frombuffer(b"ACGTACGT$TTGCA$GGG$", np.uint8).copy()
+    g, m = B().overlap_search_approx(ctx, torch.from_numpy(t).cuda(), 40, 1, 10, True)
+    assert g.shape[0] == 0 and m == 6
+    assert oracle.overlaps_approx(t, 40, 1, 10, True)[0].size == 0
+    L = B().lib()
+    d = torch.from_numpy(t).cuda()
+    edges = torch.empty((16, 4), dtype=torch.int32, device="cuda")
+    n, mo = ctypes.c_int64(0), ctypes.c_int64(0)
+    for lmin, num, den, both in [(5, 3, 3, 0), (0, 0, 1, 0), (5, -1, 2, 0), (5, 0, 1, 2)]:
+        rc = L.overlap_search_approx(ctx.handle, ctypes.c_void_p(d.data_ptr()), d.numel(), lmin, num, den, both,
+                                     ctypes.c_void_p(edges.data_ptr()), 16, ctypes.byref(n), ctypes.byref(mo),
+                                     None)
+        assert rc == B().INVALID_ARG
+    rc = L.overlap_search_approx(ctx.handle, ctypes.c_void_p(t.ctypes.data), t.size, 3, 0, 1, 0,
+                                 ctypes.c_void_p(edges.data_ptr()), 16, ctypes.byref(n), ctypes.byref(mo), None)
+    assert rc == B().INVALID_ARG
+    # a single fragment has no partner on either strand
+    one = np.frombuffer(b"ACGTTGCAACGT$", np.uint8).copy()
+    g1, m1 = B().overlap_search_approx(ctx, torch.from_numpy(one).cuda(), 3, 0, 1, True)
+    assert g1.shape[0] == 0 and m1 == 2

@@ -86,3 +86,37 @@ def test_batched_mix_equals_oracle(ctx):
         assert (st, steps) == (ost, osteps), i
         assert np.array_equal(start, ostart), i
         assert rs == ors, i
+
+
+def test_capacity_and_argument_errors(ctx):
+    """Undersized outputs report DNASA_CAPACITY with the size needed; bad
+    arguments and host pointers are refused before any launch."""
+    import ctypes
+
+    d = synth.two_cut(77, 6_000, mean_len=300)
+    text = torch.from_numpy(d["text"]).cuda()
+    nf = int((d["text"] == ord("$")).sum())
+    start = torch.empty(nf, dtype=torch.int64, device="cuda")
+    rs = torch.empty(10, dtype=torch.uint8, device="cuda")          # far too small
+    rl, st, steps = ctypes.c_int64(0), ctypes.c_int32(0), ctypes.c_int64(0)
+    L = B().lib()
+    rc = L.fir_reconstruct(ctx.handle, ctypes.c_void_p(text.data_ptr()), text.numel(), 1 << 30,
+                           ctypes.c_void_p(start.data_ptr()), nf, ctypes.c_void_p(rs.data_ptr()), rs.numel(),
+                           ctypes.byref(rl), ctypes.byref(st), ctypes.byref(steps), None)
+    assert rc == B().CAPACITY and rl.value == d["genome"].size
+    rc = L.fir_reconstruct(ctx.handle, ctypes.c_void_p(text.data_ptr()), text.numel(), 1 << 30,
+                           ctypes.c_void_p(start.data_ptr()), nf - 1, ctypes.c_void_p(rs.data_ptr()),
+                           rs.numel(), ctypes.byref(rl), ctypes.byref(st), ctypes.byref(steps), None)
+    assert rc == B().CAPACITY
+    host = np.zeros(nf, dtype=np.int64)
+    rc = L.fir_reconstruct(ctx.handle, ctypes.c_void_p(text.data_ptr()), text.numel(), 1 << 30,
+                           ctypes.c_void_p(host.ctypes.data), nf, ctypes.c_void_p(rs.data_ptr()), rs.numel(),
+                           ctypes.byref(rl), ctypes.byref(st), ctypes.byref(steps), None)
+    assert rc == B().INVALID_ARG
+    rc = L.fir_reconstruct(ctx.handle, ctypes.c_void_p(text.data_ptr()), text.numel(), 0,
+                           ctypes.c_void_p(start.data_ptr()), nf, ctypes.c_void_p(rs.data_ptr()), rs.numel(),
+                           ctypes.byref(rl), ctypes.byref(st), ctypes.byref(steps), None)
+    assert rc == B().INVALID_ARG
+    # the context still works afterwards
+    st2, rs2 = check_one(ctx, d["text"])
+    assert st2 == B().FIR_SOLVED and rs2 == d["genome"].tobytes()
