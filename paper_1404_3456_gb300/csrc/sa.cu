@@ -903,6 +903,33 @@ __device__ __forceinline__ unsigned long long shfl_xor_u64(unsigned long long x,
     return ((unsigned long long)hi << 32) | lo;
 }
 
+// A group whose members sit at the positions i, i+p, ..., i+(n-1)p of one arithmetic
+// progression with p <= h (h: the number of symbols every member shares) lies in a
+// periodic stretch of the text: T[x] = T[x+p] for every x from i up to past
+// i+(n-1)p+h.  Any two members first differ at the same text position e, where that
+// period breaks, and compare there as T[e] against T[e-p]; the whole group is
+// therefore in position order or in the reverse order.  The last two members
+// (max-p, max) tell which: they agree beyond their first h symbols, so they compare
+// as the suffixes h further on, and those two differ within their first h symbols
+// (max+p is not a member, so the period breaks before max+p+h), so their h-ranks
+// rank[max-p+h] and rank[max+h], gathered as the members' low key parts, differ and
+// order them.  Such a group is ordered at once instead of log2(run length / h) rounds
+// later: the suffixes of one phase of a tandem array.  ap_period() returns p, or 0
+// when the positions are not such a progression.
+__device__ __forceinline__ uint32_t ap_period(uint32_t pmin, uint32_t pmax, int n, uint32_t h) {
+    if (n < 3) return 0;   // two members: their low key parts already differ if it applies
+    const uint32_t d = pmax - pmin;
+    if (d % (uint32_t)(n - 1) != 0) return 0;
+    const uint32_t p = d / (uint32_t)(n - 1);
+    return p <= h ? p : 0;
+}
+
+// Index of a member within an arithmetic-progression group in suffix order.
+__device__ __forceinline__ uint32_t ap_index(uint32_t pos, uint32_t pmin, uint32_t pmax, uint32_t p,
+                                             bool ascending) {
+    return (ascending ? pos - pmin : pmax - pos) / p;
+}
+
 // Splits the group list into five lists by size (<= 8, <= 32, <= kSegWarpMax,
 // <= seg_max, larger), one atomic per warp and list.
 __global__ void __launch_bounds__(256) k_classify(const uint2 *__restrict__ groups, int64_t ng,
@@ -934,7 +961,7 @@ __global__ void __launch_bounds__(256) k_classify(const uint2 *__restrict__ grou
 // Groups of at most 8 members: one thread each, insertion sort in registers.
 __global__ void __launch_bounds__(256) k_seg_thread(const uint2 *__restrict__ groups,
                                                     const unsigned long long *__restrict__ d_ng,
-                                                    int b, unsigned long long *__restrict__ keys,
+                                                    int b, uint32_t h, unsigned long long *__restrict__ keys,
                                                     uint32_t *__restrict__ vals) {
     const int64_t ng = (int64_t)*d_ng;
     const unsigned long long rmask = (1ull << b) - 1ull;
@@ -944,9 +971,38 @@ __global__ void __launch_bounds__(256) k_seg_thread(const uint2 *__restrict__ gr
         const int n = (int)gs.y;   // 2..8
         const unsigned long long hi = keys[gs.x] & ~rmask;
         unsigned long long w[8];
+        uint32_t pmin = ~0u, pmax = 0u;
 #pragma unroll
-        for (int i = 0; i < 8; ++i)
+        for (int i = 0; i < 8; ++i) {
             w[i] = i < n ? seg_word(keys[gs.x + i], vals[gs.x + i], rmask) : ~0ull;
+            if (i < n) {
+                pmin = min(pmin, (uint32_t)w[i]);
+                pmax = max(pmax, (uint32_t)w[i]);
+            }
+        }
+        if (const uint32_t p = ap_period(pmin, pmax, n, h)) {
+            bool ok = true;
+            uint32_t kmax = 0, kprev = 0;
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+                if (i < n) {
+                    const uint32_t v = (uint32_t)w[i];
+                    ok = ok && (v - pmin) % p == 0;
+                    if (v == pmax) kmax = (uint32_t)(w[i] >> 32);
+                    if (v == pmax - p) kprev = (uint32_t)(w[i] >> 32);
+                }
+            if (ok && kmax != kprev) {
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+                    if (i < n) {
+                        const uint32_t v = (uint32_t)w[i];
+                        const uint32_t j = ap_index(v, pmin, pmax, p, kprev < kmax);
+                        keys[gs.x + j] = hi | j;
+                        vals[gs.x + j] = v;
+                    }
+                continue;
+            }
+        }
 #pragma unroll
         for (int i = 1; i < 8; ++i) {
 #pragma unroll
@@ -1003,20 +1059,52 @@ __device__ __forceinline__ void warp_bitonic(unsigned long long (&w)[E], int lan
 
 template <int E>
 __device__ __forceinline__ void warp_sort_group(uint2 gs, int lane, int n2, unsigned long long rmask,
-                                                unsigned long long *__restrict__ keys,
+                                                uint32_t h, unsigned long long *__restrict__ keys,
                                                 uint32_t *__restrict__ vals) {
     const int n = (int)gs.y;
     const unsigned long long k0 = keys[gs.x];
     const unsigned long long hi = k0 & ~rmask;
     unsigned long long w[E];
     uint32_t x = 0;   // bits in which some rank differs from the first
+    uint32_t pmin = ~0u, pmax = 0u;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
         const int i = e * 32 + lane;
         w[e] = i < n ? seg_word(keys[gs.x + i], vals[gs.x + i], rmask) : ~0ull;
-        if (i < n) x |= (uint32_t)(w[e] >> 32) ^ (uint32_t)(k0 & rmask);
+        if (i < n) {
+            x |= (uint32_t)(w[e] >> 32) ^ (uint32_t)(k0 & rmask);
+            pmin = min(pmin, (uint32_t)w[e]);
+            pmax = max(pmax, (uint32_t)w[e]);
+        }
     }
     if (!__any_sync(0xffffffffu, x != 0)) return;   // one rank for all: already in order
+    pmin = __reduce_min_sync(0xffffffffu, pmin);
+    pmax = __reduce_max_sync(0xffffffffu, pmax);
+    if (const uint32_t p = ap_period(pmin, pmax, n, h)) {   // warp-uniform
+        bool ok = true;
+        uint32_t kmax = 0, kprev = 0;
+#pragma unroll
+        for (int e = 0; e < E; ++e)
+            if (e * 32 + lane < n) {
+                const uint32_t v = (uint32_t)w[e];
+                ok = ok && (v - pmin) % p == 0;
+                if (v == pmax) kmax = (uint32_t)(w[e] >> 32);
+                if (v == pmax - p) kprev = (uint32_t)(w[e] >> 32);
+            }
+        kmax = __reduce_or_sync(0xffffffffu, kmax);     // one lane holds each
+        kprev = __reduce_or_sync(0xffffffffu, kprev);
+        if (__all_sync(0xffffffffu, ok) && kmax != kprev) {
+#pragma unroll
+            for (int e = 0; e < E; ++e)
+                if (e * 32 + lane < n) {
+                    const uint32_t v = (uint32_t)w[e];
+                    const uint32_t j = ap_index(v, pmin, pmax, p, kprev < kmax);
+                    keys[gs.x + j] = hi | j;
+                    vals[gs.x + j] = v;
+                }
+            return;
+        }
+    }
     warp_bitonic<E>(w, lane, n2);
 #pragma unroll
     for (int e = 0; e < E; ++e) {
@@ -1032,7 +1120,7 @@ __device__ __forceinline__ void warp_sort_group(uint2 gs, int lane, int n2, unsi
 // (one per lane up to 32 members; 2, 4 or 8 per lane above).
 __global__ void __launch_bounds__(256) k_seg_warp(const uint2 *__restrict__ groups,
                                                   const unsigned long long *__restrict__ d_ng, int b,
-                                                  unsigned long long *__restrict__ keys,
+                                                  uint32_t h, unsigned long long *__restrict__ keys,
                                                   uint32_t *__restrict__ vals) {
     const int lane = threadIdx.x & 31;
     const int64_t ng = (int64_t)*d_ng;
@@ -1043,10 +1131,10 @@ __global__ void __launch_bounds__(256) k_seg_warp(const uint2 *__restrict__ grou
         const int n = (int)gs.y;
         int n2 = 2;
         while (n2 < n) n2 <<= 1;   // network only as wide as the group
-        if (n2 <= 32) warp_sort_group<1>(gs, lane, n2, rmask, keys, vals);
-        else if (n2 <= 64) warp_sort_group<2>(gs, lane, n2, rmask, keys, vals);
-        else if (n2 <= 128) warp_sort_group<4>(gs, lane, n2, rmask, keys, vals);
-        else warp_sort_group<8>(gs, lane, n2, rmask, keys, vals);
+        if (n2 <= 32) warp_sort_group<1>(gs, lane, n2, rmask, h, keys, vals);
+        else if (n2 <= 64) warp_sort_group<2>(gs, lane, n2, rmask, h, keys, vals);
+        else if (n2 <= 128) warp_sort_group<4>(gs, lane, n2, rmask, h, keys, vals);
+        else warp_sort_group<8>(gs, lane, n2, rmask, h, keys, vals);
     }
 }
 
@@ -1066,7 +1154,8 @@ constexpr size_t seg_radix_smem() {
 template <int ROWS>
 __global__ void __launch_bounds__(kSegThreads) k_seg_radix(const uint2 *__restrict__ groups,
                                                            const unsigned long long *__restrict__ d_ng,
-                                                           int b, unsigned long long *__restrict__ keys,
+                                                           int b, uint32_t h,
+                                                           unsigned long long *__restrict__ keys,
                                                            uint32_t *__restrict__ vals, uint32_t *err) {
     constexpr int NW = kSegRadixWarps, CAP = kSegThreads * ROWS;
     extern __shared__ __align__(16) unsigned char seg_raw[];
@@ -1074,6 +1163,7 @@ __global__ void __launch_bounds__(kSegThreads) k_seg_radix(const uint2 *__restri
     unsigned long long *buf1 = buf0 + CAP;
     uint32_t *wh = reinterpret_cast<uint32_t *>(buf1 + CAP);   // [NW][256] digit offsets
     __shared__ uint32_t s_tmp[NW + 1];
+    __shared__ uint32_t s_min[NW], s_max[NW], s_k[2];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t ng = (int64_t)*d_ng;
     const unsigned long long rmask = (1ull << b) - 1ull;
@@ -1088,22 +1178,57 @@ __global__ void __launch_bounds__(kSegThreads) k_seg_radix(const uint2 *__restri
         const unsigned long long hi = k0 & ~rmask;
         const uint32_t r0 = (uint32_t)(k0 & rmask);
         uint32_t x = 0;   // bits in which some rank differs from the first
+        uint32_t pmin = ~0u, pmax = 0u;
         for (int i = tid; i < n; i += kSegThreads) {
             const unsigned long long k = keys[gs.x + i];
-            buf0[i] = seg_word(k, vals[gs.x + i], rmask);
+            const uint32_t v = vals[gs.x + i];
+            buf0[i] = seg_word(k, v, rmask);
             x |= (uint32_t)(k & rmask) ^ r0;
+            pmin = min(pmin, v);
+            pmax = max(pmax, v);
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) x |= __shfl_xor_sync(0xffffffffu, x, o);
-        if (lane == 0) s_tmp[warp] = x;
+        x = __reduce_or_sync(0xffffffffu, x);
+        pmin = __reduce_min_sync(0xffffffffu, pmin);
+        pmax = __reduce_max_sync(0xffffffffu, pmax);
+        if (lane == 0) {
+            s_tmp[warp] = x;
+            s_min[warp] = pmin;
+            s_max[warp] = pmax;
+        }
         __syncthreads();
         x = 0;
 #pragma unroll
-        for (int w = 0; w < NW; ++w) x |= s_tmp[w];
+        for (int w = 0; w < NW; ++w) {
+            x |= s_tmp[w];
+            pmin = min(pmin, s_min[w]);
+            pmax = max(pmax, s_max[w]);
+        }
         const int passes = x ? (32 - __clz(x) + 7) / 8 : 0;
         if (passes == 0) {   // one rank for all: the group is already in order
             __syncthreads();
             continue;
+        }
+        if (const uint32_t p = ap_period(pmin, pmax, n, h)) {   // block-uniform
+            int ok = 1;
+            for (int i = tid; i < n; i += kSegThreads) {
+                const unsigned long long w = buf0[i];
+                const uint32_t v = (uint32_t)w;
+                ok &= (v - pmin) % p == 0;
+                if (v == pmax) s_k[0] = (uint32_t)(w >> 32);
+                if (v == pmax - p) s_k[1] = (uint32_t)(w >> 32);
+            }
+            ok = __syncthreads_and(ok);   // also publishes s_k
+            const uint32_t kmax = s_k[0], kprev = s_k[1];
+            if (ok && kmax != kprev) {
+                for (int i = tid; i < n; i += kSegThreads) {
+                    const uint32_t v = (uint32_t)buf0[i];
+                    const uint32_t j = ap_index(v, pmin, pmax, p, kprev < kmax);
+                    keys[gs.x + j] = hi | j;
+                    vals[gs.x + j] = v;
+                }
+                __syncthreads();
+                continue;
+            }
         }
         const int chunk = ((n + NW * 32 - 1) / (NW * 32)) * 32;   // warp slice, whole rows
         const int rows = chunk / 32;
@@ -1511,6 +1636,7 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
         }
         DNASA_CUDA(ctx, cudaGetLastError());
         // order every group by rank[i+h]: small groups on chip, large ones by radix
+        const uint32_t hs = (uint32_t)h;   // h < N < 2^32 here: the members share h symbols
         DNASA_CUDA(ctx, cudaMemsetAsync(cnt + CNT_SEG, 0, 5 * sizeof(unsigned long long), s));
         {
             LaunchScope ls_(ctx, PK_SEGSORT, s, 8.0 * ngroups);
@@ -1521,14 +1647,14 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
         {
             LaunchScope ls_(ctx, PK_SEGSORT, s, 24.0 * kept);
             int gt = (int)std::min<int64_t>(ceil_div(ngroups, 256), (int64_t)ctx->num_sms * 16);
-            k_seg_thread<<<std::max(gt, 1), 256, 0, s>>>(gtiny, cnt + CNT_SEG, b, keys[0], vals[0]);
+            k_seg_thread<<<std::max(gt, 1), 256, 0, s>>>(gtiny, cnt + CNT_SEG, b, hs, keys[0], vals[0]);
         }
         for (int cls = 1; cls <= 2; ++cls) {   // 9..32 and 33..kSegWarpMax members: a warp each
             if (maxgroup <= (cls == 1 ? 8 : 32) || seg_max <= (cls == 1 ? 8 : 32)) break;
             LaunchScope ls_(ctx, PK_SEGSORT, s, 0.0);
             int gw = (int)std::min<int64_t>(ceil_div(ngroups, 8), (int64_t)ctx->num_sms * 16);
             k_seg_warp<<<std::max(gw, 1), 256, 0, s>>>(cls == 1 ? gsmall : gwmid, cnt + CNT_SEG + cls, b,
-                                                       keys[0], vals[0]);
+                                                       hs, keys[0], vals[0]);
         }
         if (maxgroup > kSegWarpMax && seg_max > kSegWarpMax) {
             const int64_t biggest = std::min<int64_t>(maxgroup, seg_max);
@@ -1536,8 +1662,8 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
             auto launch = [&](auto kern, size_t smem) {
                 const int per_sm = std::max(1, (int)((200u << 10) / smem));
                 const int gb = (int)std::min<int64_t>(ngroups, (int64_t)ctx->num_sms * per_sm);
-                kern<<<std::max(gb, 1), kSegThreads, smem, s>>>(gmid, cnt + CNT_SEG + 3, b, keys[0], vals[0],
-                                                                &c->err);
+                kern<<<std::max(gb, 1), kSegThreads, smem, s>>>(gmid, cnt + CNT_SEG + 3, b, hs, keys[0],
+                                                                vals[0], &c->err);
             };
             if (biggest <= kSegThreads * 4) launch(k_seg_radix<4>, seg_radix_smem<4>());
             else if (biggest <= kSegThreads * 12) launch(k_seg_radix<12>, seg_radix_smem<12>());

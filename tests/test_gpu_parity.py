@@ -143,6 +143,57 @@ def test_sa_group_sort_tiers(ctx, seg_max):
     assert ctx.trace()["rounds"] >= 2
 
 
+def tandem_text(rng, arrays, flank=(0, 400), reads=1, end_with_array=True):
+    """Random flanks around tandem arrays (p, c, name): c copies of a unit of p
+    bases, one unit per name (arrays of one name repeat one unit); several reads
+    if asked, the last array of each read running up to its '$' unless
+    end_with_array is False."""
+    parts = [[] for _ in range(reads)]
+    units = {}
+    for k, (p, c, name) in enumerate(arrays):
+        if name not in units:
+            units[name] = synth.iid(rng, p)
+        r = k % reads
+        parts[r].append(synth.iid(rng, int(rng.integers(flank[0], flank[1] + 1))))
+        parts[r].append(np.tile(units[name], c))
+    if not end_with_array:
+        for r in range(reads):
+            parts[r].append(synth.iid(rng, 50))
+    return synth.join_reads([np.concatenate(x) if x else synth.iid(rng, 10) for x in parts])
+
+
+# (unit length, copies, unit name): phase groups of 3..8, 9..32, 33..256 and 257..6000
+# members, periods below and above the initial key length, a homopolymer, and one
+# unit in two arrays (its phase groups are then no single progression)
+TANDEM_ARRAYS = [(1, 40, "a"), (2, 6, "b"), (3, 50, "c"), (5, 400, "d"), (7, 1000, "e"),
+                 (19, 20, "f"), (20, 300, "g"), (33, 40, "h"), (50, 12, "i"), (64, 100, "j"),
+                 (2, 3000, "k"), (4, 8, "l"), (11, 200, "m"), (7, 700, "e")]
+
+
+@pytest.mark.parametrize("seg_max", [8, 256, 12288])
+@pytest.mark.parametrize("reads,end_with_array", [(1, True), (1, False), (5, True), (5, False)])
+def test_sa_tandem_progressions(ctx, seg_max, reads, end_with_array):
+    """Groups whose members form one arithmetic progression (a phase of a tandem
+    array) are ordered at once in every on-chip tier; the SA equals the oracle's."""
+    rng = np.random.default_rng(31 + reads)
+    t = tandem_text(rng, TANDEM_ARRAYS, reads=reads, end_with_array=end_with_array)
+    sa = gpu_sa(ctx, t, opts=B().make_opts(finish_threshold=-1, seg_max=seg_max))[0]
+    assert np.array_equal(sa.cpu().numpy().astype(np.int64), oracle.suffix_array(t))
+
+
+def test_sa_tandem_rounds(ctx):
+    """One 21,000 bp array of a 7 bp unit: its phase groups are progressions with
+    p = 7 below the initial key length, so they are ordered in the first doubling
+    round instead of log2(21,000 / h0) rounds later."""
+    rng = np.random.default_rng(5)
+    g = np.concatenate([synth.iid(rng, 200), np.tile(synth.iid(rng, 7), 3000), synth.iid(rng, 200)])
+    t = synth.genome_text(g)
+    sa = gpu_sa(ctx, t, opts=B().make_opts(finish_threshold=-1))[0]
+    assert np.array_equal(sa.cpu().numpy().astype(np.int64), oracle.suffix_array(t))
+    tr = ctx.trace()
+    assert tr["h0"] >= 7 and tr["rounds"] <= 2, tr
+
+
 @pytest.mark.parametrize("pack", [0, -1])
 @pytest.mark.parametrize("seed,n_reads,lo,hi", [(21, 1, 300_001, 300_001), (22, 700, 1, 900)])
 def test_sa_packed_and_pair_initial_sort(ctx, pack, seed, n_reads, lo, hi):
