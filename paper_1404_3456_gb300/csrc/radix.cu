@@ -183,7 +183,10 @@ __device__ __forceinline__ void onesweep_tile(
         const uint32_t peers = match_digit(d, vmask);
         const int leader = __ffs(peers) - 1;   // valid lanes: peers holds the lane itself
         uint32_t old = 0;
-        if (valid && lane == leader) old = atomicAdd(&wh[d], (uint32_t)__popc(peers));
+        if (valid && lane == leader) {   // the leaders of one ballot hold distinct digits
+            old = wh[d];
+            wh[d] = old + (uint32_t)__popc(peers);
+        }
         old = __shfl_sync(0xffffffffu, old, leader < 0 ? 0 : leader);
         dl[i] = d | ((old + __popc(peers & lanemask_lt())) << kRadixBits);
         __syncwarp();
