@@ -439,7 +439,8 @@ __device__ __forceinline__ bool own_head(unsigned long long k, unsigned long lon
 struct OwnSmem {
     unsigned long long k[kR0Tile + 2];   // compared keys, one halo key on each side
     uint32_t v[kR0Tile];                 // positions
-    uint32_t hd[kR0Tile];                // rank of each owned item
+    uint32_t hd[kR0Tile + kR0Tile / 32]; // rank of each owned item, item li at li + li / 32 (the
+                                         // blocked writes, 8 items per thread, hit distinct banks)
     uint32_t hb[kR0Tile / 32];           // bit l of word w: item 32w + l starts a group
     uint32_t nb[kR0Tile / 32];           // ... the item after it starts one (or the data end)
     int64_t tmp[kR0Threads / 32 + 1];
@@ -493,7 +494,7 @@ __device__ __forceinline__ void own_load(const unsigned long long *__restrict__ 
     r0_decode(keys[j], o.pb ? 0u : vals[j], o, h0, key, pos);
 }
 
-__global__ void __launch_bounds__(kR0Threads) k_rerank0(const unsigned long long *__restrict__ keys,
+__global__ void __launch_bounds__(kR0Threads, 5) k_rerank0(const unsigned long long *__restrict__ keys,
                                                         const uint32_t *__restrict__ vals, int64_t n, int h0,
                                                         RerankOut o, uint32_t *err) {
     __shared__ OwnSmem S;
@@ -502,18 +503,46 @@ __global__ void __launch_bounds__(kR0Threads) k_rerank0(const unsigned long long
     if (base >= n) return;
     const int tile_n = (int)min((int64_t)kR0Tile, n - base);
 
-    // ---- keys (one halo each side) and positions; SA of the tile's items
-    for (int i = tid; i < tile_n + 2; i += kR0Threads) {
-        const int64_t j = base - 1 + i;
-        unsigned long long key = 0;
-        uint32_t pos = 0;
-        if (j >= 0 && j < n) own_load(keys, vals, j, o, h0, &key, &pos);
-        else r0_decode(0ull, 0u, o, h0, &key, &pos);
-        S.k[i] = key;
-        if (i >= 1 && i <= tile_n) {
-            S.v[i - 1] = pos;
-            if ((int64_t)pos < o.N) o.sa[j] = pos;
+    // ---- keys (one halo each side) and positions; SA of the tile's items.  All
+    // of a thread's loads are issued before its first store (the SA store could
+    // alias the keys as far as the compiler knows, which would serialise them).
+    {
+        unsigned long long w[kR0Items];
+        uint32_t vv[kR0Items];
+#pragma unroll
+        for (int q = 0; q < kR0Items; ++q) {
+            const int i = tid + q * kR0Threads;
+            w[q] = i < tile_n ? keys[base + i] : 0ull;
+            vv[q] = (i < tile_n && !o.pb) ? vals[base + i] : 0u;
+        }
+        int64_t hj = -1;   // threads 0 and 1: the halo items before and after the tile
+        unsigned long long hw = 0;
+        uint32_t hv = 0;
+        if (tid < 2) {
+            hj = tid == 0 ? base - 1 : base + tile_n;
+            if (hj >= 0 && hj < n) {
+                hw = keys[hj];
+                hv = o.pb ? 0u : vals[hj];
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < kR0Items; ++q) {
+            const int i = tid + q * kR0Threads;
+            if (i >= tile_n) break;
+            unsigned long long key;
+            uint32_t pos;
+            r0_decode(w[q], vv[q], o, h0, &key, &pos);
+            S.k[i + 1] = key;
+            S.v[i] = pos;
+            if ((int64_t)pos < o.N) o.sa[base + i] = pos;
             else atomicOr(err, DERR_BOUNDS);
+        }
+        if (tid < 2) {   // outside [0, n): the decode of a zero word, as a neighbour only
+            unsigned long long key;
+            uint32_t pos;
+            if (hj >= 0 && hj < n) r0_decode(hw, hv, o, h0, &key, &pos);
+            else r0_decode(0ull, 0u, o, h0, &key, &pos);
+            S.k[tid == 0 ? 0 : tile_n + 1] = key;
         }
     }
     __syncthreads();
@@ -649,7 +678,7 @@ __global__ void __launch_bounds__(kR0Threads) k_rerank0(const unsigned long long
             const int64_t j = base + li;
             if ((headbits >> i) & 1u) cur = j;
             const uint32_t rk = (uint32_t)cur;
-            S.hd[li] = rk;
+            S.hd[li + (li >> 5)] = rk;
             if ((keepbits >> i) & 1u) {
                 if (kp >= (unsigned long long)n) {
                     atomicOr(err, DERR_BOUNDS);
@@ -673,11 +702,11 @@ __global__ void __launch_bounds__(kR0Threads) k_rerank0(const unsigned long long
     }
     __syncthreads();
     // ---- ranks of the owned items in the tile
-    own_stage(S, o, tile_n, [&](int i) { return S.v[i]; }, [&](int i) { return S.hd[i]; },
+    own_stage(S, o, tile_n, [&](int i) { return S.v[i]; }, [&](int i) { return S.hd[i + (i >> 5)]; },
               [&](int i) { return i >= fh; }, err);
     if (spill <= 0) return;
     // ---- the last group continues past the tile: all of it kept, one rank
-    const uint32_t rk = S.hd[tile_n - 1];
+    const uint32_t rk = S.hd[(tile_n - 1) + ((tile_n - 1) >> 5)];
     const unsigned long long kps = kp0 + (unsigned long long)tile_keep;
     for (int64_t c0 = base + tile_n; c0 < S.own_end; c0 += kR0Tile) {
         const int cnt = (int)min((int64_t)kR0Tile, S.own_end - c0);
