@@ -240,7 +240,9 @@ def pctl(xs, q):
     return xs[k]
 
 
-ROOF_TIMING = "per-launch CUDA events on the launching stream, second pass of the same K steps"
+ROOF_TIMING = ("per-launch CUDA events on the launching stream, second pass of the same K steps "
+               "(with per-launch events the doubling rounds run from the host, not inside the "
+               "captured graph the timed steps use)")
 
 
 def traffic_ratio(kind: str):
@@ -1016,7 +1018,8 @@ def main():
                                 f"(N = {N:,} suffixes), int32 SA and LCP"),
                    "genome_bp": N - 1, "seed": args.seed, "parallelism": f"replicas{world}",
                    "l2": "working set >> L2 (no flush needed)",
-                   "rounds": trace["rounds"], "finished_direct": trace["finished_direct"],
+                   "rounds": trace["rounds"], "graph_rounds": trace.get("graph_rounds", 0),
+                   "finished_direct": trace["finished_direct"],
                    "active_per_round": trace["active"], "sa_only_ms": sa_only_ms,
                    "autotuned": tuned, "builder": args.builder,
                    **({"dc3_levels": trace["rounds"]} if args.builder == "dc3" else {}),

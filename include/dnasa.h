@@ -99,6 +99,17 @@ typedef struct {
                                   i+1) and a merge; same suffix array; one instance only
                                   (sa_build_batched refuses it); the other options are
                                   ignored */
+    int32_t rounds_on_host;    /* 0 (default): after round 0 the doubling rounds run as one
+                                  captured CUDA graph -- a device-side loop (a WHILE node,
+                                  two rounds per pass) whose kernels read their counts from
+                                  device memory, so the stream is synchronized after round 0
+                                  and at the end only -- whenever profiling is off, the
+                                  direct-comparison finisher is off and every group fits
+                                  the on-chip sorts (seg_max); rounds outside those
+                                  conditions run from the host.  The graph is kept in the
+                                  context and captured again when the buffers or sizes
+                                  change.  1: every round from the host, which reads three
+                                  counters back after each */
 } dnasa_opts;
 
 /* One suffix-prefix overlap: the last L bases of fragment j equal the first L
@@ -120,6 +131,8 @@ typedef struct {
     int32_t h0;                /* symbols in the initial packed key */
     int32_t pack_bits;         /* position bits packed under the initial key (0: pairs) */
     int64_t active[64];        /* unsorted suffixes after the initial sort and each round */
+    int32_t graph_rounds;      /* rounds of those run inside the captured graph */
+    int32_t reserved;
 } dnasa_trace;
 
 /* ---- context --------------------------------------------------------------- */
@@ -241,7 +254,8 @@ int dnasa_pack(dnasa_ctx *ctx, const uint8_t *text, int64_t N, uint64_t *packed,
  *   sa             device, N entries of int32 or int64 (idx_width): sa[j] is
  *                  the text position of the j-th smallest suffix
  *   opts           host, may be NULL (defaults)
- * Enqueues on the stream and synchronizes it once per doubling round. */
+ * Enqueues on the stream; synchronizes it after round 0 and at the end when the
+ * doubling rounds run as a graph (rounds_on_host), else once per round. */
 int sa_build(dnasa_ctx *ctx, const uint64_t *packed, const int64_t *toff, int64_t n_reads,
              int64_t N, void *sa, int idx_width, const dnasa_opts *opts, void *stream);
 

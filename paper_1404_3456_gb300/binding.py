@@ -34,13 +34,15 @@ class Opts(ctypes.Structure):
     _fields_ = [("reserved0", ctypes.c_int32), ("tile_items", ctypes.c_int32),
                 ("finish_threshold", ctypes.c_int64), ("max_rounds", ctypes.c_int32),
                 ("lookback", ctypes.c_int32), ("seg_max", ctypes.c_int32),
-                ("pack_position", ctypes.c_int32), ("builder", ctypes.c_int32)]
+                ("pack_position", ctypes.c_int32), ("builder", ctypes.c_int32),
+                ("rounds_on_host", ctypes.c_int32)]
 
 
 class Trace(ctypes.Structure):
     _fields_ = [("rounds", ctypes.c_int32), ("finished_direct", ctypes.c_int32),
                 ("h0", ctypes.c_int32), ("pack_bits", ctypes.c_int32),
-                ("active", ctypes.c_int64 * 64)]
+                ("active", ctypes.c_int64 * 64), ("graph_rounds", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class ProfEntry(ctypes.Structure):
@@ -169,7 +171,8 @@ class Context:
         tr = Trace()
         self.check(lib().dnasa_get_trace(self.handle, ctypes.byref(tr)))
         return dict(rounds=tr.rounds, finished_direct=tr.finished_direct, h0=tr.h0,
-                    pack_bits=tr.pack_bits, active=list(tr.active[: tr.rounds + 1]))
+                    pack_bits=tr.pack_bits, active=list(tr.active[: tr.rounds + 1]),
+                    graph_rounds=tr.graph_rounds)
 
     def profile(self, enable: bool = True):
         """Start (or stop) recording CUDA events around every kernel launch."""
@@ -199,9 +202,9 @@ class Context:
 
 
 def make_opts(reserved0=0, tile_items=0, finish_threshold=0, max_rounds=0, lookback=0, seg_max=0,
-              pack_position=0, builder=0):
+              pack_position=0, builder=0, rounds_on_host=0):
     return Opts(reserved0, tile_items, finish_threshold, max_rounds, lookback, seg_max,
-                pack_position, builder)
+                pack_position, builder, rounds_on_host)
 
 
 # ---------------------------------------------------------------- entry points

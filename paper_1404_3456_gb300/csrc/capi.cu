@@ -218,6 +218,8 @@ int sa_build(dnasa_ctx *ctx, const uint64_t *packed, const int64_t *toff, int64_
         return fail(ctx, DNASA_INVALID_ARG, "sa_build: pack_position must be 0 or -1");
     if (opts && opts->builder != 0 && opts->builder != 1)
         return fail(ctx, DNASA_INVALID_ARG, "sa_build: builder must be 0 (doubling) or 1 (DC3)");
+    if (opts && opts->rounds_on_host != 0 && opts->rounds_on_host != 1)
+        return fail(ctx, DNASA_INVALID_ARG, "sa_build: rounds_on_host must be 0 or 1");
     cudaSetDevice(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
     TextDesc t = one_instance(packed, toff, n_reads, N);

@@ -79,6 +79,9 @@ struct dnasa_ctx {
     bool prof_on = false;
     std::vector<dnasa::ProfRec> prof;
     std::vector<cudaEvent_t> ev_pool;
+    // sa_build's doubling loop as a captured graph (owned by sa.cu; freed with the context)
+    void *sa_graph = nullptr;
+    void (*sa_graph_free)(void *) = nullptr;
 };
 
 namespace dnasa {

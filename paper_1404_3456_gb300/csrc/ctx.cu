@@ -370,6 +370,7 @@ int dnasa_create(int device, size_t workspace_cap, dnasa_ctx **out) {
 void dnasa_destroy(dnasa_ctx *ctx) {
     if (!ctx) return;
     cudaSetDevice(ctx->device);
+    if (ctx->sa_graph && ctx->sa_graph_free) ctx->sa_graph_free(ctx->sa_graph);
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->lb_buf) cudaFree(ctx->lb_buf);
     if (ctx->ctrl) cudaFree(ctx->ctrl);

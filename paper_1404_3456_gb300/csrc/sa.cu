@@ -20,6 +20,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <vector>
 
 #include "block.cuh"
 #include "common.cuh"
@@ -156,12 +157,13 @@ struct RerankSmem {
     int stop;
 };
 
-__global__ void __launch_bounds__(kRrThreads) k_rerank(
+// One tile of a doubling round's rerank: the next tile id from the counter (ids
+// are taken in order, so every tile a look-back waits on is held by a running
+// CTA).  Returns false when there is no tile left or the look-back gave up.
+__device__ __forceinline__ bool rerank_tile(RerankSmem &S,
     const unsigned long long *__restrict__ keys, const uint32_t *__restrict__ vals,
-    const uint32_t *__restrict__ slots, int64_t n_host, const unsigned long long *__restrict__ d_n,
-    int h0, RerankOut o, unsigned long long *status, uint32_t *tile_ctr, uint32_t *err) {
-    extern __shared__ __align__(16) unsigned char rr_raw[];
-    RerankSmem &S = *reinterpret_cast<RerankSmem *>(rr_raw);
+    const uint32_t *__restrict__ slots, int64_t n, const RerankOut &o,
+    unsigned long long *status, uint32_t *tile_ctr, uint32_t *err) {
     const int tid = threadIdx.x;
     if (tid == 0) {
         S.tile = atomicAdd(tile_ctr, 1u);
@@ -169,9 +171,8 @@ __global__ void __launch_bounds__(kRrThreads) k_rerank(
     }
     __syncthreads();
     const uint32_t tile = S.tile;
-    const int64_t n = d_n ? (int64_t)*d_n : n_host;
     const int64_t base = (int64_t)tile * kRrTile;
-    if (base >= n) return;
+    if (base >= n) return false;
     const int tile_n = (int)min((int64_t)kRrTile, n - base);
 
     // ---- striped, coalesced loads
@@ -306,7 +307,7 @@ __global__ void __launch_bounds__(kRrThreads) k_rerank(
         }
     }
     __syncthreads();
-    if (S.abort) return;   // prefix unknown: write nothing
+    if (S.abort) return false;   // prefix unknown: write nothing
     // ---- blocked: new rank and output index of every item.  A kept item that
     // ends its group records (first kept index, size) in the group list; the
     // list slots and the largest size are claimed with one atomic per warp.
@@ -393,6 +394,20 @@ __global__ void __launch_bounds__(kRrThreads) k_rerank(
             o.nhead[kp] = hs;
         }
     }
+    return true;
+}
+
+// A doubling round's rerank.  Persistent: each CTA takes tiles until none is
+// left, so any grid covers the items (n from d_n when given: the count the
+// previous round left on the device).
+__global__ void __launch_bounds__(kRrThreads) k_rerank(
+    const unsigned long long *__restrict__ keys, const uint32_t *__restrict__ vals,
+    const uint32_t *__restrict__ slots, int64_t n_host, const unsigned long long *__restrict__ d_n,
+    RerankOut o, unsigned long long *status, uint32_t *tile_ctr, uint32_t *err) {
+    extern __shared__ __align__(16) unsigned char rr_raw[];
+    RerankSmem &S = *reinterpret_cast<RerankSmem *>(rr_raw);
+    const int64_t n = d_n ? (int64_t)*d_n : n_host;
+    while (rerank_tile(S, keys, vals, slots, n, o, status, tile_ctr, err)) __syncthreads();
 }
 
 // ------------------------------------------------------------------ round 0 without a look-back
@@ -767,49 +782,58 @@ __global__ void __launch_bounds__(256) k_rank_apply(const uint2 *__restrict__ st
     }
     __syncthreads();
     const uint32_t total = s_off[nbuckets];
-    const uint32_t f0 = blockIdx.x * kApplyItems;
-    if (f0 >= total) return;
-    const uint32_t f1 = min(total, f0 + kApplyItems);
-    // first bucket holding flat index f0
-    int b = 0;
-    {
-        int lo = 0, hi = nbuckets - 1;
-        while (lo < hi) {
-            int m = (lo + hi + 1) >> 1;
-            if (s_off[m] <= f0) lo = m; else hi = m - 1;
+    // slices of kApplyItems staged pairs, grid-stride (one CTA per slice when the
+    // grid matches the items staged)
+    for (uint64_t g0 = (uint64_t)blockIdx.x * kApplyItems; g0 < total;
+         g0 += (uint64_t)gridDim.x * kApplyItems) {
+        const uint32_t f0 = (uint32_t)g0;
+        const uint32_t f1 = min(total, f0 + kApplyItems);
+        // first bucket holding flat index f0
+        int b = 0;
+        {
+            int lo = 0, hi = nbuckets - 1;
+            while (lo < hi) {
+                int m = (lo + hi + 1) >> 1;
+                if (s_off[m] <= f0) lo = m; else hi = m - 1;
+            }
+            b = lo;
         }
-        b = lo;
-    }
-    // all of a thread's staged pairs are loaded before any rank write, so that
-    // the loads are in flight together
-    constexpr int kPer = kApplyItems / 256;
-    uint2 pr[kPer];
-    int pb_[kPer];
+        // all of a thread's staged pairs are loaded before any rank write, so that
+        // the loads are in flight together
+        constexpr int kPer = kApplyItems / 256;
+        uint2 pr[kPer];
+        int pb_[kPer];
 #pragma unroll
-    for (int q = 0; q < kPer; ++q) {
-        const uint32_t f = f0 + threadIdx.x + q * 256;
-        pb_[q] = -1;
-        if (f < f1) {
-            while (f >= s_off[b + 1]) ++b;   // non-decreasing f per thread
-            pb_[q] = b;
-            pr[q] = stage[((uint64_t)b << bshift) + (f - s_off[b])];
+        for (int q = 0; q < kPer; ++q) {
+            const uint32_t f = f0 + threadIdx.x + q * 256;
+            pb_[q] = -1;
+            if (f < f1) {
+                while (f >= s_off[b + 1]) ++b;   // non-decreasing f per thread
+                pb_[q] = b;
+                pr[q] = stage[((uint64_t)b << bshift) + (f - s_off[b])];
+            }
         }
-    }
 #pragma unroll
-    for (int q = 0; q < kPer; ++q) {
-        if (pb_[q] < 0) continue;
-        if ((int64_t)pr[q].x < N && (pr[q].x >> bshift) == (uint32_t)pb_[q]) rank[pr[q].x] = pr[q].y;
-        else atomicOr(err, DERR_BOUNDS);
+        for (int q = 0; q < kPer; ++q) {
+            if (pb_[q] < 0) continue;
+            if ((int64_t)pr[q].x < N && (pr[q].x >> bshift) == (uint32_t)pb_[q]) rank[pr[q].x] = pr[q].y;
+            else atomicOr(err, DERR_BOUNDS);
+        }
     }
 }
 
 // ------------------------------------------------------------------ doubling gather
+// n and h from d_n / d_h when given (a device-driven round).
 __global__ void __launch_bounds__(256) k_gather(const uint32_t *__restrict__ npos,
-                                                const uint32_t *__restrict__ nhead, int64_t n,
-                                                const uint32_t *__restrict__ rank, uint32_t h,
+                                                const uint32_t *__restrict__ nhead, int64_t n_host,
+                                                const unsigned long long *__restrict__ d_n,
+                                                const uint32_t *__restrict__ rank, uint32_t h_host,
+                                                const uint32_t *__restrict__ d_h,
                                                 int b, unsigned long long *__restrict__ keys,
                                                 uint32_t *__restrict__ vals, int64_t N,
                                                 uint32_t *err) {
+    const int64_t n = d_n ? (int64_t)*d_n : n_host;
+    const uint32_t h = d_h ? *d_h : h_host;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
          t += (int64_t)gridDim.x * blockDim.x) {
         uint32_t pos = npos[t];
@@ -961,12 +985,14 @@ __device__ __forceinline__ uint32_t ap_index(uint32_t pos, uint32_t pmin, uint32
 
 // Splits the group list into five lists by size (<= 8, <= 32, <= kSegWarpMax,
 // <= seg_max, larger), one atomic per warp and list.
-__global__ void __launch_bounds__(256) k_classify(const uint2 *__restrict__ groups, int64_t ng,
+__global__ void __launch_bounds__(256) k_classify(const uint2 *__restrict__ groups, int64_t ng_host,
+                                                  const unsigned long long *__restrict__ d_ng,
                                                   int seg_max, uint2 *__restrict__ tiny,
                                                   uint2 *__restrict__ small, uint2 *__restrict__ wmid,
                                                   uint2 *__restrict__ mid, uint2 *__restrict__ large,
                                                   unsigned long long *__restrict__ counts) {
     const int lane = threadIdx.x & 31;
+    const int64_t ng = d_ng ? (int64_t)*d_ng : ng_host;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane; b < ng; b += stride) {
         const int64_t g = b + lane;
@@ -990,9 +1016,11 @@ __global__ void __launch_bounds__(256) k_classify(const uint2 *__restrict__ grou
 // Groups of at most 8 members: one thread each, insertion sort in registers.
 __global__ void __launch_bounds__(256) k_seg_thread(const uint2 *__restrict__ groups,
                                                     const unsigned long long *__restrict__ d_ng,
-                                                    int b, uint32_t h, unsigned long long *__restrict__ keys,
+                                                    int b, uint32_t h_host, const uint32_t *__restrict__ d_h,
+                                                    unsigned long long *__restrict__ keys,
                                                     uint32_t *__restrict__ vals) {
     const int64_t ng = (int64_t)*d_ng;
+    const uint32_t h = d_h ? *d_h : h_host;
     const unsigned long long rmask = (1ull << b) - 1ull;
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < ng;
          g += (int64_t)gridDim.x * blockDim.x) {
@@ -1149,10 +1177,12 @@ __device__ __forceinline__ void warp_sort_group(uint2 gs, int lane, int n2, unsi
 // (one per lane up to 32 members; 2, 4 or 8 per lane above).
 __global__ void __launch_bounds__(256) k_seg_warp(const uint2 *__restrict__ groups,
                                                   const unsigned long long *__restrict__ d_ng, int b,
-                                                  uint32_t h, unsigned long long *__restrict__ keys,
+                                                  uint32_t h_host, const uint32_t *__restrict__ d_h,
+                                                  unsigned long long *__restrict__ keys,
                                                   uint32_t *__restrict__ vals) {
     const int lane = threadIdx.x & 31;
     const int64_t ng = (int64_t)*d_ng;
+    const uint32_t h = d_h ? *d_h : h_host;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     const unsigned long long rmask = (1ull << b) - 1ull;
     for (int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < ng; g += nw) {
@@ -1183,8 +1213,9 @@ constexpr size_t seg_radix_smem() {
 template <int ROWS>
 __global__ void __launch_bounds__(kSegThreads) k_seg_radix(const uint2 *__restrict__ groups,
                                                            const unsigned long long *__restrict__ d_ng,
-                                                           int b, uint32_t h,
-                                                           unsigned long long *__restrict__ keys,
+                                                           int b, uint32_t h_host,
+                                                           const uint32_t *__restrict__ d_h, int min_n,
+                                                           int max_n, unsigned long long *__restrict__ keys,
                                                            uint32_t *__restrict__ vals, uint32_t *err) {
     constexpr int NW = kSegRadixWarps, CAP = kSegThreads * ROWS;
     extern __shared__ __align__(16) unsigned char seg_raw[];
@@ -1195,10 +1226,12 @@ __global__ void __launch_bounds__(kSegThreads) k_seg_radix(const uint2 *__restri
     __shared__ uint32_t s_min[NW], s_max[NW], s_k[2];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t ng = (int64_t)*d_ng;
+    const uint32_t h = d_h ? *d_h : h_host;
     const unsigned long long rmask = (1ull << b) - 1ull;
     for (int64_t g = blockIdx.x; g < ng; g += gridDim.x) {
         const uint2 gs = groups[g];
         const int n = (int)gs.y;
+        if (n <= min_n || n > max_n) continue;   // another variant's size class (device-driven rounds)
         if (n > CAP) {   // the host sizes ROWS for the list: never taken
             if (tid == 0) atomicOr(err, DERR_BOUNDS);
             continue;
@@ -1426,7 +1459,90 @@ __global__ void k_widen(const uint32_t *__restrict__ a, int64_t n, int64_t *__re
         b[i] = a[i];
 }
 
+// ------------------------------------------------------------------ device-driven rounds
+// The doubling rounds after round 0 can run as one captured CUDA graph: a WHILE
+// node whose body holds two rounds (the list buffers alternate between them),
+// with an IF node before the second.  Every launch of a round has a fixed grid
+// (grid-stride or persistent kernels) and takes its counts and h from RoundDev,
+// so the graph depends only on the buffers and sizes, and no count comes back to
+// the host between rounds.  k_round_check ends the loop when no suffix is left
+// active, when a group outgrows the on-chip sorts (the host then finishes the
+// rounds), after kDevRoundsMax rounds, when h would reach N, or on an error flag.
+constexpr int kDevRoundsMax = 59;
+
+struct RoundDev {   // 64 words: read back whole into the pinned buffer
+    unsigned long long kept, ngroups, maxgroup;   // the previous round's counts: this round's input
+    uint32_t h;                                   // symbols every group member shares
+    uint32_t round;                               // doubling rounds done
+    unsigned long long max_rounds;
+    unsigned long long active[59];                // trace: active suffixes after round r (index r - 1)
+};
+static_assert(sizeof(RoundDev) == 64 * 8, "one pinned read-back");
+
+// Start of a round: the counts the last rerank left become the round's inputs
+// (thread 0, before it clears them); the rerank's tile counter, look-back words
+// and rank-bucket fills are cleared.
+__global__ void k_round_begin(RoundDev *rd, unsigned long long *cnt, uint32_t *tile_ctr,
+                              unsigned long long *rr_status, int64_t rr_tiles, uint32_t *bucket_fill) {
+    const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    if (i0 == 0) {
+        rd->kept = cnt[CNT_ACTIVE];
+        rd->ngroups = cnt[CNT_GROUPS];
+        rd->maxgroup = cnt[CNT_MAXGROUP];
+        for (int k = 0; k < 4; ++k) cnt[k] = 0;
+        for (int k = 0; k < 5; ++k) cnt[CNT_SEG + k] = 0;
+        for (int k = 0; k < 4; ++k) tile_ctr[k] = 0;
+    }
+    for (int64_t i = i0; i < rr_tiles; i += stride) rr_status[i] = 0;
+    for (int64_t i = i0; i < kMaxBuckets; i += stride) bucket_fill[i] = 0;
+}
+
+// Sets up the loop state before the graph runs (outside it: per call values).
+__global__ void k_round_init(RoundDev *rd, uint32_t h0, int max_rounds) {
+    rd->h = h0;
+    rd->round = 0;
+    rd->max_rounds = (unsigned long long)min(max_rounds, kDevRoundsMax);
+}
+
+// End of a round: count it, double h, record the trace, and decide whether the
+// graph runs another round.  One thread sets the conditional handles.
+__global__ void k_round_check(RoundDev *rd, const unsigned long long *cnt, const uint32_t *err, int64_t N,
+                              int seg_max, cudaGraphConditionalHandle h_loop,
+                              cudaGraphConditionalHandle h_second, int first) {
+    const unsigned long long kept = cnt[CNT_ACTIVE], maxg = cnt[CNT_MAXGROUP];
+    rd->kept = kept;   // the round's outputs (the next round_begin copies the same)
+    rd->ngroups = cnt[CNT_GROUPS];
+    rd->maxgroup = maxg;
+    const uint32_t r = rd->round + 1;
+    rd->round = r;
+    if (r <= (uint32_t)kDevRoundsMax) rd->active[r - 1] = kept;
+    const uint64_t h2 = 2ull * rd->h;
+    rd->h = (uint32_t)min(h2, (uint64_t)0xffffffffu);
+    const bool go = kept > 0 && maxg <= (unsigned long long)seg_max && r < rd->max_rounds &&
+                    h2 < (uint64_t)N && *err == 0;
+    cudaGraphSetConditional(h_loop, go ? 1u : 0u);
+    if (first) cudaGraphSetConditional(h_second, go ? 1u : 0u);
+}
+
 }  // namespace
+
+// The captured doubling loop of one sa_build configuration (held by the context).
+struct SaGraph {
+    std::vector<unsigned long long> key;   // buffers and sizes the kernels were given
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t cs = nullptr;             // capture stream
+    int launches_per_round = 0;
+};
+
+static void sa_graph_free(void *p) {
+    SaGraph *g = static_cast<SaGraph *>(p);
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    if (g->cs) cudaStreamDestroy(g->cs);
+    delete g;
+}
 
 // Symbols in the initial key.  Enough that i.i.d. text leaves few suffixes
 // unsorted (4^h0 >= 32 * symbols per instance: expected colliding pairs at most
@@ -1484,6 +1600,7 @@ size_t sa_workspace_bytes(int64_t N, int tile_items) {
     for (int i = 0; i < 5; ++i) add((n / 2 + 1) * 8);   // group lists by size class
     add(compact_scratch_bytes(N));
     add(radix_scratch_bytes(N, 64, tile_items));
+    add(sizeof(RoundDev));                  // device-driven round state
     return need;
 }
 
@@ -1545,7 +1662,8 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
     unsigned long long *ck2 = a.take<unsigned long long>(n);
     uint32_t *cv2 = a.take<uint32_t>(n);
     RadixScratch rs = radix_scratch_take(a, N, 64, tile_items);
-    if (!rs.hist || !rr_status) return fail(ctx, DNASA_OOM, "sa_build workspace");
+    RoundDev *rd = a.take<RoundDev>(1);
+    if (!rs.hist || !rr_status || !rd) return fail(ctx, DNASA_OOM, "sa_build workspace");
 
     // dynamic shared-memory limits of this call's kernels, once per (kernel, device)
     DNASA_CUDA(ctx, smem_attr(k_rerank, sizeof(RerankSmem)));
@@ -1601,6 +1719,141 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
     ro.pb = pb;
     ro.single = single ? 1 : 0;
 
+    // ---- one doubling round with fixed grids and device-side counts (captured)
+    int rr_grid = 0;
+    {
+        int per_sm = 0;
+        DNASA_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_rerank, kRrThreads,
+                                                                      sizeof(RerankSmem)));
+        rr_grid = ctx->num_sms * std::max(per_sm, 1);
+    }
+    auto launch_round = [&](cudaStream_t cs, int cr) -> int {   // returns the launch count
+        const int G = ctx->num_sms * 16;
+        int nl = 0;
+        k_round_begin<<<ctx->num_sms, 256, 0, cs>>>(rd, cnt, c->tile_ctr + 32, rr_status, rr_tiles,
+                                                    bucket_fill);
+        k_gather<<<G, 256, 0, cs>>>(L[cr][1], L[cr][2], 0, &rd->kept, rank, 0u, &rd->h, b, keys[0], vals[0],
+                                    N, &c->err);
+        k_classify<<<G, 256, 0, cs>>>(groups, 0, &rd->ngroups, seg_max, gtiny, gsmall, gwmid, gmid, glarge,
+                                      cnt + CNT_SEG);
+        k_seg_thread<<<G, 256, 0, cs>>>(gtiny, cnt + CNT_SEG, b, 0u, &rd->h, keys[0], vals[0]);
+        k_seg_warp<<<G, 256, 0, cs>>>(gsmall, cnt + CNT_SEG + 1, b, 0u, &rd->h, keys[0], vals[0]);
+        k_seg_warp<<<G, 256, 0, cs>>>(gwmid, cnt + CNT_SEG + 2, b, 0u, &rd->h, keys[0], vals[0]);
+        nl += 6;
+        // each CTA-radix variant takes its own size class of the one list
+        auto radix = [&](auto kern, size_t smem, int lo, int hi) {
+            if (seg_max <= lo) return;
+            const int per_sm = std::max(1, (int)((200u << 10) / smem));
+            kern<<<ctx->num_sms * per_sm, kSegThreads, smem, cs>>>(gmid, cnt + CNT_SEG + 3, b, 0u, &rd->h, lo,
+                                                                    hi, keys[0], vals[0], &c->err);
+            ++nl;
+        };
+        radix(k_seg_radix<4>, seg_radix_smem<4>(), kSegWarpMax, kSegThreads * 4);
+        radix(k_seg_radix<12>, seg_radix_smem<12>(), kSegThreads * 4, kSegThreads * 12);
+        radix(k_seg_radix<24>, seg_radix_smem<24>(), kSegThreads * 12, kSegThreads * 24);
+        RerankOut r2 = ro;
+        r2.nslots = L[cr ^ 1][0];
+        r2.npos = L[cr ^ 1][1];
+        r2.nhead = L[cr ^ 1][2];
+        r2.stage = reinterpret_cast<uint2 *>(keys[1]);
+        k_rerank<<<rr_grid, kRrThreads, sizeof(RerankSmem), cs>>>(keys[0], vals[0], L[cr][0], 0, &rd->kept, r2,
+                                                                  rr_status, c->tile_ctr + 32, &c->err);
+        k_rank_apply<<<ctx->num_sms * 8, 256, 0, cs>>>(reinterpret_cast<const uint2 *>(keys[1]), bucket_fill,
+                                                       nbuckets, bshift, N, rank, &c->err);
+        return nl + 2;
+    };
+    // Runs the doubling rounds as the captured graph (captured on first use, or
+    // again when a buffer or size differs from the cached one); returns the
+    // rounds done and the counts the last one left.
+    auto device_rounds = [&](int *rounds, int64_t *kept, int64_t *ngroups, int64_t *maxgroup) -> int {
+        const std::vector<unsigned long long> key = {
+            (unsigned long long)N, (unsigned long long)b, (unsigned long long)seg_max,
+            (unsigned long long)bshift, (unsigned long long)nbuckets, (unsigned long long)rr_grid,
+            (unsigned long long)(uintptr_t)keys[0], (unsigned long long)(uintptr_t)keys[1],
+            (unsigned long long)(uintptr_t)vals[0], (unsigned long long)(uintptr_t)rank,
+            (unsigned long long)(uintptr_t)sa32, (unsigned long long)(uintptr_t)groups,
+            (unsigned long long)(uintptr_t)gtiny, (unsigned long long)(uintptr_t)gsmall,
+            (unsigned long long)(uintptr_t)gwmid, (unsigned long long)(uintptr_t)gmid,
+            (unsigned long long)(uintptr_t)glarge, (unsigned long long)(uintptr_t)L[0][0],
+            (unsigned long long)(uintptr_t)L[1][0], (unsigned long long)(uintptr_t)rr_status,
+            (unsigned long long)(uintptr_t)bucket_fill, (unsigned long long)(uintptr_t)rd,
+            (unsigned long long)(uintptr_t)c};
+        SaGraph *gph = static_cast<SaGraph *>(ctx->sa_graph);
+        if (!gph || gph->key != key) {
+            if (gph) sa_graph_free(gph);
+            gph = new SaGraph();
+            ctx->sa_graph = gph;
+            ctx->sa_graph_free = sa_graph_free;
+            auto drop = [&](cudaError_t e, const char *where) -> int {   // no half-built graph is kept
+                sa_graph_free(gph);
+                ctx->sa_graph = nullptr;
+                return cuda_fail(ctx, e, where);
+            };
+            cudaError_t e = cudaStreamCreateWithFlags(&gph->cs, cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaGraphCreate(&gph->graph, 0);
+            cudaGraphConditionalHandle h_loop = 0, h_second = 0;
+            if (e == cudaSuccess)
+                e = cudaGraphConditionalHandleCreate(&h_loop, gph->graph, 1, cudaGraphCondAssignDefault);
+            if (e == cudaSuccess)
+                e = cudaGraphConditionalHandleCreate(&h_second, gph->graph, 0, cudaGraphCondAssignDefault);
+            if (e != cudaSuccess) return drop(e, "sa_build: graph setup");
+            cudaGraphNodeParams wp = {};
+            wp.type = cudaGraphNodeTypeConditional;
+            wp.conditional.handle = h_loop;
+            wp.conditional.type = cudaGraphCondTypeWhile;
+            wp.conditional.size = 1;
+            cudaGraphNode_t wnode;
+            e = cudaGraphAddNode(&wnode, gph->graph, nullptr, nullptr, 0, &wp);
+            if (e != cudaSuccess) return drop(e, "sa_build: loop node");
+            cudaGraph_t body = wp.conditional.phGraph_out[0];
+            // pass body: round (lists 0 -> 1), check, IF node holding round (1 -> 0) and check
+            e = cudaStreamBeginCaptureToGraph(gph->cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+            if (e != cudaSuccess) return drop(e, "sa_build: capture");
+            gph->launches_per_round = launch_round(gph->cs, 0) + 1;
+            k_round_check<<<1, 1, 0, gph->cs>>>(rd, cnt, &c->err, N, seg_max, h_loop, h_second, 1);
+            cudaStreamCaptureStatus cst;
+            const cudaGraphNode_t *deps = nullptr;
+            size_t ndeps = 0;
+            e = cudaStreamGetCaptureInfo(gph->cs, &cst, nullptr, nullptr, &deps, nullptr, &ndeps);
+            cudaGraphNodeParams ip = {};
+            ip.type = cudaGraphNodeTypeConditional;
+            ip.conditional.handle = h_second;
+            ip.conditional.type = cudaGraphCondTypeIf;
+            ip.conditional.size = 1;
+            cudaGraphNode_t inode;
+            if (e == cudaSuccess) e = cudaGraphAddNode(&inode, body, deps, nullptr, ndeps, &ip);
+            cudaGraph_t captured = nullptr;
+            const cudaError_t e_end = cudaStreamEndCapture(gph->cs, &captured);
+            if (e == cudaSuccess) e = e_end;
+            if (e == cudaSuccess) e = cudaGetLastError();
+            if (e != cudaSuccess) return drop(e, "sa_build: first round capture");
+            e = cudaStreamBeginCaptureToGraph(gph->cs, ip.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                              cudaStreamCaptureModeThreadLocal);
+            if (e != cudaSuccess) return drop(e, "sa_build: capture");
+            launch_round(gph->cs, 1);
+            k_round_check<<<1, 1, 0, gph->cs>>>(rd, cnt, &c->err, N, seg_max, h_loop, h_second, 0);
+            e = cudaStreamEndCapture(gph->cs, &captured);
+            if (e == cudaSuccess) e = cudaGetLastError();
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&gph->exec, gph->graph, 0);
+            if (e != cudaSuccess) return drop(e, "sa_build: second round capture");
+            gph->key = key;
+        }
+        k_round_init<<<1, 1, 0, s>>>(rd, (uint32_t)h0, max_rounds);
+        DNASA_CUDA(ctx, cudaGetLastError());
+        DNASA_CUDA(ctx, cudaGraphLaunch(gph->exec, s));
+        DNASA_CUDA(ctx, cudaMemcpyAsync(ctx->pinned, rd, sizeof(RoundDev), cudaMemcpyDeviceToHost, s));
+        DNASA_TRY(check_device_status(ctx, s, "sa_build"));
+        RoundDev hr;
+        memcpy(&hr, (const void *)ctx->pinned, sizeof(hr));
+        *rounds = (int)hr.round;
+        *kept = (int64_t)hr.kept;
+        *ngroups = (int64_t)hr.ngroups;
+        *maxgroup = (int64_t)hr.maxgroup;
+        for (int r = 1; r <= *rounds && r <= kDevRoundsMax && r < 64; ++r) tr.active[r] = (int64_t)hr.active[r - 1];
+        ctx->launches += 1 + (unsigned long long)hr.round * (unsigned long long)gph->launches_per_round;
+        return DNASA_OK;
+    };
+
     // ---- round 0: initial keys, sort, rerank
     {
         const int passes0 = ceil_div(key_bits0, 8);
@@ -1636,6 +1889,16 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
     int cur = 0;
     uint64_t h = (uint64_t)h0;
     int round = 0;
+    if (kept > 0 && opts.rounds_on_host == 0 && finish_threshold < 0 && !ctx->prof_on &&
+        maxgroup <= seg_max && h < (uint64_t)N) {
+        int rounds = 0;
+        DNASA_TRY(device_rounds(&rounds, &kept, &ngroups, &maxgroup));
+        round = rounds;
+        cur = rounds & 1;
+        h = (uint64_t)h0 << rounds;
+        tr.rounds = rounds;
+        tr.graph_rounds = rounds;
+    }
     while (kept > 0) {
         if (finish_threshold >= 0 && kept <= finish_threshold && maxgroup <= kFinMax) {
             int grid = (int)std::min<int64_t>(ngroups, (int64_t)ctx->num_sms * 4);
@@ -1660,8 +1923,8 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
         int grid = (int)std::min<int64_t>(ceil_div(kept, 256), (int64_t)ctx->num_sms * 16);
         {
             LaunchScope ls_(ctx, PK_GATHER, s, 24.0 * kept);
-            k_gather<<<std::max(grid, 1), 256, 0, s>>>(L[cur][1], L[cur][2], kept, rank,
-                                                       (uint32_t)h, b, keys[0], vals[0], N, &c->err);
+            k_gather<<<std::max(grid, 1), 256, 0, s>>>(L[cur][1], L[cur][2], kept, nullptr, rank,
+                                                       (uint32_t)h, nullptr, b, keys[0], vals[0], N, &c->err);
         }
         DNASA_CUDA(ctx, cudaGetLastError());
         // order every group by rank[i+h]: small groups on chip, large ones by radix
@@ -1670,20 +1933,20 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
         {
             LaunchScope ls_(ctx, PK_SEGSORT, s, 8.0 * ngroups);
             int gc = (int)std::min<int64_t>(ceil_div(ngroups, 256), (int64_t)ctx->num_sms * 16);
-            k_classify<<<std::max(gc, 1), 256, 0, s>>>(groups, ngroups, seg_max, gtiny, gsmall, gwmid, gmid,
-                                                       glarge, cnt + CNT_SEG);
+            k_classify<<<std::max(gc, 1), 256, 0, s>>>(groups, ngroups, nullptr, seg_max, gtiny, gsmall, gwmid,
+                                                       gmid, glarge, cnt + CNT_SEG);
         }
         {
             LaunchScope ls_(ctx, PK_SEGSORT, s, 24.0 * kept);
             int gt = (int)std::min<int64_t>(ceil_div(ngroups, 256), (int64_t)ctx->num_sms * 16);
-            k_seg_thread<<<std::max(gt, 1), 256, 0, s>>>(gtiny, cnt + CNT_SEG, b, hs, keys[0], vals[0]);
+            k_seg_thread<<<std::max(gt, 1), 256, 0, s>>>(gtiny, cnt + CNT_SEG, b, hs, nullptr, keys[0], vals[0]);
         }
         for (int cls = 1; cls <= 2; ++cls) {   // 9..32 and 33..kSegWarpMax members: a warp each
             if (maxgroup <= (cls == 1 ? 8 : 32) || seg_max <= (cls == 1 ? 8 : 32)) break;
             LaunchScope ls_(ctx, PK_SEGSORT, s, 0.0);
             int gw = (int)std::min<int64_t>(ceil_div(ngroups, 8), (int64_t)ctx->num_sms * 16);
             k_seg_warp<<<std::max(gw, 1), 256, 0, s>>>(cls == 1 ? gsmall : gwmid, cnt + CNT_SEG + cls, b,
-                                                       hs, keys[0], vals[0]);
+                                                       hs, nullptr, keys[0], vals[0]);
         }
         if (maxgroup > kSegWarpMax && seg_max > kSegWarpMax) {
             const int64_t biggest = std::min<int64_t>(maxgroup, seg_max);
@@ -1691,8 +1954,8 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
             auto launch = [&](auto kern, size_t smem) {
                 const int per_sm = std::max(1, (int)((200u << 10) / smem));
                 const int gb = (int)std::min<int64_t>(ngroups, (int64_t)ctx->num_sms * per_sm);
-                kern<<<std::max(gb, 1), kSegThreads, smem, s>>>(gmid, cnt + CNT_SEG + 3, b, hs, keys[0],
-                                                                vals[0], &c->err);
+                kern<<<std::max(gb, 1), kSegThreads, smem, s>>>(gmid, cnt + CNT_SEG + 3, b, hs, nullptr, 0,
+                                                                0x7fffffff, keys[0], vals[0], &c->err);
             };
             if (biggest <= kSegThreads * 4) launch(k_seg_radix<4>, seg_radix_smem<4>());
             else if (biggest <= kSegThreads * 12) launch(k_seg_radix<12>, seg_radix_smem<12>());
@@ -1740,8 +2003,7 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
             // cross a tile boundary once most groups are a few dozen members
             LaunchScope ls_(ctx, PK_RERANK, s, 24.0 * kept);
             k_rerank<<<tiles, kRrThreads, sizeof(RerankSmem), s>>>(keys[0], vals[0], L[cur][0], kept,
-                                                         nullptr, h0, ro, rr_status, c->tile_ctr + 32,
-                                                         &c->err);
+                                                         nullptr, ro, rr_status, c->tile_ctr + 32, &c->err);
         }
         DNASA_CUDA(ctx, cudaGetLastError());
         DNASA_TRY(apply_ranks(kept, 1));

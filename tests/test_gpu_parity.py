@@ -194,6 +194,70 @@ def test_sa_tandem_rounds(ctx):
     assert tr["h0"] >= 7 and tr["rounds"] <= 2, tr
 
 
+GRAPH_TEXTS = ["repeat", "tandem", "multi", "tiny"]
+
+
+def graph_text(kind):
+    if kind == "repeat":
+        rng = synth.rng_for(7, 11)
+        return synth.genome_text(synth.genome_with_repeats(rng, 400_003, 0.05, (2, 50), (10, 200),
+                                                           0.05, 300, 0.01))
+    if kind == "tandem":
+        return tandem_text(np.random.default_rng(40), TANDEM_ARRAYS, reads=3)
+    if kind == "multi":
+        return random_text(np.random.default_rng(41), 300, 50, 2000)
+    return np.frombuffer(b"ACGTACGTAC$ACGTT$", np.uint8)
+
+
+@pytest.mark.parametrize("kind", GRAPH_TEXTS)
+def test_sa_graph_rounds_equal_host_rounds(ctx, kind):
+    """The doubling rounds run as one captured graph (a device-side WHILE loop)
+    or from the host: the same SA (the oracle's), the same rounds and actives."""
+    t = graph_text(kind)
+    want = oracle.suffix_array(t)
+    sa = gpu_sa(ctx, t, opts=B().make_opts(rounds_on_host=1))[0]
+    assert np.array_equal(sa.cpu().numpy().astype(np.int64), want)
+    host = ctx.trace()
+    assert host["graph_rounds"] == 0
+    sa = gpu_sa(ctx, t, opts=B().make_opts())[0]
+    assert np.array_equal(sa.cpu().numpy().astype(np.int64), want)
+    dev_tr = ctx.trace()
+    assert dev_tr["rounds"] == host["rounds"] and dev_tr["active"] == host["active"]
+    assert dev_tr["graph_rounds"] == dev_tr["rounds"]
+
+
+def test_sa_graph_recaptured_for_new_sizes(ctx):
+    """The cached graph is captured again when the text size changes, and reused
+    (same buffers) when it does not: every call still equals the oracle."""
+    texts = [graph_text("repeat"), graph_text("multi"), graph_text("repeat"), graph_text("tandem")]
+    for t in texts + texts[:1]:
+        sa = gpu_sa(ctx, t)[0]
+        assert np.array_equal(sa.cpu().numpy().astype(np.int64), oracle.suffix_array(t))
+        assert ctx.trace()["graph_rounds"] >= 1
+
+
+@pytest.mark.parametrize("seg_max", [8, 256])
+def test_sa_graph_hands_large_groups_to_host(ctx, seg_max):
+    """A group larger than the on-chip limit ends the device loop; the host runs
+    the remaining rounds (global radix passes) and the SA still equals the oracle's."""
+    rng = synth.rng_for(12, 11)
+    t = synth.genome_text(synth.genome_with_repeats(rng, 400_000, 0.05, (2, 50), (10, 200), 0.30, 40, 0.01))
+    sa = gpu_sa(ctx, t, opts=B().make_opts(seg_max=seg_max))[0]
+    assert np.array_equal(sa.cpu().numpy().astype(np.int64), oracle.suffix_array(t))
+    tr = ctx.trace()
+    assert tr["graph_rounds"] < tr["rounds"]
+
+
+def test_sa_graph_max_rounds(ctx):
+    """max_rounds bounds the device loop as it bounds the host loop."""
+    t = graph_text("repeat")
+    with pytest.raises(B().DnasaError) as e:
+        gpu_sa(ctx, t, opts=B().make_opts(max_rounds=2))
+    assert e.value.status == B().INVALID_ARG
+    sa = gpu_sa(ctx, t)[0]   # the context is still usable
+    assert np.array_equal(sa.cpu().numpy().astype(np.int64), oracle.suffix_array(t))
+
+
 @pytest.mark.parametrize("pack", [0, -1])
 @pytest.mark.parametrize("seed,n_reads,lo,hi", [(21, 1, 300_001, 300_001), (22, 700, 1, 900)])
 def test_sa_packed_and_pair_initial_sort(ctx, pack, seed, n_reads, lo, hi):
