@@ -39,9 +39,15 @@ constexpr int kInitItems = 8;
 // sort word from bit lo_bit on) are counted here too, so that the sort does not
 // read the keys once more for them.  Grid-stride over chunks of 32 * kInitItems
 // positions per warp.
+//
+// hist4 (one sequence, h0 = 4 * passes): a digit of the sort word is then the
+// 4-mer code at a fixed offset from the suffix start, so every pass's histogram
+// is the text's 4-mer histogram except near the two ends; only that histogram
+// is counted here (one atomic per key instead of one per pass), into pass 0's
+// slot, and k_hist4_fix derives each pass's histogram from it.
 __global__ void __launch_bounds__(kInitThreads) k_init_keys(TextDesc t, int h0, int inst_shift,
                                                             int pb, int single, int passes, int lo_bit,
-                                                            uint32_t *__restrict__ ghist,
+                                                            int hist4, uint32_t *__restrict__ ghist,
                                                             unsigned long long *__restrict__ keys,
                                                             uint32_t *__restrict__ vals) {
     __shared__ uint32_t sh[8 * 256];
@@ -85,14 +91,49 @@ __global__ void __launch_bounds__(kInitThreads) k_init_keys(TextDesc t, int h0, 
                 vals[p] = (uint32_t)p;
             }
             keys[at] = w;
-            for (int q = 0; q < passes; ++q)
-                atomicAdd(&sh[q * 256 + (uint32_t)((w >> (lo_bit + 8 * q)) & 255ull)], 1u);
+            if (hist4) {
+                if (left >= 4) atomicAdd(&sh[(uint32_t)(x >> 56)], 1u);
+            } else {
+                for (int q = 0; q < passes; ++q)
+                    atomicAdd(&sh[q * 256 + (uint32_t)((w >> (lo_bit + 8 * q)) & 255ull)], 1u);
+            }
         }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < passes * 256; i += kInitThreads) {
+    for (int i = threadIdx.x; i < (hist4 ? 1 : passes) * 256; i += kInitThreads) {
         const uint32_t c = sh[i];
         if (c) atomicAdd(&ghist[i], c);
+    }
+}
+
+// One block of 256 threads, thread d = digit value d.  The 4-mer histogram H
+// counts the codes at x = 0 .. N-5 (four bases before the '$').  Pass q's digit
+// of a suffix p with h0 bases left is the code at x = p + o, o = h0 - 4 - 4q, for
+// p = 0 .. N-1-h0: H without x < o and without x > N-1-h0+o; the h0 suffixes
+// with fewer bases left carry a zero-padded key, counted one by one.
+__global__ void __launch_bounds__(256) k_hist4_fix(TextDesc t, int h0, int passes, uint32_t *ghist) {
+    // the codes near both ends and the ended suffixes' keys, fetched once (h0 <= 32 here)
+    __shared__ uint32_t s_head[32], s_tail[32];
+    __shared__ unsigned long long s_kmer[32];
+    const uint32_t d = threadIdx.x;
+    const int64_t N = t.N;
+    if (d < 32 && (int)d < h0) {
+        s_head[d] = (uint32_t)(bases32(t.packed, (uint64_t)d) >> 56);                  // x = d
+        s_tail[d] = (uint32_t)(bases32(t.packed, (uint64_t)(N - h0 - 4 + d)) >> 56);   // x = N-h0-4+d
+        const int64_t p = N - h0 + d;                                                  // ended suffix
+        const int lc = (int)(N - 1 - p);                                               // 0 .. h0 - 1
+        uint64_t kmer = bases32(t.packed, (uint64_t)p) >> (64 - 2 * h0);
+        s_kmer[d] = kmer & ~((1ull << (2 * (h0 - lc))) - 1ull);
+    }
+    const uint32_t H = ghist[d];
+    __syncthreads();
+    for (int q = 0; q < passes; ++q) {
+        const int o = h0 - 4 - 4 * q;
+        int64_t c = H;
+        for (int x = 0; x < o; ++x) c -= s_head[x] == d;
+        for (int i = o + 4; i < h0; ++i) c -= s_tail[i] == d;   // x = N-h0-4+i = N-h0+o .. N-5
+        for (int i = 0; i < h0; ++i) c += (uint32_t)((s_kmer[i] >> (8 * q)) & 255ull) == d;
+        ghist[q * 256 + d] = (uint32_t)c;
     }
 }
 
@@ -1857,6 +1898,8 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
     // ---- round 0: initial keys, sort, rerank
     {
         const int passes0 = ceil_div(key_bits0, 8);
+        // one sequence whose key is whole 4-mers: count one 4-mer histogram (k_hist4_fix)
+        const bool hist4 = single && h0 == 4 * passes0 && h0 <= 32 && N >= 2 * h0 + 8;
         DNASA_CUDA(ctx, cudaMemsetAsync(rs.hist, 0, (size_t)passes0 * 256 * 4, s));
         {
             LaunchScope ls_(ctx, PK_INIT, s, (pb ? 8.25 : 12.25) * N);
@@ -1864,8 +1907,12 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
             const int grid = (int)std::min<int64_t>(ceil_div(warps, kInitThreads / 32),
                                                     (int64_t)ctx->num_sms * 8);
             k_init_keys<<<std::max(grid, 1), kInitThreads, 0, s>>>(t, h0, inst_shift, pb, single ? 1 : 0,
-                                                                   passes0, pb,
+                                                                   passes0, pb, hist4 ? 1 : 0,
                                                                    rs.hist, keys[0], vals[0]);
+        }
+        if (hist4) {
+            LaunchScope ls_(ctx, PK_HIST, s, 0.0);
+            k_hist4_fix<<<1, 256, 0, s>>>(t, h0, passes0, rs.hist);
         }
         DNASA_CUDA(ctx, cudaGetLastError());
         int which;
