@@ -67,6 +67,8 @@ def parse():
     ap.add_argument("--lambdas", default="0.25,0.5,0.75,0.9,1.0,1.25",
                     help="served: arrival rates as multiples of one-job-per-launch capacity")
     ap.add_argument("--no-tune", action="store_true", help="skip the build-option autotuner")
+    ap.add_argument("--host-rounds", action="store_true",
+                    help="run the doubling rounds from the host instead of the captured graph")
     ap.add_argument("--builder", default="doubling", choices=["doubling", "dc3"],
                     help="sa64m / large: suffix-array builder (dc3: the difference-cover algorithm)")
     ap.add_argument("--slots", type=int, default=2)
@@ -870,6 +872,9 @@ def main():
         opts, tms = binding.dnasa_autotune(ctx, packed, toff, nr, N, cache_path=TUNE_CACHE)
         tuned = {"tile_items": opts.tile_items, "finish_threshold": opts.finish_threshold,
                  "lookback": opts.lookback, "sa_ms": tms}
+    if args.host_rounds:
+        opts = opts or binding.make_opts()
+        opts.rounds_on_host = 1
 
     def step():
         binding.sa_build(ctx, packed, toff, nr, N, sa, opts)
