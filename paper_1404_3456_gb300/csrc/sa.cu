@@ -1013,9 +1013,11 @@ __device__ __forceinline__ unsigned long long shfl_xor_u64(unsigned long long x,
 __device__ __forceinline__ uint32_t ap_period(uint32_t pmin, uint32_t pmax, int n, uint32_t h) {
     if (n < 3) return 0;   // two members: their low key parts already differ if it applies
     const uint32_t d = pmax - pmin;
+    // a step above h is excluded first by a multiply, so most groups (members far
+    // apart: copies of a repeat, reads of one locus) never reach the division
+    if ((uint64_t)d > (uint64_t)h * (uint64_t)(n - 1)) return 0;
     if (d % (uint32_t)(n - 1) != 0) return 0;
-    const uint32_t p = d / (uint32_t)(n - 1);
-    return p <= h ? p : 0;
+    return d / (uint32_t)(n - 1);
 }
 
 // Index of a member within an arithmetic-progression group in suffix order.
