@@ -259,6 +259,20 @@ int dnasa_pack(dnasa_ctx *ctx, const uint8_t *text, int64_t N, uint64_t *packed,
 int sa_build(dnasa_ctx *ctx, const uint64_t *packed, const int64_t *toff, int64_t n_reads,
              int64_t N, void *sa, int idx_width, const dnasa_opts *opts, void *stream);
 
+/* The suffix array and its LCP array (as lcp_build defines it) in one call: the
+ * same SA as sa_build and the same LCP as lcp_build, bit for bit.  Round 0 of the
+ * build compares each SA slot's initial key with its predecessor's anyway; for
+ * every pair the initial keys separate (all but the pairs sharing their first h0
+ * bases) it writes the LCP from the two keys -- the equal leading bases of their
+ * packed h0-mers, capped by the bases each has before its '$', 0 across instances
+ * -- so that only the remaining pairs are compared on the text afterwards,
+ * starting at base h0.  Arguments as sa_build, plus
+ *   lcp   device, N int32 (written entirely)
+ * With builder = 1 (DC3) it is sa_build followed by lcp_build.  Synchronizes the
+ * stream as sa_build does, and once more to size the pass over long pairs. */
+int sa_lcp_build(dnasa_ctx *ctx, const uint64_t *packed, const int64_t *toff, int64_t n_reads,
+                 int64_t N, void *sa, int idx_width, int32_t *lcp, const dnasa_opts *opts, void *stream);
+
 /* ---- LCP ----------------------------------------------------------------- */
 
 /* lcp[0] = 0; lcp[j] = number of equal bases at the start of suffixes sa[j-1]

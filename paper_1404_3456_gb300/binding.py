@@ -87,6 +87,7 @@ _SIGS = {
     "dnasa_pack": (_INT, [_P, _P, _I64, _P, _P, _I64, ctypes.POINTER(_I64), _P]),
     "sa_build": (_INT, [_P, _P, _P, _I64, _I64, _P, _INT, ctypes.POINTER(Opts), _P]),
     "lcp_build": (_INT, [_P, _P, _P, _I64, _I64, _P, _INT, _P, _P]),
+    "sa_lcp_build": (_INT, [_P, _P, _P, _I64, _I64, _P, _INT, _P, ctypes.POINTER(Opts), _P]),
     "overlap_search": (_INT, [_P, _P, _P, _I64, _I64, _P, _P, _INT, _I32, _P, _I64,
                               ctypes.POINTER(_I64), _P, _P]),
     "assemble": (_INT, [_P, _P, _I64, _I32, _P, _I64, _P, _I64, ctypes.POINTER(_I64),
@@ -271,6 +272,15 @@ def lcp_build(ctx: Context, packed, toff, n_reads: int, N: int, sa, lcp, stream=
     width = I64 if sa.dtype == torch.int64 else I32
     ctx.check(lib().lcp_build(ctx.handle, _ptr(packed), _ptr(toff), n_reads, N, _ptr(sa), width,
                               _ptr(lcp), _stream(stream)))
+
+
+def sa_lcp_build(ctx: Context, packed, toff, n_reads: int, N: int, sa, lcp, opts: Opts | None = None,
+                 stream=None):
+    """Suffix array and LCP in one call (sa_build + lcp_build results)."""
+    width = I64 if sa.dtype == torch.int64 else I32
+    ctx.check(lib().sa_lcp_build(ctx.handle, _ptr(packed), _ptr(toff), n_reads, N, _ptr(sa), width,
+                                 _ptr(lcp), ctypes.byref(opts) if opts is not None else None,
+                                 _stream(stream)))
 
 
 def overlap_search(ctx: Context, packed, toff, n_reads: int, N: int, sa, lcp, min_overlap: int,

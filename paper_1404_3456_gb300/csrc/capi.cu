@@ -195,6 +195,25 @@ int assemble_impl(dnasa_ctx *ctx, const uint8_t *text, int64_t N, const int64_t 
 
 using namespace dnasa;
 
+namespace {
+
+int check_sa_opts(dnasa_ctx *ctx, const dnasa_opts *opts, const char *who) {
+    if (!opts) return DNASA_OK;
+    auto bad = [&](const char *what) { return fail(ctx, DNASA_INVALID_ARG, std::string(who) + ": " + what); };
+    if (opts->tile_items != 0 && opts->tile_items != 2048 && opts->tile_items != 3840 && opts->tile_items != 5120)
+        return bad("tile_items must be 0, 2048, 3840 or 5120");
+    if (opts->reserved0 != 0) return bad("reserved0 must be 0");
+    if (opts->lookback != 0 && opts->lookback != 1 && opts->lookback != 8) return bad("lookback must be 0, 1 or 8");
+    if (opts->seg_max != 0 && (opts->seg_max < 8 || opts->seg_max > 12288))
+        return bad("seg_max must be 0 or in [8, 12288]");
+    if (opts->pack_position != 0 && opts->pack_position != -1) return bad("pack_position must be 0 or -1");
+    if (opts->builder != 0 && opts->builder != 1) return bad("builder must be 0 (doubling) or 1 (DC3)");
+    if (opts->rounds_on_host != 0 && opts->rounds_on_host != 1) return bad("rounds_on_host must be 0 or 1");
+    return DNASA_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 int sa_build(dnasa_ctx *ctx, const uint64_t *packed, const int64_t *toff, int64_t n_reads,
@@ -205,21 +224,7 @@ int sa_build(dnasa_ctx *ctx, const uint64_t *packed, const int64_t *toff, int64_
     if (idx_width != DNASA_I32 && idx_width != DNASA_I64)
         return fail(ctx, DNASA_INVALID_ARG, "sa_build: idx_width must be DNASA_I32 or DNASA_I64");
     if (!is_device_ptr(ctx, sa)) return fail(ctx, DNASA_INVALID_ARG, "sa_build: sa must be a device pointer");
-    if (opts && (opts->tile_items != 0 && opts->tile_items != 2048 && opts->tile_items != 3840 &&
-                 opts->tile_items != 5120))
-        return fail(ctx, DNASA_INVALID_ARG, "sa_build: tile_items must be 0, 2048, 3840 or 5120");
-    if (opts && opts->reserved0 != 0)
-        return fail(ctx, DNASA_INVALID_ARG, "sa_build: reserved0 must be 0");
-    if (opts && opts->lookback != 0 && opts->lookback != 1 && opts->lookback != 8)
-        return fail(ctx, DNASA_INVALID_ARG, "sa_build: lookback must be 0, 1 or 8");
-    if (opts && opts->seg_max != 0 && (opts->seg_max < 8 || opts->seg_max > 12288))
-        return fail(ctx, DNASA_INVALID_ARG, "sa_build: seg_max must be 0 or in [8, 12288]");
-    if (opts && opts->pack_position != 0 && opts->pack_position != -1)
-        return fail(ctx, DNASA_INVALID_ARG, "sa_build: pack_position must be 0 or -1");
-    if (opts && opts->builder != 0 && opts->builder != 1)
-        return fail(ctx, DNASA_INVALID_ARG, "sa_build: builder must be 0 (doubling) or 1 (DC3)");
-    if (opts && opts->rounds_on_host != 0 && opts->rounds_on_host != 1)
-        return fail(ctx, DNASA_INVALID_ARG, "sa_build: rounds_on_host must be 0 or 1");
+    DNASA_TRY(check_sa_opts(ctx, opts, "sa_build"));
     cudaSetDevice(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
     TextDesc t = one_instance(packed, toff, n_reads, N);
@@ -227,6 +232,35 @@ int sa_build(dnasa_ctx *ctx, const uint64_t *packed, const int64_t *toff, int64_
     DevBuf tmp;
     DNASA_TRY(dev_alloc(ctx, tmp, (size_t)N * 4, s));
     DNASA_TRY(sa_build_u32(ctx, t, (uint32_t *)tmp.p, opts, s));
+    return widen_u32_to_i64(ctx, (const uint32_t *)tmp.p, N, (int64_t *)sa, s);
+}
+
+int sa_lcp_build(dnasa_ctx *ctx, const uint64_t *packed, const int64_t *toff, int64_t n_reads,
+                 int64_t N, void *sa, int idx_width, int32_t *lcp, const dnasa_opts *opts, void *stream) {
+    if (!ctx) return DNASA_INVALID_ARG;
+    ctx->last_error.clear();
+    if (!is_device_ptr(ctx, lcp)) return fail(ctx, DNASA_INVALID_ARG, "sa_lcp_build: lcp must be a device pointer");
+    if (opts && opts->builder == 1) {   // DC3 has no initial keys to read LCPs from
+        DNASA_TRY(sa_build(ctx, packed, toff, n_reads, N, sa, idx_width, opts, stream));
+        return lcp_build(ctx, packed, toff, n_reads, N, sa, idx_width, lcp, stream);
+    }
+    // the same argument checks as sa_build, then the build writing round 0's LCPs
+    DNASA_TRY(check_text_args(ctx, packed, toff, n_reads, N, "sa_lcp_build"));
+    if (idx_width != DNASA_I32 && idx_width != DNASA_I64)
+        return fail(ctx, DNASA_INVALID_ARG, "sa_lcp_build: idx_width must be DNASA_I32 or DNASA_I64");
+    if (!is_device_ptr(ctx, sa)) return fail(ctx, DNASA_INVALID_ARG, "sa_lcp_build: sa must be a device pointer");
+    DNASA_TRY(check_sa_opts(ctx, opts, "sa_lcp_build"));
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const TextDesc t = one_instance(packed, toff, n_reads, N);
+    if (idx_width == DNASA_I32) {
+        DNASA_TRY(sa_build_u32(ctx, t, (uint32_t *)sa, opts, s, nullptr, lcp));
+        return lcp_build_impl(ctx, t, (const uint32_t *)sa, lcp, s, nullptr, ctx->trace.h0);
+    }
+    DevBuf tmp;
+    DNASA_TRY(dev_alloc(ctx, tmp, (size_t)N * 4, s));
+    DNASA_TRY(sa_build_u32(ctx, t, (uint32_t *)tmp.p, opts, s, nullptr, lcp));
+    DNASA_TRY(lcp_build_impl(ctx, t, (const uint32_t *)tmp.p, lcp, s, nullptr, ctx->trace.h0));
     return widen_u32_to_i64(ctx, (const uint32_t *)tmp.p, N, (int64_t *)sa, s);
 }
 

@@ -103,6 +103,51 @@ __global__ void __launch_bounds__(256) k_lcp(TextDesc t, const uint32_t *__restr
     }
 }
 
+// After sa_lcp_build's round 0 wrote the LCP of every pair the initial keys
+// separate: only the slots marked -1 are left, pairs that share their first
+// `skip` bases (the initial key).  Each compares two packed words from there; a
+// pair still equal past them (at least 64 bases) is queued for k_lcp_chain.
+__global__ void __launch_bounds__(256) k_lcp_rest(TextDesc t, const uint32_t *__restrict__ sa,
+                                                  int32_t *__restrict__ lcp, int skip,
+                                                  uint32_t *__restrict__ qpos, uint32_t *__restrict__ qj,
+                                                  unsigned long long *__restrict__ nlong) {
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane; b < t.N; b += stride) {
+        const int64_t j = b + lane;
+        bool queue = false;
+        if (j > 0 && j < t.N && lcp[j] < 0) {
+            const PairInfo pi = pair_info(t, sa, j);
+            int64_t h = skip;
+            bool exact = false;
+#pragma unroll
+            for (int w = 0; w < 2; ++w) {
+                if (exact || h >= pi.m) break;
+                const uint64_t d = bases32(t.packed, pi.bp + h) ^ bases32(t.packed, pi.bq + h);
+                if (d) {
+                    h += __clzll((long long)d) >> 1;
+                    exact = true;
+                } else {
+                    h += 32;
+                }
+            }
+            if (exact || h >= pi.m) lcp[j] = (int32_t)min(h, pi.m);
+            else queue = true;   // equal on at least skip + 64 >= 64 bases
+        }
+        const uint32_t qm = __ballot_sync(0xffffffffu, queue);
+        if (qm) {
+            unsigned long long qb = 0;
+            if (lane == 0) qb = atomicAdd(nlong, (unsigned long long)__popc(qm));
+            qb = __shfl_sync(0xffffffffu, qb, 0);
+            if (queue) {
+                const unsigned long long at = qb + __popc(qm & lanemask_lt());
+                qpos[at] = sa[j];
+                qj[at] = (uint32_t)j;
+            }
+        }
+    }
+}
+
 // The queued pairs (LCP over 64 bases: repeats), sorted by the text position p
 // of their lower suffix.  Kasai's bound: the LCP of suffix p+1 with its SA
 // predecessor is at least that of p minus one, so along a run of consecutive
@@ -206,8 +251,8 @@ __global__ void k_lcp_gather(const uint32_t *__restrict__ sa, const uint32_t *__
 }  // namespace
 
 int lcp_build_impl(dnasa_ctx *ctx, const TextDesc &t, const uint32_t *sa32, int32_t *lcp,
-                   cudaStream_t s, const uint32_t *isa) {
-    if (isa) {   // Phi / PLCP in text order, then one gather
+                   cudaStream_t s, const uint32_t *isa, int rest_skip) {
+    if (isa && rest_skip < 0) {   // Phi / PLCP in text order, then one gather
         DNASA_TRY(ws_reserve(ctx, ((size_t)t.N * 4 + 255) / 256 * 256 + 4096, s));
         Arena a = ws_arena(ctx);
         uint32_t *plcp = a.take<uint32_t>((size_t)t.N);
@@ -237,7 +282,10 @@ int lcp_build_impl(dnasa_ctx *ctx, const TextDesc &t, const uint32_t *sa32, int3
     unsigned long long *nlong = ctx->ctrl->count + CNT_TMP;
     DNASA_CUDA(ctx, cudaMemsetAsync(nlong, 0, 8, s));
     int grid = (int)std::min<int64_t>(ceil_div(t.N, 256), (int64_t)ctx->num_sms * 16);
-    {
+    if (rest_skip >= 0) {   // the pairs the SA build left (-1): 4 B read per slot + their own work
+        LaunchScope ls_(ctx, PK_LCP, s, 4.0 * t.N);
+        k_lcp_rest<<<std::max(grid, 1), 256, 0, s>>>(t, sa32, lcp, rest_skip, qk[0], qv[0], nlong);
+    } else {
         LaunchScope ls_(ctx, PK_LCP, s, 8.5 * t.N);
         k_lcp<<<std::max(grid, 1), 256, 0, s>>>(t, sa32, lcp, qk[0], qv[0], nlong);
     }

@@ -169,6 +169,8 @@ struct RerankOut {
     int bshift;
     int pb;             // round 0 only: keys hold (key << pb) | position, no value array
     int single;         // round 0 only: (bases << pb) | f, f as in h0_single
+    int32_t *lcp;       // round 0 only, may be null: LCP of every pair the initial keys separate,
+                        // -1 where both suffixes share their initial key (LCP >= h0)
 };
 
 // Shared memory of one rerank tile of a doubling round (dynamic, > 48 KB).
@@ -492,6 +494,31 @@ __device__ __forceinline__ bool own_head(unsigned long long k, unsigned long lon
     return k != kp;
 }
 
+// LCP (bases, a '$' never matching) of two suffixes with different initial keys,
+// from the keys alone: the equal leading bases of their h0-mers, capped by the
+// bases each has before its '$'; 0 across instances.  ka/kb as r0_decode gives them.
+__device__ __forceinline__ int32_t r0_lcp(unsigned long long ka, uint32_t pa, unsigned long long kb,
+                                          uint32_t pb_, const RerankOut &o, int h0) {
+    const unsigned long long km = (1ull << (2 * h0)) - 1ull;
+    unsigned long long xa, xb;
+    int la, lb;
+    if (o.single) {   // (h0-mer << 1) | not-ended; bases left from the position
+        xa = ka >> 1;
+        xb = kb >> 1;
+        la = (int)min((int64_t)h0, o.N - 1 - (int64_t)pa);
+        lb = (int)min((int64_t)h0, o.N - 1 - (int64_t)pb_);
+    } else {          // (instance << (2 h0 + 5)) | (h0-mer << 5) | bases left
+        if ((ka >> (2 * h0 + 5)) != (kb >> (2 * h0 + 5))) return 0;
+        xa = (ka >> 5) & km;
+        xb = (kb >> 5) & km;
+        la = (int)(ka & 31ull);
+        lb = (int)(kb & 31ull);
+    }
+    const unsigned long long d = (xa ^ xb) << (64 - 2 * h0);
+    const int eq = d ? (__clzll((long long)d) >> 1) : h0;
+    return (int32_t)min(eq, min(la, lb));
+}
+
 struct OwnSmem {
     unsigned long long k[kR0Tile + 2];   // compared keys, one halo key on each side
     uint32_t v[kR0Tile];                 // positions
@@ -501,6 +528,7 @@ struct OwnSmem {
     uint32_t nb[kR0Tile / 32];           // ... the item after it starts one (or the data end)
     int64_t tmp[kR0Threads / 32 + 1];
     uint32_t bcnt[kMaxBuckets];          // per-bucket counts of a chunk, then global bases
+    uint32_t vh;                         // position of the item before the tile (its halo)
     int64_t own_end;                     // end of the last group whose head is in the tile
     unsigned long long kp_base;          // list index of the tile's first kept item
     int first_head;                      // tile-local index of the first head (tile_n: none)
@@ -599,6 +627,7 @@ __global__ void __launch_bounds__(kR0Threads, 5) k_rerank0(const unsigned long l
             if (hj >= 0 && hj < n) r0_decode(hw, hv, o, h0, &key, &pos);
             else r0_decode(0ull, 0u, o, h0, &key, &pos);
             S.k[tid == 0 ? 0 : tile_n + 1] = key;
+            if (tid == 0) S.vh = pos;
         }
     }
     __syncthreads();
@@ -622,6 +651,17 @@ __global__ void __launch_bounds__(kR0Threads, 5) k_rerank0(const unsigned long l
         }
     }
     __syncthreads();
+    // ---- LCP with the SA predecessor, where the initial keys decide it (coalesced)
+    if (o.lcp) {
+        for (int i = tid; i < tile_n; i += kR0Threads) {
+            const int64_t j = base + i;
+            int32_t v;
+            if (j == 0) v = 0;
+            else if (((S.hb[i >> 5] >> (i & 31)) & 1u) == 0u) v = -1;   // same initial key
+            else v = r0_lcp(S.k[i], i > 0 ? S.v[i - 1] : S.vh, S.k[i + 1], S.v[i], o, h0);
+            o.lcp[j] = v;
+        }
+    }
     // ---- first head of the tile; end of its last group (past the tile if needed)
     if (tid < 32) {
         int fh = tile_n;
@@ -1648,7 +1688,7 @@ size_t sa_workspace_bytes(int64_t N, int tile_items) {
 }
 
 int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_opts *opts_in,
-                 cudaStream_t s, uint32_t *isa_out) {
+                 cudaStream_t s, uint32_t *isa_out, int32_t *lcp_out) {
     dnasa_opts opts{};
     if (opts_in) opts = *opts_in;
     if (opts.builder == 1) return sa_build_dc3(ctx, t, sa32, s, isa_out);
@@ -1761,6 +1801,7 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
     ro.kb = b;
     ro.pb = pb;
     ro.single = single ? 1 : 0;
+    ro.lcp = lcp_out;
 
     // ---- one doubling round with fixed grids and device-side counts (captured)
     int rr_grid = 0;
@@ -1925,7 +1966,7 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
         ro.nslots = L[0][0]; ro.npos = L[0][1]; ro.nhead = L[0][2];
         ro.stage = reinterpret_cast<uint2 *>(keys[which ^ 1]);   // the free key buffer
         {
-            LaunchScope ls_(ctx, PK_RERANK, s, 20.0 * N);
+            LaunchScope ls_(ctx, PK_RERANK, s, (lcp_out ? 24.0 : 20.0) * N);   // + 4 B of LCP per slot
             k_rerank0<<<ceil_div(N, kR0Tile), kR0Threads, 0, s>>>(keys[which], vals[which], N, h0, ro, &c->err);
         }
         DNASA_CUDA(ctx, cudaGetLastError());

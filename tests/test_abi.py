@@ -20,7 +20,7 @@ def declared_functions():
 
 def test_header_declares_the_boundary():
     names = declared_functions()
-    for n in ["dnasa_create", "dnasa_destroy", "dnasa_pack", "sa_build", "lcp_build",
+    for n in ["dnasa_create", "dnasa_destroy", "dnasa_pack", "sa_build", "lcp_build", "sa_lcp_build",
               "overlap_search", "assemble"]:
         assert n in names
 

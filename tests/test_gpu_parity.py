@@ -258,6 +258,53 @@ def test_sa_graph_max_rounds(ctx):
     assert np.array_equal(sa.cpu().numpy().astype(np.int64), oracle.suffix_array(t))
 
 
+def lcp_texts():
+    rng = np.random.default_rng(50)
+    return {
+        "repeat": graph_text("repeat"),
+        "tandem": graph_text("tandem"),
+        "multi": random_text(rng, 300, 1, 2000),
+        "short_reads": random_text(rng, 3000, 1, 40),
+        "endings": synth.genome_text(np.tile(synth.iid(rng, 7), 40)),
+        "tiny": np.frombuffer(b"ACGTACGTAC$ACGTT$A$", np.uint8),
+    }
+
+
+@pytest.mark.parametrize("kind", ["repeat", "tandem", "multi", "short_reads", "endings", "tiny"])
+@pytest.mark.parametrize("opts_kw", [{}, {"pack_position": -1}, {"rounds_on_host": 1}, {"builder": 1}],
+                         ids=["packed", "pairs", "host_rounds", "dc3"])
+def test_sa_lcp_build(ctx, kind, opts_kw):
+    """SA and LCP in one call: round 0 writes the LCP of every pair its keys separate,
+    the rest is compared on the text; both arrays equal the oracle's."""
+    t = lcp_texts()[kind]
+    want = oracle.suffix_array(t)
+    text = dev(t)
+    packed, toff, nr = B().pack_text(ctx, text)
+    for dtype in (torch.int32, torch.int64):
+        sa = torch.empty(t.size, dtype=dtype, device="cuda")
+        lcp = torch.full((t.size,), -7, dtype=torch.int32, device="cuda")
+        B().sa_lcp_build(ctx, packed, toff, nr, t.size, sa, lcp, B().make_opts(**opts_kw))
+        assert np.array_equal(sa.cpu().numpy().astype(np.int64), want)
+        assert np.array_equal(lcp.cpu().numpy(), oracle.lcp_kasai(t, want))
+
+
+def test_sa_lcp_build_64m_sampled(ctx):
+    """The fused call on the 64 Mbp benchmark genome equals the separate calls."""
+    g = synth.sa64m_genome(1)
+    t = synth.genome_text(g)
+    text = dev(t)
+    packed, toff, nr = B().pack_text(ctx, text)
+    del text
+    sa1 = torch.empty(t.size, dtype=torch.int32, device="cuda")
+    lcp1 = torch.empty_like(sa1)
+    B().sa_build(ctx, packed, toff, nr, t.size, sa1)
+    B().lcp_build(ctx, packed, toff, nr, t.size, sa1, lcp1)
+    sa2 = torch.empty_like(sa1)
+    lcp2 = torch.empty_like(sa1)
+    B().sa_lcp_build(ctx, packed, toff, nr, t.size, sa2, lcp2)
+    assert torch.equal(sa1, sa2) and torch.equal(lcp1, lcp2)
+
+
 @pytest.mark.parametrize("pack", [0, -1])
 @pytest.mark.parametrize("seed,n_reads,lo,hi", [(21, 1, 300_001, 300_001), (22, 700, 1, 900)])
 def test_sa_packed_and_pair_initial_sort(ctx, pack, seed, n_reads, lo, hi):
