@@ -266,10 +266,13 @@ int sa_build(dnasa_ctx *ctx, const uint64_t *packed, const int64_t *toff, int64_
  * bases) it writes the LCP from the two keys -- the equal leading bases of their
  * packed h0-mers, capped by the bases each has before its '$', 0 across instances
  * -- so that only the remaining pairs are compared on the text afterwards,
- * starting at base h0.  Arguments as sa_build, plus
+ * starting at base h0: their lower suffixes are marked in a bitmap of text
+ * positions and walked in text order through the build's final ranks (the
+ * inverse SA), each comparison starting where the previous position's ended
+ * (Kasai's bound) -- no sort by position.  Arguments as sa_build, plus
  *   lcp   device, N int32 (written entirely)
  * With builder = 1 (DC3) it is sa_build followed by lcp_build.  Synchronizes the
- * stream as sa_build does, and once more to size the pass over long pairs. */
+ * stream as sa_build does. */
 int sa_lcp_build(dnasa_ctx *ctx, const uint64_t *packed, const int64_t *toff, int64_t n_reads,
                  int64_t N, void *sa, int idx_width, int32_t *lcp, const dnasa_opts *opts, void *stream);
 

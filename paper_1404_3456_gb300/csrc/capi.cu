@@ -253,14 +253,10 @@ int sa_lcp_build(dnasa_ctx *ctx, const uint64_t *packed, const int64_t *toff, in
     cudaSetDevice(ctx->device);
     cudaStream_t s = (cudaStream_t)stream;
     const TextDesc t = one_instance(packed, toff, n_reads, N);
-    if (idx_width == DNASA_I32) {
-        DNASA_TRY(sa_build_u32(ctx, t, (uint32_t *)sa, opts, s, nullptr, lcp));
-        return lcp_build_impl(ctx, t, (const uint32_t *)sa, lcp, s, nullptr, ctx->trace.h0);
-    }
+    if (idx_width == DNASA_I32) return sa_build_u32(ctx, t, (uint32_t *)sa, opts, s, nullptr, lcp);
     DevBuf tmp;
     DNASA_TRY(dev_alloc(ctx, tmp, (size_t)N * 4, s));
     DNASA_TRY(sa_build_u32(ctx, t, (uint32_t *)tmp.p, opts, s, nullptr, lcp));
-    DNASA_TRY(lcp_build_impl(ctx, t, (const uint32_t *)tmp.p, lcp, s, nullptr, ctx->trace.h0));
     return widen_u32_to_i64(ctx, (const uint32_t *)tmp.p, N, (int64_t *)sa, s);
 }
 

@@ -198,9 +198,8 @@ int make_instances(dnasa_ctx *ctx, const int64_t *toff, int64_t n_reads, int64_t
 size_t sa_workspace_bytes(int64_t N, int tile_items);
 // Builds the SA into sa32 (uint32, N entries, text coordinates).  If isa_out is
 // non-null it also receives the inverse SA (the final rank array), N uint32.
-// lcp_out (may be null): the LCP of every SA pair the initial keys separate, -1 for
-// the pairs that share their initial key (lcp_build_impl with rest_skip = the
-// trace's h0 finishes it).
+// lcp_out (may be null): also the LCP array (as lcp_build_impl) -- round 0 writes
+// the LCP of every SA pair the initial keys separate, lcp_finish_with_isa the rest.
 int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_opts *opts,
                  cudaStream_t s, uint32_t *isa_out = nullptr, int32_t *lcp_out = nullptr);
 // x[i] = x[0] + ... + x[i] in place (dc3.cu; sums below 2^32).
@@ -210,10 +209,13 @@ int sa_build_dc3(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, cudaStream_t
 // fid[p] = fragment holding text position p, for p in [0, N).
 int fragment_ids(dnasa_ctx *ctx, const TextDesc &t, uint32_t *fid, cudaStream_t s);
 // isa (may be null) = inverse of sa32: the LCP is then computed in text order.
-// rest_skip >= 0: lcp already holds sa_build_u32's lcp_out; only its -1 slots
-// (pairs equal on their first rest_skip bases) are computed.
+// Finishes sa_build_u32's lcp_out with the inverse SA (the build's final ranks):
+// the -1 slots (pairs equal on their first `skip` bases) are computed by a walk in
+// text order.  bits: (N + 31) / 32 words of device scratch.
+int lcp_finish_with_isa(dnasa_ctx *ctx, const TextDesc &t, const uint32_t *sa32, const uint32_t *isa,
+                        int32_t *lcp, int skip, uint32_t *bits, cudaStream_t s);
 int lcp_build_impl(dnasa_ctx *ctx, const TextDesc &t, const uint32_t *sa32, int32_t *lcp,
-                   cudaStream_t s, const uint32_t *isa = nullptr, int rest_skip = -1);
+                   cudaStream_t s, const uint32_t *isa = nullptr);
 // isa (may be null: rebuilt from sa32) is the inverse of sa32.
 int overlap_impl(dnasa_ctx *ctx, const TextDesc &t, const uint32_t *sa32, const int32_t *lcp,
                  int32_t min_overlap, dnasa_edge *edges, int64_t cap, int64_t *n_edges,

@@ -103,51 +103,6 @@ __global__ void __launch_bounds__(256) k_lcp(TextDesc t, const uint32_t *__restr
     }
 }
 
-// After sa_lcp_build's round 0 wrote the LCP of every pair the initial keys
-// separate: only the slots marked -1 are left, pairs that share their first
-// `skip` bases (the initial key).  Each compares two packed words from there; a
-// pair still equal past them (at least 64 bases) is queued for k_lcp_chain.
-__global__ void __launch_bounds__(256) k_lcp_rest(TextDesc t, const uint32_t *__restrict__ sa,
-                                                  int32_t *__restrict__ lcp, int skip,
-                                                  uint32_t *__restrict__ qpos, uint32_t *__restrict__ qj,
-                                                  unsigned long long *__restrict__ nlong) {
-    const int lane = threadIdx.x & 31;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x - lane; b < t.N; b += stride) {
-        const int64_t j = b + lane;
-        bool queue = false;
-        if (j > 0 && j < t.N && lcp[j] < 0) {
-            const PairInfo pi = pair_info(t, sa, j);
-            int64_t h = skip;
-            bool exact = false;
-#pragma unroll
-            for (int w = 0; w < 2; ++w) {
-                if (exact || h >= pi.m) break;
-                const uint64_t d = bases32(t.packed, pi.bp + h) ^ bases32(t.packed, pi.bq + h);
-                if (d) {
-                    h += __clzll((long long)d) >> 1;
-                    exact = true;
-                } else {
-                    h += 32;
-                }
-            }
-            if (exact || h >= pi.m) lcp[j] = (int32_t)min(h, pi.m);
-            else queue = true;   // equal on at least skip + 64 >= 64 bases
-        }
-        const uint32_t qm = __ballot_sync(0xffffffffu, queue);
-        if (qm) {
-            unsigned long long qb = 0;
-            if (lane == 0) qb = atomicAdd(nlong, (unsigned long long)__popc(qm));
-            qb = __shfl_sync(0xffffffffu, qb, 0);
-            if (queue) {
-                const unsigned long long at = qb + __popc(qm & lanemask_lt());
-                qpos[at] = sa[j];
-                qj[at] = (uint32_t)j;
-            }
-        }
-    }
-}
-
 // The queued pairs (LCP over 64 bases: repeats), sorted by the text position p
 // of their lower suffix.  Kasai's bound: the LCP of suffix p+1 with its SA
 // predecessor is at least that of p minus one, so along a run of consecutive
@@ -248,11 +203,74 @@ __global__ void k_lcp_gather(const uint32_t *__restrict__ sa, const uint32_t *__
         lcp[j] = (int32_t)__ldg(plcp + sa[j]);
 }
 
+// ---- finishing the LCP inside a suffix-array build (sa_lcp_build), with the
+// inverse SA at hand: the pairs round 0 left (-1: they share their first `skip`
+// bases) are marked by the text position of their lower suffix in a bitmap, then
+// walked in text order, 32 positions per thread.  Kasai's bound chains the walk:
+// the LCP of position p with its SA predecessor is at least that of p - 1 minus
+// one, so a comparison starts where the previous one ended.  No sort by position
+// is needed: the bitmap is the order.
+__global__ void __launch_bounds__(256) k_lcp_mark(const uint32_t *__restrict__ sa,
+                                                  const int32_t *__restrict__ lcp, int64_t N,
+                                                  uint32_t *__restrict__ bits) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < N;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        if (lcp[j] < 0) {
+            const uint32_t p = sa[j];
+            atomicOr(bits + (p >> 5), 1u << (p & 31u));
+        }
+    }
+}
+
+__global__ void __launch_bounds__(128) k_lcp_walk(TextDesc t, const uint32_t *__restrict__ sa,
+                                                  const uint32_t *__restrict__ isa,
+                                                  const uint32_t *__restrict__ bits, int skip,
+                                                  int32_t *__restrict__ lcp) {
+    const int64_t words = (t.N + 31) >> 5;
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < words;
+         w += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t m = bits[w];
+        int64_t prev_p = -2, prev_h = 0;
+        while (m) {
+            const int b = __ffs(m) - 1;
+            m &= m - 1u;
+            const int64_t p = (w << 5) + b;
+            const int64_t j = isa[p];
+            if (j <= 0 || j >= t.N) continue;   // never marked: slot 0 has LCP 0
+            const int64_t q = sa[j - 1];
+            const int64_t rp = frag_of(t, p), rq = frag_of(t, q);
+            const int64_t mlen = min(__ldg(t.toff + rp + 1) - 1 - p, __ldg(t.toff + rq + 1) - 1 - q);
+            const uint64_t bp = (uint64_t)(p - rp), bq = (uint64_t)(q - rq);
+            int64_t h = (p == prev_p + 1 && prev_h - 1 > skip) ? prev_h - 1 : skip;
+            int64_t res = mlen;
+            for (; h < mlen; h += 4 * 32) {
+                uint64_t d[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int64_t o = h + 32 * u;   // past the shorter suffix's end: a "mismatch"
+                    d[u] = o < mlen ? bases32(t.packed, bp + o) ^ bases32(t.packed, bq + o) : ~0ull;
+                }
+                int64_t at = -1;
+#pragma unroll
+                for (int u = 3; u >= 0; --u)
+                    if (d[u]) at = h + 32 * u + (__clzll((long long)d[u]) >> 1);
+                if (at >= 0) {
+                    res = min(at, mlen);
+                    break;
+                }
+            }
+            lcp[j] = (int32_t)res;
+            prev_p = p;
+            prev_h = res;
+        }
+    }
+}
+
 }  // namespace
 
 int lcp_build_impl(dnasa_ctx *ctx, const TextDesc &t, const uint32_t *sa32, int32_t *lcp,
-                   cudaStream_t s, const uint32_t *isa, int rest_skip) {
-    if (isa && rest_skip < 0) {   // Phi / PLCP in text order, then one gather
+                   cudaStream_t s, const uint32_t *isa) {
+    if (isa) {   // Phi / PLCP in text order, then one gather
         DNASA_TRY(ws_reserve(ctx, ((size_t)t.N * 4 + 255) / 256 * 256 + 4096, s));
         Arena a = ws_arena(ctx);
         uint32_t *plcp = a.take<uint32_t>((size_t)t.N);
@@ -282,10 +300,7 @@ int lcp_build_impl(dnasa_ctx *ctx, const TextDesc &t, const uint32_t *sa32, int3
     unsigned long long *nlong = ctx->ctrl->count + CNT_TMP;
     DNASA_CUDA(ctx, cudaMemsetAsync(nlong, 0, 8, s));
     int grid = (int)std::min<int64_t>(ceil_div(t.N, 256), (int64_t)ctx->num_sms * 16);
-    if (rest_skip >= 0) {   // the pairs the SA build left (-1): 4 B read per slot + their own work
-        LaunchScope ls_(ctx, PK_LCP, s, 4.0 * t.N);
-        k_lcp_rest<<<std::max(grid, 1), 256, 0, s>>>(t, sa32, lcp, rest_skip, qk[0], qv[0], nlong);
-    } else {
+    {
         LaunchScope ls_(ctx, PK_LCP, s, 8.5 * t.N);
         k_lcp<<<std::max(grid, 1), 256, 0, s>>>(t, sa32, lcp, qk[0], qv[0], nlong);
     }
@@ -301,6 +316,25 @@ int lcp_build_impl(dnasa_ctx *ctx, const TextDesc &t, const uint32_t *sa32, int3
         int g2 = (int)std::max<int64_t>(1, std::min<int64_t>(ceil_div(ceil_div(nq, kChain), 128),
                                                            (int64_t)ctx->num_sms * 64));
         k_lcp_chain<<<g2, 128, 0, s>>>(t, sa32, lcp, qk[which], qv[which], nq);
+    }
+    DNASA_CUDA(ctx, cudaGetLastError());
+    return DNASA_OK;
+}
+
+
+int lcp_finish_with_isa(dnasa_ctx *ctx, const TextDesc &t, const uint32_t *sa32, const uint32_t *isa,
+                        int32_t *lcp, int skip, uint32_t *bits, cudaStream_t s) {
+    const int64_t words = (t.N + 31) >> 5;
+    DNASA_CUDA(ctx, cudaMemsetAsync(bits, 0, (size_t)words * 4, s));
+    {
+        LaunchScope ls_(ctx, PK_LCP, s, 4.0 * t.N);
+        const int g = (int)std::min<int64_t>(ceil_div(t.N, 256), (int64_t)ctx->num_sms * 16);
+        k_lcp_mark<<<std::max(g, 1), 256, 0, s>>>(sa32, lcp, t.N, bits);
+    }
+    {
+        LaunchScope ls_(ctx, PK_LCP, s, (double)words * 4.0);
+        const int g = (int)std::min<int64_t>(ceil_div(words, 128), (int64_t)ctx->num_sms * 64);
+        k_lcp_walk<<<std::max(g, 1), 128, 0, s>>>(t, sa32, isa, bits, skip, lcp);
     }
     DNASA_CUDA(ctx, cudaGetLastError());
     return DNASA_OK;

@@ -2106,6 +2106,9 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
     }
     if (isa_out)   // every rank is now final: the rank array is the inverse SA
         DNASA_CUDA(ctx, cudaMemcpyAsync(isa_out, rank, (size_t)N * 4, cudaMemcpyDeviceToDevice, s));
+    if (lcp_out)   // the pairs round 0 left (-1), walked in text order through the inverse SA;
+                   // the free key buffer holds the walk's bitmap
+        DNASA_TRY(lcp_finish_with_isa(ctx, t, sa32, rank, lcp_out, h0, reinterpret_cast<uint32_t *>(keys[1]), s));
     return check_device_status(ctx, s, "sa_build");
 }
 
