@@ -206,7 +206,8 @@ __global__ void k_lcp_gather(const uint32_t *__restrict__ sa, const uint32_t *__
 // ---- finishing the LCP inside a suffix-array build (sa_lcp_build), with the
 // inverse SA at hand: the pairs round 0 left (-1: they share their first `skip`
 // bases) are marked by the text position of their lower suffix in a bitmap, then
-// walked in text order, 32 positions per thread.  Kasai's bound chains the walk:
+// walked in text order, 16 positions per thread (more threads in flight beat
+// longer chains: 32 or 64 positions measured slower).  Kasai's bound chains the walk:
 // the LCP of position p with its SA predecessor is at least that of p - 1 minus
 // one, so a comparison starts where the previous one ended.  No sort by position
 // is needed: the bitmap is the order.
@@ -226,13 +227,15 @@ __global__ void __launch_bounds__(128) k_lcp_walk(TextDesc t, const uint32_t *__
                                                   const uint32_t *__restrict__ isa,
                                                   const uint32_t *__restrict__ bits, int skip,
                                                   int32_t *__restrict__ lcp) {
-    const int64_t words = (t.N + 31) >> 5;
-    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < words;
-         w += (int64_t)gridDim.x * blockDim.x) {
-        uint32_t m = bits[w];
+    const int64_t halves = ((t.N + 31) >> 5) * 2;   // 16 positions per thread
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < halves;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t w = c >> 1;
+        const int sh = (int)(c & 1) * 16;
+        uint32_t m = (bits[w] >> sh) & 0xffffu;
         int64_t prev_p = -2, prev_h = 0;
         while (m) {
-            const int b = __ffs(m) - 1;
+            const int b = __ffs(m) - 1 + sh;
             m &= m - 1u;
             const int64_t p = (w << 5) + b;
             const int64_t j = isa[p];
@@ -333,7 +336,7 @@ int lcp_finish_with_isa(dnasa_ctx *ctx, const TextDesc &t, const uint32_t *sa32,
     }
     {
         LaunchScope ls_(ctx, PK_LCP, s, (double)words * 4.0);
-        const int g = (int)std::min<int64_t>(ceil_div(words, 128), (int64_t)ctx->num_sms * 64);
+        const int g = (int)std::min<int64_t>(ceil_div(words * 2, 128), (int64_t)ctx->num_sms * 64);
         k_lcp_walk<<<std::max(g, 1), 128, 0, s>>>(t, sa32, isa, bits, skip, lcp);
     }
     DNASA_CUDA(ctx, cudaGetLastError());
