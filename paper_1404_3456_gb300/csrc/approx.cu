@@ -237,6 +237,7 @@ int approx_seed_length(int64_t lmin, int64_t max_len, int32_t num, int32_t den) 
 int overlap_approx_impl(dnasa_ctx *ctx, const uint8_t *text, int64_t N, int32_t lmin, int32_t mu_num,
                         int32_t mu_den, int rc, dnasa_aedge *edges, int64_t cap, int64_t *n_edges,
                         int64_t *n_oriented, cudaStream_t s) {
+    PhaseRange nvtx_("dnasa.overlap_approx");
     // ---- oriented text: each fragment followed by its reverse complement
     DevBuf packed0, toff0, text2, packed, toff, sa, isa, lcp, fid;
     const int64_t toff_cap = N / 2 + 2;

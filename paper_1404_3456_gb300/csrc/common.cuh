@@ -3,6 +3,7 @@
 // device helpers for the 2-bit packed text.
 #pragma once
 
+#include <nvtx3/nvToolsExt.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string>
@@ -111,6 +112,16 @@ inline cudaError_t smem_attr(F *fn, size_t bytes) { return smem_attr_fn((const v
 // Counts one kernel launch of class `kind` and, when profiling is on, brackets
 // it with CUDA events on its stream; `bytes` is the launch's algorithmic
 // traffic.  Construct immediately before the launch, destroy right after it.
+// A named range for profilers (NVTX v3, header-only: a no-op unless a tool such as
+// Nsight Systems is attached).  One per phase: pack, initial sort, doubling
+// rounds, LCP, overlap search, layout.
+struct PhaseRange {
+    explicit PhaseRange(const char *name) { nvtxRangePushA(name); }
+    ~PhaseRange() { nvtxRangePop(); }
+    PhaseRange(const PhaseRange &) = delete;
+    PhaseRange &operator=(const PhaseRange &) = delete;
+};
+
 struct LaunchScope {
     dnasa_ctx *ctx;
     int idx = -1;

@@ -300,6 +300,7 @@ __global__ void k_pack_words(const uint8_t *__restrict__ codes, const int64_t *n
 
 int pack_impl(dnasa_ctx *ctx, const uint8_t *text, int64_t N, uint64_t *packed, int64_t *toff,
               int64_t toff_cap, int64_t *n_reads, cudaStream_t s) {
+    PhaseRange nvtx_("dnasa.pack");
     int tiles = ceil_div(N, kPackTile);
     size_t need = ((size_t)(tiles + 1) * 8 + 255) / 256 * 256 + (size_t)N + 4096;
     DNASA_TRY(ws_reserve(ctx, need, s));

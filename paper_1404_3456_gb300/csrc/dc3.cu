@@ -401,6 +401,7 @@ int scan_inclusive_u32(dnasa_ctx *ctx, uint32_t *x, int64_t n, cudaStream_t st) 
 // Suffix array of the packed text by DC3 (one instance); isa_out (may be null)
 // receives the inverse.
 int sa_build_dc3(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, cudaStream_t st, uint32_t *isa_out) {
+    PhaseRange nvtx_("dnasa.sa_dc3");
     const int64_t N = t.N;
     if (t.n_inst > 1) return fail(ctx, DNASA_INVALID_ARG, "sa_build: the DC3 builder takes one instance");
     DevBuf sb;

@@ -364,6 +364,7 @@ int fir_impl(dnasa_ctx *ctx, const uint8_t *text, int64_t N, const int64_t *inst
              int32_t n_inst, int64_t max_steps, int64_t *frag_start, int64_t frag_cap, uint8_t *rs,
              int64_t rs_cap, int64_t *rs_off, int32_t *status, int64_t *steps, int64_t *rs_total,
              int64_t *n_frags, cudaStream_t s) {
+    PhaseRange nvtx_("dnasa.fir");
     DevBuf packed, toff, sa, isa, fid, inst_toff, inst_roff, rs_len;
     const int64_t toff_cap = N / 2 + 2;
     DNASA_TRY(dev_alloc(ctx, packed, (size_t)dnasa_packed_words(N) * 8, s));

@@ -242,6 +242,7 @@ int layout_impl(dnasa_ctx *ctx, const TextDesc &t, int64_t max_reads_per_inst,
                 const dnasa_edge *edges, int64_t ne, const uint8_t *contained, uint8_t *contigs,
                 int64_t cap, int64_t *contig_off, int64_t off_cap, int64_t *inst_contig_off,
                 int64_t *n_contigs, int64_t *needed, cudaStream_t s) {
+    PhaseRange nvtx_("dnasa.layout");
     const int64_t nr = t.n_reads;
     const int kbl = bits_for((uint64_t)std::max<int64_t>(max_reads_per_inst - 1, 1));
     const int ib = t.n_inst > 1 ? bits_for((uint64_t)(t.n_inst - 1)) : 0;

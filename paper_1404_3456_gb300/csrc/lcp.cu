@@ -273,6 +273,7 @@ __global__ void __launch_bounds__(128) k_lcp_walk(TextDesc t, const uint32_t *__
 
 int lcp_build_impl(dnasa_ctx *ctx, const TextDesc &t, const uint32_t *sa32, int32_t *lcp,
                    cudaStream_t s, const uint32_t *isa) {
+    PhaseRange nvtx_("dnasa.lcp");
     if (isa) {   // Phi / PLCP in text order, then one gather
         DNASA_TRY(ws_reserve(ctx, ((size_t)t.N * 4 + 255) / 256 * 256 + 4096, s));
         Arena a = ws_arena(ctx);
@@ -327,6 +328,7 @@ int lcp_build_impl(dnasa_ctx *ctx, const TextDesc &t, const uint32_t *sa32, int3
 
 int lcp_finish_with_isa(dnasa_ctx *ctx, const TextDesc &t, const uint32_t *sa32, const uint32_t *isa,
                         int32_t *lcp, int skip, uint32_t *bits, cudaStream_t s) {
+    PhaseRange nvtx_("dnasa.lcp_walk");
     const int64_t words = (t.N + 31) >> 5;
     DNASA_CUDA(ctx, cudaMemsetAsync(bits, 0, (size_t)words * 4, s));
     {

@@ -246,6 +246,7 @@ inline int grid_for(dnasa_ctx *ctx, int64_t n, int threads = 256) {
 int overlap_impl(dnasa_ctx *ctx, const TextDesc &t, const uint32_t *sa32, const int32_t *lcp,
                  int32_t min_overlap, dnasa_edge *edges, int64_t cap, int64_t *n_edges,
                  uint8_t *contained, cudaStream_t s, const uint32_t *isa_in) {
+    PhaseRange nvtx_("dnasa.overlap");
     const int64_t N = t.N, nr = t.n_reads;
     const int kb = bits_for((uint64_t)std::max<int64_t>(nr - 1, 1));
     const int tile = radix_tile_default();

@@ -1940,6 +1940,7 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
 
     // ---- round 0: initial keys, sort, rerank
     {
+        PhaseRange nvtx_("dnasa.sa_round0");
         const int passes0 = ceil_div(key_bits0, 8);
         // one sequence whose key is whole 4-mers: count one 4-mer histogram (k_hist4_fix)
         const bool hist4 = single && h0 == 4 * passes0 && h0 <= 32 && N >= 2 * h0 + 8;
@@ -1982,6 +1983,7 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
     if (kept > 0 && opts.rounds_on_host == 0 && finish_threshold < 0 && !ctx->prof_on &&
         maxgroup <= seg_max && h < (uint64_t)N) {
         int rounds = 0;
+        PhaseRange nvtx_("dnasa.sa_rounds_graph");
         DNASA_TRY(device_rounds(&rounds, &kept, &ngroups, &maxgroup));
         round = rounds;
         cur = rounds & 1;
@@ -2008,6 +2010,7 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
             break;
         }
         if (++round > max_rounds) return fail(ctx, DNASA_INVALID_ARG, "sa_build: max_rounds exceeded");
+        PhaseRange nvtx_("dnasa.sa_round");
         if (h >= (uint64_t)N) return fail(ctx, DNASA_CUDA_ERROR, "sa_build: doubling did not converge");
         // keys for this round
         int grid = (int)std::min<int64_t>(ceil_div(kept, 256), (int64_t)ctx->num_sms * 16);
