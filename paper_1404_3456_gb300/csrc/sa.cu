@@ -396,25 +396,30 @@ __device__ __forceinline__ bool rerank_tile(RerankSmem &S,
         if (lane == 0 && my_maxsize) atomicMax(o.maxgroup, (unsigned long long)my_maxsize);
     }
     __syncthreads();
-    // ---- striped, coalesced writes; rank[pos] goes to its position bucket,
-    // unless it is unchanged (rounds >= 1: the item's group head kept its slot)
-    const int nb = (int)((o.N + (1ll << o.bshift) - 1) >> o.bshift);
-    for (int b = tid; b < nb; b += kRrThreads) S.bcnt[b] = 0;
-    __syncthreads();
+    // ---- striped, coalesced writes; rank[pos] changes only where the item's group
+    // head moved.  Staged by position bucket (o.stage) or, with o.stage null,
+    // written in place: a doubling round changes few ranks, which then cost less
+    // as direct writes than as a staged pass of their own.
+    const bool direct = o.stage == nullptr;
     auto restage = [&](int li) -> bool { return S.u.o.head[li + (li >> 5)] != S.oh[li]; };
     uint32_t bidx[kRrItems];
+    if (!direct) {   // uniform
+        const int nb = (int)((o.N + (1ll << o.bshift) - 1) >> o.bshift);
+        for (int b = tid; b < nb; b += kRrThreads) S.bcnt[b] = 0;
+        __syncthreads();
 #pragma unroll
-    for (int i = 0; i < kRrItems; ++i) {
-        int li = tid + i * kRrThreads;
-        bidx[i] = 0;
-        if (li < tile_n && restage(li)) bidx[i] = atomicAdd(&S.bcnt[S.v[li] >> o.bshift], 1u);
+        for (int i = 0; i < kRrItems; ++i) {
+            int li = tid + i * kRrThreads;
+            bidx[i] = 0;
+            if (li < tile_n && restage(li)) bidx[i] = atomicAdd(&S.bcnt[S.v[li] >> o.bshift], 1u);
+        }
+        __syncthreads();
+        for (int b = tid; b < nb; b += kRrThreads) {
+            uint32_t c = S.bcnt[b];
+            if (c) S.bcnt[b] = atomicAdd(&o.bucket_fill[b], c);
+        }
+        __syncthreads();
     }
-    __syncthreads();
-    for (int b = tid; b < nb; b += kRrThreads) {
-        uint32_t c = S.bcnt[b];
-        if (c) S.bcnt[b] = atomicAdd(&o.bucket_fill[b], c);
-    }
-    __syncthreads();
 #pragma unroll
     for (int i = 0; i < kRrItems; ++i) {
         int li = tid + i * kRrThreads;
@@ -423,14 +428,21 @@ __device__ __forceinline__ bool rerank_tile(RerankSmem &S,
         uint32_t pos = S.v[li];
         uint32_t hs = S.u.o.head[li + (li >> 5)];
         int32_t kp = S.u.o.kp[li + (li >> 5)];
-        uint32_t b = pos >> o.bshift;
-        uint64_t st = ((uint64_t)b << o.bshift) + S.bcnt[b] + bidx[i];
-        if ((int64_t)slot >= o.N || (int64_t)pos >= o.N || kp >= n || (int64_t)st >= o.N) {
+        if ((int64_t)slot >= o.N || (int64_t)pos >= o.N || kp >= n) {
             atomicOr(err, DERR_BOUNDS);
             continue;
         }
         o.sa[slot] = pos;
-        if (restage(li)) o.stage[st] = make_uint2(pos, hs);
+        if (restage(li)) {
+            if (direct) {
+                o.rank[pos] = hs;
+            } else {
+                const uint32_t b = pos >> o.bshift;
+                const uint64_t st = ((uint64_t)b << o.bshift) + S.bcnt[b] + bidx[i];
+                if ((int64_t)st < o.N) o.stage[st] = make_uint2(pos, hs);
+                else atomicOr(err, DERR_BOUNDS);
+            }
+        }
         if (kp >= 0) {
             o.nslots[kp] = slot;
             o.npos[kp] = pos;
@@ -1839,12 +1851,10 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
         r2.nslots = L[cr ^ 1][0];
         r2.npos = L[cr ^ 1][1];
         r2.nhead = L[cr ^ 1][2];
-        r2.stage = reinterpret_cast<uint2 *>(keys[1]);
+        r2.stage = nullptr;   // changed ranks written in place
         k_rerank<<<rr_grid, kRrThreads, sizeof(RerankSmem), cs>>>(keys[0], vals[0], L[cr][0], 0, &rd->kept, r2,
                                                                   rr_status, c->tile_ctr + 32, &c->err);
-        k_rank_apply<<<ctx->num_sms * 8, 256, 0, cs>>>(reinterpret_cast<const uint2 *>(keys[1]), bucket_fill,
-                                                       nbuckets, bshift, N, rank, &c->err);
-        return nl + 2;
+        return nl + 1;
     };
     // Runs the doubling rounds as the captured graph (captured on first use, or
     // again when a buffer or size differs from the cached one); returns the
@@ -2088,7 +2098,7 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
         }
         DNASA_TRY(reset_counters());
         ro.nslots = L[cur ^ 1][0]; ro.npos = L[cur ^ 1][1]; ro.nhead = L[cur ^ 1][2];
-        ro.stage = reinterpret_cast<uint2 *>(keys[1]);   // free again: stage the rank writes
+        ro.stage = nullptr;   // later rounds write their few changed ranks in place
         int tiles = ceil_div(kept, kRrTile);
         {
             // later rounds keep the decoupled look-back: measured faster here than the
@@ -2098,8 +2108,6 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
             k_rerank<<<tiles, kRrThreads, sizeof(RerankSmem), s>>>(keys[0], vals[0], L[cur][0], kept,
                                                          nullptr, ro, rr_status, c->tile_ctr + 32, &c->err);
         }
-        DNASA_CUDA(ctx, cudaGetLastError());
-        DNASA_TRY(apply_ranks(kept, 1));
         DNASA_CUDA(ctx, cudaGetLastError());
         DNASA_TRY(read_counters(&kept, &ngroups, &maxgroup));
         cur ^= 1;
