@@ -1072,6 +1072,45 @@ __device__ __forceinline__ uint32_t ap_period(uint32_t pmin, uint32_t pmax, int 
     return d / (uint32_t)(n - 1);
 }
 
+// For sa_lcp_build: the LCP of every adjacent pair of an arithmetic-progression
+// group, in closed form.  The members share the period up to the text position e
+// where it breaks (the same e for every pair), so two members at positions a < b
+// agree on exactly e - b bases; e = max + LCP(max - p, max), and that LCP is h
+// plus the LCP of the suffixes h further on, which differ within h bases: one
+// comparison of at most h bases per group.  lcp null: not wanted.
+struct ApLcp {
+    int32_t *lcp;
+    const uint32_t *slots;   // SA slot of each active item (a group's are consecutive)
+    TextDesc t;
+};
+
+// Common prefix (bases, a '$' never matching) of the suffixes at a and b, at most lim.
+__device__ __forceinline__ int64_t text_lcp(const TextDesc &t, int64_t a, int64_t b, int64_t lim) {
+    const int64_t ra = frag_of(t, a), rb = frag_of(t, b);
+    const int64_t m = min(lim, min(__ldg(t.toff + ra + 1) - 1 - a, __ldg(t.toff + rb + 1) - 1 - b));
+    for (int64_t k = 0; k < m; k += 32) {
+        const uint64_t d = bases32(t.packed, (uint64_t)(a - ra + k)) ^ bases32(t.packed, (uint64_t)(b - rb + k));
+        if (d) return min(m, k + (int64_t)(__clzll((long long)d) >> 1));
+    }
+    return m;
+}
+
+// The break position e of a progression group (members pmin .. pmax, step p,
+// sharing h symbols).
+__device__ __forceinline__ int64_t ap_break(const TextDesc &t, uint32_t pmax, uint32_t p, uint32_t h) {
+    return (int64_t)pmax + h + text_lcp(t, (int64_t)pmax - p + h, (int64_t)pmax + h, h);
+}
+
+// LCP entry of the member at sorted index j >= 1 of a progression group.
+__device__ __forceinline__ void ap_lcp_write(const ApLcp &al, uint32_t slot0, uint32_t j, uint32_t pmin,
+                                             uint32_t pmax, uint32_t p, bool asc, int64_t e, uint32_t *err) {
+    if (j == 0) return;   // the pair before the group was separated earlier
+    const int64_t hi_pos = asc ? (int64_t)pmin + (int64_t)j * p : (int64_t)pmax - (int64_t)(j - 1) * p;
+    const int64_t slot = (int64_t)slot0 + j;
+    if (slot < al.t.N && e >= hi_pos) al.lcp[slot] = (int32_t)(e - hi_pos);
+    else atomicOr(err, DERR_BOUNDS);
+}
+
 // Index of a member within an arithmetic-progression group in suffix order.
 __device__ __forceinline__ uint32_t ap_index(uint32_t pos, uint32_t pmin, uint32_t pmax, uint32_t p,
                                              bool ascending) {
@@ -1113,7 +1152,7 @@ __global__ void __launch_bounds__(256) k_seg_thread(const uint2 *__restrict__ gr
                                                     const unsigned long long *__restrict__ d_ng,
                                                     int b, uint32_t h_host, const uint32_t *__restrict__ d_h,
                                                     unsigned long long *__restrict__ keys,
-                                                    uint32_t *__restrict__ vals) {
+                                                    uint32_t *__restrict__ vals, ApLcp al, uint32_t *err) {
     const int64_t ng = (int64_t)*d_ng;
     const uint32_t h = d_h ? *d_h : h_host;
     const unsigned long long rmask = (1ull << b) - 1ull;
@@ -1144,6 +1183,8 @@ __global__ void __launch_bounds__(256) k_seg_thread(const uint2 *__restrict__ gr
                     if (v == pmax - p) kprev = (uint32_t)(w[i] >> 32);
                 }
             if (ok && kmax != kprev) {
+                const int64_t e = al.lcp ? ap_break(al.t, pmax, p, h) : 0;
+                const uint32_t slot0 = al.lcp ? al.slots[gs.x] : 0u;
 #pragma unroll
                 for (int i = 0; i < 8; ++i)
                     if (i < n) {
@@ -1151,6 +1192,7 @@ __global__ void __launch_bounds__(256) k_seg_thread(const uint2 *__restrict__ gr
                         const uint32_t j = ap_index(v, pmin, pmax, p, kprev < kmax);
                         keys[gs.x + j] = hi | j;
                         vals[gs.x + j] = v;
+                        if (al.lcp) ap_lcp_write(al, slot0, j, pmin, pmax, p, kprev < kmax, e, err);
                     }
                 continue;
             }
@@ -1212,7 +1254,7 @@ __device__ __forceinline__ void warp_bitonic(unsigned long long (&w)[E], int lan
 template <int E>
 __device__ __forceinline__ void warp_sort_group(uint2 gs, int lane, int n2, unsigned long long rmask,
                                                 uint32_t h, unsigned long long *__restrict__ keys,
-                                                uint32_t *__restrict__ vals) {
+                                                uint32_t *__restrict__ vals, const ApLcp &al, uint32_t *err) {
     const int n = (int)gs.y;
     const unsigned long long k0 = keys[gs.x];
     const unsigned long long hi = k0 & ~rmask;
@@ -1246,6 +1288,13 @@ __device__ __forceinline__ void warp_sort_group(uint2 gs, int lane, int n2, unsi
         kmax = __reduce_or_sync(0xffffffffu, kmax);     // one lane holds each
         kprev = __reduce_or_sync(0xffffffffu, kprev);
         if (__all_sync(0xffffffffu, ok) && kmax != kprev) {
+            int64_t brk = 0;
+            uint32_t slot0 = 0;
+            if (al.lcp) {
+                if (lane == 0) brk = ap_break(al.t, pmax, p, h);
+                brk = __shfl_sync(0xffffffffu, brk, 0);
+                slot0 = al.slots[gs.x];
+            }
 #pragma unroll
             for (int e = 0; e < E; ++e)
                 if (e * 32 + lane < n) {
@@ -1253,6 +1302,7 @@ __device__ __forceinline__ void warp_sort_group(uint2 gs, int lane, int n2, unsi
                     const uint32_t j = ap_index(v, pmin, pmax, p, kprev < kmax);
                     keys[gs.x + j] = hi | j;
                     vals[gs.x + j] = v;
+                    if (al.lcp) ap_lcp_write(al, slot0, j, pmin, pmax, p, kprev < kmax, brk, err);
                 }
             return;
         }
@@ -1274,7 +1324,7 @@ __global__ void __launch_bounds__(256) k_seg_warp(const uint2 *__restrict__ grou
                                                   const unsigned long long *__restrict__ d_ng, int b,
                                                   uint32_t h_host, const uint32_t *__restrict__ d_h,
                                                   unsigned long long *__restrict__ keys,
-                                                  uint32_t *__restrict__ vals) {
+                                                  uint32_t *__restrict__ vals, ApLcp al, uint32_t *err) {
     const int lane = threadIdx.x & 31;
     const int64_t ng = (int64_t)*d_ng;
     const uint32_t h = d_h ? *d_h : h_host;
@@ -1285,10 +1335,10 @@ __global__ void __launch_bounds__(256) k_seg_warp(const uint2 *__restrict__ grou
         const int n = (int)gs.y;
         int n2 = 2;
         while (n2 < n) n2 <<= 1;   // network only as wide as the group
-        if (n2 <= 32) warp_sort_group<1>(gs, lane, n2, rmask, h, keys, vals);
-        else if (n2 <= 64) warp_sort_group<2>(gs, lane, n2, rmask, h, keys, vals);
-        else if (n2 <= 128) warp_sort_group<4>(gs, lane, n2, rmask, h, keys, vals);
-        else warp_sort_group<8>(gs, lane, n2, rmask, h, keys, vals);
+        if (n2 <= 32) warp_sort_group<1>(gs, lane, n2, rmask, h, keys, vals, al, err);
+        else if (n2 <= 64) warp_sort_group<2>(gs, lane, n2, rmask, h, keys, vals, al, err);
+        else if (n2 <= 128) warp_sort_group<4>(gs, lane, n2, rmask, h, keys, vals, al, err);
+        else warp_sort_group<8>(gs, lane, n2, rmask, h, keys, vals, al, err);
     }
 }
 
@@ -1311,7 +1361,7 @@ __global__ void __launch_bounds__(kSegThreads) k_seg_radix(const uint2 *__restri
                                                            int b, uint32_t h_host,
                                                            const uint32_t *__restrict__ d_h, int min_n,
                                                            int max_n, unsigned long long *__restrict__ keys,
-                                                           uint32_t *__restrict__ vals, uint32_t *err) {
+                                                           uint32_t *__restrict__ vals, uint32_t *err, ApLcp al) {
     constexpr int NW = kSegRadixWarps, CAP = kSegThreads * ROWS;
     extern __shared__ __align__(16) unsigned char seg_raw[];
     unsigned long long *buf0 = reinterpret_cast<unsigned long long *>(seg_raw);
@@ -1319,6 +1369,7 @@ __global__ void __launch_bounds__(kSegThreads) k_seg_radix(const uint2 *__restri
     uint32_t *wh = reinterpret_cast<uint32_t *>(buf1 + CAP);   // [NW][256] digit offsets
     __shared__ uint32_t s_tmp[NW + 1];
     __shared__ uint32_t s_min[NW], s_max[NW], s_k[2];
+    __shared__ long long s_brk;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t ng = (int64_t)*d_ng;
     const uint32_t h = d_h ? *d_h : h_host;
@@ -1377,11 +1428,15 @@ __global__ void __launch_bounds__(kSegThreads) k_seg_radix(const uint2 *__restri
             ok = __syncthreads_and(ok);   // also publishes s_k
             const uint32_t kmax = s_k[0], kprev = s_k[1];
             if (ok && kmax != kprev) {
+                if (al.lcp && tid == 0) s_brk = ap_break(al.t, pmax, p, h);
+                __syncthreads();
+                const uint32_t slot0 = al.lcp ? al.slots[gs.x] : 0u;
                 for (int i = tid; i < n; i += kSegThreads) {
                     const uint32_t v = (uint32_t)buf0[i];
                     const uint32_t j = ap_index(v, pmin, pmax, p, kprev < kmax);
                     keys[gs.x + j] = hi | j;
                     vals[gs.x + j] = v;
+                    if (al.lcp) ap_lcp_write(al, slot0, j, pmin, pmax, p, kprev < kmax, s_brk, err);
                 }
                 __syncthreads();
                 continue;
@@ -1823,6 +1878,14 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
                                                                       sizeof(RerankSmem)));
         rr_grid = ctx->num_sms * std::max(per_sm, 1);
     }
+    // the progression groups' LCP entries, for sa_lcp_build (lcp_out), in a round reading list cr
+    auto ap_lcp = [&](int cr) -> ApLcp {
+        ApLcp al;
+        al.lcp = lcp_out;
+        al.slots = L[cr][0];
+        al.t = t;
+        return al;
+    };
     auto launch_round = [&](cudaStream_t cs, int cr) -> int {   // returns the launch count
         const int G = ctx->num_sms * 16;
         int nl = 0;
@@ -1832,16 +1895,17 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
                                     N, &c->err);
         k_classify<<<G, 256, 0, cs>>>(groups, 0, &rd->ngroups, seg_max, gtiny, gsmall, gwmid, gmid, glarge,
                                       cnt + CNT_SEG);
-        k_seg_thread<<<G, 256, 0, cs>>>(gtiny, cnt + CNT_SEG, b, 0u, &rd->h, keys[0], vals[0]);
-        k_seg_warp<<<G, 256, 0, cs>>>(gsmall, cnt + CNT_SEG + 1, b, 0u, &rd->h, keys[0], vals[0]);
-        k_seg_warp<<<G, 256, 0, cs>>>(gwmid, cnt + CNT_SEG + 2, b, 0u, &rd->h, keys[0], vals[0]);
+        const ApLcp al = ap_lcp(cr);
+        k_seg_thread<<<G, 256, 0, cs>>>(gtiny, cnt + CNT_SEG, b, 0u, &rd->h, keys[0], vals[0], al, &c->err);
+        k_seg_warp<<<G, 256, 0, cs>>>(gsmall, cnt + CNT_SEG + 1, b, 0u, &rd->h, keys[0], vals[0], al, &c->err);
+        k_seg_warp<<<G, 256, 0, cs>>>(gwmid, cnt + CNT_SEG + 2, b, 0u, &rd->h, keys[0], vals[0], al, &c->err);
         nl += 6;
         // each CTA-radix variant takes its own size class of the one list
         auto radix = [&](auto kern, size_t smem, int lo, int hi) {
             if (seg_max <= lo) return;
             const int per_sm = std::max(1, (int)((200u << 10) / smem));
             kern<<<ctx->num_sms * per_sm, kSegThreads, smem, cs>>>(gmid, cnt + CNT_SEG + 3, b, 0u, &rd->h, lo,
-                                                                    hi, keys[0], vals[0], &c->err);
+                                                                    hi, keys[0], vals[0], &c->err, al);
             ++nl;
         };
         radix(k_seg_radix<4>, seg_radix_smem<4>(), kSegWarpMax, kSegThreads * 4);
@@ -1871,7 +1935,12 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
             (unsigned long long)(uintptr_t)glarge, (unsigned long long)(uintptr_t)L[0][0],
             (unsigned long long)(uintptr_t)L[1][0], (unsigned long long)(uintptr_t)rr_status,
             (unsigned long long)(uintptr_t)bucket_fill, (unsigned long long)(uintptr_t)rd,
-            (unsigned long long)(uintptr_t)c};
+            (unsigned long long)(uintptr_t)c,
+            // the progression groups' LCP writes read the text
+            (unsigned long long)(uintptr_t)lcp_out, (unsigned long long)(uintptr_t)t.packed,
+            (unsigned long long)(uintptr_t)t.toff, (unsigned long long)t.n_reads,
+            (unsigned long long)(uintptr_t)t.inst_toff, (unsigned long long)(uintptr_t)t.inst_roff,
+            (unsigned long long)t.n_inst, (unsigned long long)(uintptr_t)t.fid};
         SaGraph *gph = static_cast<SaGraph *>(ctx->sa_graph);
         if (!gph || gph->key != key) {
             if (gph) sa_graph_free(gph);
@@ -2042,14 +2111,15 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
         {
             LaunchScope ls_(ctx, PK_SEGSORT, s, 24.0 * kept);
             int gt = (int)std::min<int64_t>(ceil_div(ngroups, 256), (int64_t)ctx->num_sms * 16);
-            k_seg_thread<<<std::max(gt, 1), 256, 0, s>>>(gtiny, cnt + CNT_SEG, b, hs, nullptr, keys[0], vals[0]);
+            k_seg_thread<<<std::max(gt, 1), 256, 0, s>>>(gtiny, cnt + CNT_SEG, b, hs, nullptr, keys[0], vals[0],
+                                                         ap_lcp(cur), &c->err);
         }
         for (int cls = 1; cls <= 2; ++cls) {   // 9..32 and 33..kSegWarpMax members: a warp each
             if (maxgroup <= (cls == 1 ? 8 : 32) || seg_max <= (cls == 1 ? 8 : 32)) break;
             LaunchScope ls_(ctx, PK_SEGSORT, s, 0.0);
             int gw = (int)std::min<int64_t>(ceil_div(ngroups, 8), (int64_t)ctx->num_sms * 16);
             k_seg_warp<<<std::max(gw, 1), 256, 0, s>>>(cls == 1 ? gsmall : gwmid, cnt + CNT_SEG + cls, b,
-                                                       hs, nullptr, keys[0], vals[0]);
+                                                       hs, nullptr, keys[0], vals[0], ap_lcp(cur), &c->err);
         }
         if (maxgroup > kSegWarpMax && seg_max > kSegWarpMax) {
             const int64_t biggest = std::min<int64_t>(maxgroup, seg_max);
@@ -2058,7 +2128,8 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
                 const int per_sm = std::max(1, (int)((200u << 10) / smem));
                 const int gb = (int)std::min<int64_t>(ngroups, (int64_t)ctx->num_sms * per_sm);
                 kern<<<std::max(gb, 1), kSegThreads, smem, s>>>(gmid, cnt + CNT_SEG + 3, b, hs, nullptr, 0,
-                                                                0x7fffffff, keys[0], vals[0], &c->err);
+                                                                0x7fffffff, keys[0], vals[0], &c->err,
+                                                                ap_lcp(cur));
             };
             if (biggest <= kSegThreads * 4) launch(k_seg_radix<4>, seg_radix_smem<4>());
             else if (biggest <= kSegThreads * 12) launch(k_seg_radix<12>, seg_radix_smem<12>());
