@@ -288,6 +288,36 @@ def test_sa_lcp_build(ctx, kind, opts_kw):
         assert np.array_equal(lcp.cpu().numpy(), oracle.lcp_kasai(t, want))
 
 
+def test_sa_lcp_build_graph_cache_follows_buffers(ctx):
+    """The captured rounds write LCP entries through the buffer they were captured
+    with: a second LCP buffer, a plain sa_build after sa_lcp_build, and a second text
+    of the same length must each get their own results and leave the others alone."""
+    t1 = graph_text("tandem")
+    rng = np.random.default_rng(77)
+    t2 = synth.genome_text(np.concatenate([synth.iid(rng, 500), np.tile(synth.iid(rng, 5), (t1.size - 502) // 5)]))
+    t2 = np.concatenate([t2[:-1], synth.iid(rng, t1.size - t2.size), np.frombuffer(b"$", np.uint8)])
+    assert t2.size == t1.size
+    packed1, toff1, nr1 = B().pack_text(ctx, dev(t1))
+    packed2, toff2, nr2 = B().pack_text(ctx, dev(t2))
+    sa = torch.empty(t1.size, dtype=torch.int32, device="cuda")
+    lcp_a = torch.full((t1.size,), -7, dtype=torch.int32, device="cuda")
+    lcp_b = torch.full_like(lcp_a, -7)
+    want1 = oracle.suffix_array(t1)
+    want2 = oracle.suffix_array(t2)
+    B().sa_lcp_build(ctx, packed1, toff1, nr1, t1.size, sa, lcp_a)
+    assert np.array_equal(lcp_a.cpu().numpy(), oracle.lcp_kasai(t1, want1))
+    a_copy = lcp_a.clone()
+    B().sa_lcp_build(ctx, packed1, toff1, nr1, t1.size, sa, lcp_b)       # another LCP buffer
+    assert np.array_equal(lcp_b.cpu().numpy(), oracle.lcp_kasai(t1, want1))
+    lcp_a.fill_(-9)
+    B().sa_build(ctx, packed2, toff2, nr2, t2.size, sa)                   # no LCP, other text
+    assert np.array_equal(sa.cpu().numpy().astype(np.int64), want2)
+    assert bool((lcp_a == -9).all()) and torch.equal(lcp_b.cpu(), a_copy.cpu())
+    B().sa_lcp_build(ctx, packed2, toff2, nr2, t2.size, sa, lcp_a)       # other text, first buffer
+    assert np.array_equal(lcp_a.cpu().numpy(), oracle.lcp_kasai(t2, want2))
+    assert ctx.trace()["graph_rounds"] >= 1
+
+
 def test_sa_lcp_build_64m_sampled(ctx):
     """The fused call on the 64 Mbp benchmark genome equals the separate calls."""
     g = synth.sa64m_genome(1)
