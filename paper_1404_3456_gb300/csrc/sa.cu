@@ -9,14 +9,19 @@
 //             and are final at once (distinct sentinels ordered by position).
 //   round r   (rank[i], rank[i+h]) for the suffixes still in groups of equal
 //             rank, h = h0 * 2^(r-1): the doubling step of Manber & Myers.
-// Round 0 is a stable LSD radix sort (radix.cu) of every suffix; each later
+// Round 0 is a stable LSD radix sort (radix.cu) of every suffix, then a rerank
+// in which each tile handles the groups whose head it holds (no look-back): SA
+// entries, new ranks (rank = SA index of the group head, i.e. the number of
+// smaller suffixes, Sec. IV's "rank") staged by position bucket and applied
+// bucket by bucket, the singletons dropped and the rest compacted.  Each later
 // round only orders the members of every group by rank[i+h] (in-group sorts on
-// chip, global radix passes for the largest groups).  After each sort one
-// rerank kernel, in a single pass with decoupled look-back, marks group heads,
-// writes SA entries and new ranks (rank = SA index of the group head, i.e. the
-// number of smaller suffixes, Sec. IV's "rank"), drops groups that became
-// singletons and compacts the rest.  When few suffixes remain, a finisher
-// sorts each remaining group by comparing packed words directly.
+// chip, global radix passes for the largest groups; a group that is one
+// arithmetic progression of positions is ordered at once), then reranks in a
+// single pass with decoupled look-back, writing the few changed ranks in place.
+// The later rounds run as one captured CUDA graph with a device-side loop when
+// every group fits the on-chip sorts.  For sa_lcp_build round 0 also writes the
+// LCP of every SA pair its keys separate.  A finisher (optional) sorts each
+// remaining group by comparing rank sequences directly.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -164,7 +169,7 @@ struct RerankOut {
     uint32_t *nslots, *npos, *nhead;
     uint2 *groups;
     unsigned long long *kept, *ngroups, *maxgroup;
-    uint2 *stage;       // [N]: bucket b's (pos, rank) pairs start at b << bshift
+    uint2 *stage;       // round 0 only, [N]: bucket b's (pos, rank) pairs start at b << bshift
     uint32_t *bucket_fill;   // [kMaxBuckets]
     int bshift;
     int pb;             // round 0 only: keys hold (key << pb) | position, no value array
@@ -194,7 +199,6 @@ struct RerankSmem {
     int64_t prefix[2];
     int64_t win_h[kRrThreads / 32], win_k[kRrThreads / 32];
     uint32_t win_nr[kRrThreads / 32], win_inc[kRrThreads / 32];
-    uint32_t bcnt[kMaxBuckets];          // per-bucket counts of this tile, then global bases
     uint32_t tile;
     int abort;
     int stop;
@@ -397,29 +401,9 @@ __device__ __forceinline__ bool rerank_tile(RerankSmem &S,
     }
     __syncthreads();
     // ---- striped, coalesced writes; rank[pos] changes only where the item's group
-    // head moved.  Staged by position bucket (o.stage) or, with o.stage null,
-    // written in place: a doubling round changes few ranks, which then cost less
-    // as direct writes than as a staged pass of their own.
-    const bool direct = o.stage == nullptr;
-    auto restage = [&](int li) -> bool { return S.u.o.head[li + (li >> 5)] != S.oh[li]; };
-    uint32_t bidx[kRrItems];
-    if (!direct) {   // uniform
-        const int nb = (int)((o.N + (1ll << o.bshift) - 1) >> o.bshift);
-        for (int b = tid; b < nb; b += kRrThreads) S.bcnt[b] = 0;
-        __syncthreads();
-#pragma unroll
-        for (int i = 0; i < kRrItems; ++i) {
-            int li = tid + i * kRrThreads;
-            bidx[i] = 0;
-            if (li < tile_n && restage(li)) bidx[i] = atomicAdd(&S.bcnt[S.v[li] >> o.bshift], 1u);
-        }
-        __syncthreads();
-        for (int b = tid; b < nb; b += kRrThreads) {
-            uint32_t c = S.bcnt[b];
-            if (c) S.bcnt[b] = atomicAdd(&o.bucket_fill[b], c);
-        }
-        __syncthreads();
-    }
+    // head moved, and is written in place: a doubling round changes few ranks
+    // (round 0, which writes all of them, stages them by position bucket instead)
+    auto moved = [&](int li) -> bool { return S.u.o.head[li + (li >> 5)] != S.oh[li]; };
 #pragma unroll
     for (int i = 0; i < kRrItems; ++i) {
         int li = tid + i * kRrThreads;
@@ -433,16 +417,7 @@ __device__ __forceinline__ bool rerank_tile(RerankSmem &S,
             continue;
         }
         o.sa[slot] = pos;
-        if (restage(li)) {
-            if (direct) {
-                o.rank[pos] = hs;
-            } else {
-                const uint32_t b = pos >> o.bshift;
-                const uint64_t st = ((uint64_t)b << o.bshift) + S.bcnt[b] + bidx[i];
-                if ((int64_t)st < o.N) o.stage[st] = make_uint2(pos, hs);
-                else atomicOr(err, DERR_BOUNDS);
-            }
-        }
+        if (moved(li)) o.rank[pos] = hs;
         if (kp >= 0) {
             o.nslots[kp] = slot;
             o.npos[kp] = pos;
@@ -1630,10 +1605,10 @@ struct RoundDev {   // 64 words: read back whole into the pinned buffer
 static_assert(sizeof(RoundDev) == 64 * 8, "one pinned read-back");
 
 // Start of a round: the counts the last rerank left become the round's inputs
-// (thread 0, before it clears them); the rerank's tile counter, look-back words
-// and rank-bucket fills are cleared.
+// (thread 0, before it clears them); the rerank's tile counter and look-back
+// words are cleared.
 __global__ void k_round_begin(RoundDev *rd, unsigned long long *cnt, uint32_t *tile_ctr,
-                              unsigned long long *rr_status, int64_t rr_tiles, uint32_t *bucket_fill) {
+                              unsigned long long *rr_status, int64_t rr_tiles) {
     const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     if (i0 == 0) {
@@ -1645,7 +1620,6 @@ __global__ void k_round_begin(RoundDev *rd, unsigned long long *cnt, uint32_t *t
         for (int k = 0; k < 4; ++k) tile_ctr[k] = 0;
     }
     for (int64_t i = i0; i < rr_tiles; i += stride) rr_status[i] = 0;
-    for (int64_t i = i0; i < kMaxBuckets; i += stride) bucket_fill[i] = 0;
 }
 
 // Sets up the loop state before the graph runs (outside it: per call values).
@@ -1889,8 +1863,7 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
     auto launch_round = [&](cudaStream_t cs, int cr) -> int {   // returns the launch count
         const int G = ctx->num_sms * 16;
         int nl = 0;
-        k_round_begin<<<ctx->num_sms, 256, 0, cs>>>(rd, cnt, c->tile_ctr + 32, rr_status, rr_tiles,
-                                                    bucket_fill);
+        k_round_begin<<<ctx->num_sms, 256, 0, cs>>>(rd, cnt, c->tile_ctr + 32, rr_status, rr_tiles);
         k_gather<<<G, 256, 0, cs>>>(L[cr][1], L[cr][2], 0, &rd->kept, rank, 0u, &rd->h, b, keys[0], vals[0],
                                     N, &c->err);
         k_classify<<<G, 256, 0, cs>>>(groups, 0, &rd->ngroups, seg_max, gtiny, gsmall, gwmid, gmid, glarge,
@@ -1915,7 +1888,6 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
         r2.nslots = L[cr ^ 1][0];
         r2.npos = L[cr ^ 1][1];
         r2.nhead = L[cr ^ 1][2];
-        r2.stage = nullptr;   // changed ranks written in place
         k_rerank<<<rr_grid, kRrThreads, sizeof(RerankSmem), cs>>>(keys[0], vals[0], L[cr][0], 0, &rd->kept, r2,
                                                                   rr_status, c->tile_ctr + 32, &c->err);
         return nl + 1;
@@ -2169,7 +2141,6 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
         }
         DNASA_TRY(reset_counters());
         ro.nslots = L[cur ^ 1][0]; ro.npos = L[cur ^ 1][1]; ro.nhead = L[cur ^ 1][2];
-        ro.stage = nullptr;   // later rounds write their few changed ranks in place
         int tiles = ceil_div(kept, kRrTile);
         {
             // later rounds keep the decoupled look-back: measured faster here than the
