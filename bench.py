@@ -941,19 +941,31 @@ def main():
 
         copy_stream = torch.cuda.Stream(device=dev)
 
+        # one sa_lcp_build per step into alternating output buffers: a step's two
+        # read-backs overlap the next step's build, and a buffer set is overwritten
+        # only after its own read-backs (two steps earlier) are done.  Every copy is
+        # inside the timed region.
+        sa_bufs = [sa, torch.empty_like(sa)]
+        lcp_bufs = [lcp, torch.empty_like(lcp)]
+        read_done = [torch.cuda.Event(), torch.cuda.Event()]
+        for ev in read_done:
+            ev.record(copy_stream)
+        turn = [0]
+
         def e2e_step():
+            k = turn[0]
+            turn[0] ^= 1
             d_packed.copy_(h_packed, non_blocking=True)
             d_toff.copy_(h_toff, non_blocking=True)
-            stream.wait_stream(copy_stream)   # the last step's SA read-back is done with sa
-            # with host buffers the two calls are faster than sa_lcp_build: the SA's
-            # read-back overlaps the LCP build (measured: 8,700 vs 8,470 Msuffix/s)
-            binding.sa_build(ctx, d_packed, d_toff, nr, N, sa, opts)
-            copy_stream.wait_stream(stream)   # the SA is complete
-            with torch.cuda.stream(copy_stream):   # its read-back overlaps lcp_build
-                h_sa.copy_(sa, non_blocking=True)
-            binding.lcp_build(ctx, d_packed, d_toff, nr, N, sa, lcp)
-            h_lcp.copy_(lcp, non_blocking=True)
+            stream.wait_event(read_done[k])
+            binding.sa_lcp_build(ctx, d_packed, d_toff, nr, N, sa_bufs[k], lcp_bufs[k], opts)
+            copy_stream.wait_stream(stream)
+            with torch.cuda.stream(copy_stream):
+                h_sa.copy_(sa_bufs[k], non_blocking=True)
+                h_lcp.copy_(lcp_bufs[k], non_blocking=True)
+                read_done[k].record(copy_stream)
 
+        e2e_step()   # one build per buffer set before timing (each set's graph is captured once)
         e2e_step()
         torch.cuda.synchronize()
         barrier()
@@ -967,7 +979,8 @@ def main():
         torch.cuda.synchronize()
         e2e_ms = x0.elapsed_time(x1) / args.steps
         e2e = {"ms": e2e_ms, "h2d": h_packed.numel() * 8 + h_toff.numel() * 8, "d2h": 8 * N,
-               "calls": "sa_build, lcp_build (the SA read-back overlapping lcp_build)"}
+               "calls": ("sa_lcp_build into alternating output buffers; each step's read-backs overlap the "
+                         "next step's build")}
 
     reads_info = None
     if large:   # the 10 M x 150 bp reads of the same genome: their own SA, LCP, overlap search

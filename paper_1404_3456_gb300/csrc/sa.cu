@@ -1660,12 +1660,24 @@ struct SaGraph {
     int launches_per_round = 0;
 };
 
-static void sa_graph_free(void *p) {
-    SaGraph *g = static_cast<SaGraph *>(p);
+static void sa_graph_free(SaGraph *g) {
     if (g->exec) cudaGraphExecDestroy(g->exec);
     if (g->graph) cudaGraphDestroy(g->graph);
     if (g->cs) cudaStreamDestroy(g->cs);
     delete g;
+}
+
+// The context's captured loops, most recently used last: a caller that alternates
+// output buffers (double buffering) reuses one graph per buffer set.
+struct SaGraphCache {
+    static constexpr size_t kMax = 4;
+    std::vector<SaGraph *> g;
+};
+
+static void sa_graph_cache_free(void *p) {
+    SaGraphCache *c = static_cast<SaGraphCache *>(p);
+    for (SaGraph *x : c->g) sa_graph_free(x);
+    delete c;
 }
 
 // Symbols in the initial key.  Enough that i.i.d. text leaves few suffixes
@@ -1913,15 +1925,28 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
             (unsigned long long)(uintptr_t)t.toff, (unsigned long long)t.n_reads,
             (unsigned long long)(uintptr_t)t.inst_toff, (unsigned long long)(uintptr_t)t.inst_roff,
             (unsigned long long)t.n_inst, (unsigned long long)(uintptr_t)t.fid};
-        SaGraph *gph = static_cast<SaGraph *>(ctx->sa_graph);
-        if (!gph || gph->key != key) {
-            if (gph) sa_graph_free(gph);
+        SaGraphCache *cache = static_cast<SaGraphCache *>(ctx->sa_graph);
+        if (!cache) {
+            cache = new SaGraphCache();
+            ctx->sa_graph = cache;
+            ctx->sa_graph_free = sa_graph_cache_free;
+        }
+        SaGraph *gph = nullptr;
+        for (size_t i = 0; i < cache->g.size(); ++i)
+            if (cache->g[i]->key == key) {   // reuse, and mark most recently used
+                gph = cache->g[i];
+                cache->g.erase(cache->g.begin() + (std::ptrdiff_t)i);
+                cache->g.push_back(gph);
+                break;
+            }
+        if (!gph) {
+            if (cache->g.size() >= SaGraphCache::kMax) {   // evict the least recently used
+                sa_graph_free(cache->g.front());
+                cache->g.erase(cache->g.begin());
+            }
             gph = new SaGraph();
-            ctx->sa_graph = gph;
-            ctx->sa_graph_free = sa_graph_free;
             auto drop = [&](cudaError_t e, const char *where) -> int {   // no half-built graph is kept
                 sa_graph_free(gph);
-                ctx->sa_graph = nullptr;
                 return cuda_fail(ctx, e, where);
             };
             cudaError_t e = cudaStreamCreateWithFlags(&gph->cs, cudaStreamNonBlocking);
@@ -1972,6 +1997,7 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
             if (e == cudaSuccess) e = cudaGraphInstantiate(&gph->exec, gph->graph, 0);
             if (e != cudaSuccess) return drop(e, "sa_build: second round capture");
             gph->key = key;
+            cache->g.push_back(gph);
         }
         k_round_init<<<1, 1, 0, s>>>(rd, (uint32_t)h0, max_rounds);
         DNASA_CUDA(ctx, cudaGetLastError());
