@@ -271,8 +271,9 @@ def lcp_texts():
 
 
 @pytest.mark.parametrize("kind", ["repeat", "tandem", "multi", "short_reads", "endings", "tiny"])
-@pytest.mark.parametrize("opts_kw", [{}, {"pack_position": -1}, {"rounds_on_host": 1}, {"builder": 1}],
-                         ids=["packed", "pairs", "host_rounds", "dc3"])
+@pytest.mark.parametrize("opts_kw", [{}, {"pack_position": -1}, {"rounds_on_host": 1}, {"builder": 1},
+                                     {"finish_threshold": 1 << 40}, {"seg_max": 8}],
+                         ids=["packed", "pairs", "host_rounds", "dc3", "finisher", "global_radix"])
 def test_sa_lcp_build(ctx, kind, opts_kw):
     """SA and LCP in one call: round 0 writes the LCP of every pair its keys separate,
     the rest is compared on the text; both arrays equal the oracle's."""
