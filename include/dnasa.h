@@ -106,12 +106,13 @@ typedef struct {
                                   and at the end only -- whenever profiling is off, the
                                   direct-comparison finisher is off and every group fits
                                   the on-chip sorts (seg_max); rounds outside those
-                                  conditions run from the host.  The context keeps the
-                                  graphs of its four most recently used buffer sets and
-                                  sizes (a caller that alternates output buffers reuses
-                                  one per set) and captures a new one otherwise.  1:
-                                  every round from the host, which reads three counters
-                                  back after each */
+                                  conditions run from the host.  A graph is captured on
+                                  the second build with the same buffers and sizes (the
+                                  first runs its rounds from the host), and the context
+                                  keeps the graphs of its four most recently used
+                                  configurations (a caller that alternates output
+                                  buffers reuses one per set).  1: every round from the
+                                  host, which reads three counters back after each */
 } dnasa_opts;
 
 /* One suffix-prefix overlap: the last L bases of fragment j equal the first L

@@ -1668,10 +1668,15 @@ static void sa_graph_free(SaGraph *g) {
 }
 
 // The context's captured loops, most recently used last: a caller that alternates
-// output buffers (double buffering) reuses one graph per buffer set.
+// output buffers (double buffering) reuses one graph per buffer set.  A loop is
+// captured only when its configuration comes back: the first call with new
+// buffers or sizes runs its rounds from the host and is remembered in `seen`, so a
+// stream of one-off sizes (a server's batches) never pays for a capture it would
+// not reuse.
 struct SaGraphCache {
-    static constexpr size_t kMax = 4;
+    static constexpr size_t kMax = 4, kSeen = 8;
     std::vector<SaGraph *> g;
+    std::vector<std::vector<unsigned long long>> seen;
 };
 
 static void sa_graph_cache_free(void *p) {
@@ -1939,6 +1944,16 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
                 cache->g.push_back(gph);
                 break;
             }
+        if (!gph) {   // capture only a configuration seen before
+            auto it = std::find(cache->seen.begin(), cache->seen.end(), key);
+            if (it == cache->seen.end()) {
+                if (cache->seen.size() >= SaGraphCache::kSeen) cache->seen.erase(cache->seen.begin());
+                cache->seen.push_back(key);
+                *rounds = -1;   // declined: the host runs the rounds this time
+                return DNASA_OK;
+            }
+            cache->seen.erase(it);
+        }
         if (!gph) {
             if (cache->g.size() >= SaGraphCache::kMax) {   // evict the least recently used
                 sa_graph_free(cache->g.front());
@@ -2062,11 +2077,13 @@ int sa_build_u32(dnasa_ctx *ctx, const TextDesc &t, uint32_t *sa32, const dnasa_
         int rounds = 0;
         PhaseRange nvtx_("dnasa.sa_rounds_graph");
         DNASA_TRY(device_rounds(&rounds, &kept, &ngroups, &maxgroup));
-        round = rounds;
-        cur = rounds & 1;
-        h = (uint64_t)h0 << rounds;
-        tr.rounds = rounds;
-        tr.graph_rounds = rounds;
+        if (rounds >= 0) {   // else: a first call with these buffers and sizes, rounds from the host
+            round = rounds;
+            cur = rounds & 1;
+            h = (uint64_t)h0 << rounds;
+            tr.rounds = rounds;
+            tr.graph_rounds = rounds;
+        }
     }
     while (kept > 0) {
         if (finish_threshold >= 0 && kept <= finish_threshold && maxgroup <= kFinMax) {

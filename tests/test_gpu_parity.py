@@ -209,31 +209,53 @@ def graph_text(kind):
     return np.frombuffer(b"ACGTACGTAC$ACGTT$", np.uint8)
 
 
+class FixedBuffers:
+    """One text packed once and one SA buffer, so that repeated builds present the
+    same configuration (the graph of the doubling rounds is captured on the second)."""
+
+    def __init__(self, ctx, t):
+        self.ctx, self.t = ctx, t
+        self.packed, self.toff, self.nr = B().pack_text(ctx, dev(t))
+        self.sa = torch.empty(t.size, dtype=torch.int32, device="cuda")
+
+    def build(self, opts=None):
+        B().sa_build(self.ctx, self.packed, self.toff, self.nr, self.t.size, self.sa, opts)
+        return self.sa.cpu().numpy().astype(np.int64), self.ctx.trace()
+
+
 @pytest.mark.parametrize("kind", GRAPH_TEXTS)
 def test_sa_graph_rounds_equal_host_rounds(ctx, kind):
     """The doubling rounds run as one captured graph (a device-side WHILE loop)
-    or from the host: the same SA (the oracle's), the same rounds and actives."""
+    or from the host: the same SA (the oracle's), the same rounds and actives.  The
+    first build of a configuration runs its rounds from the host; a repeat is
+    captured and runs in the graph."""
     t = graph_text(kind)
     want = oracle.suffix_array(t)
-    sa = gpu_sa(ctx, t, opts=B().make_opts(rounds_on_host=1))[0]
-    assert np.array_equal(sa.cpu().numpy().astype(np.int64), want)
-    host = ctx.trace()
-    assert host["graph_rounds"] == 0
-    sa = gpu_sa(ctx, t, opts=B().make_opts())[0]
-    assert np.array_equal(sa.cpu().numpy().astype(np.int64), want)
-    dev_tr = ctx.trace()
+    fb = FixedBuffers(ctx, t)
+    got, host = fb.build(B().make_opts(rounds_on_host=1))
+    assert np.array_equal(got, want) and host["graph_rounds"] == 0
+    got, first = fb.build()
+    assert np.array_equal(got, want) and first["graph_rounds"] == 0   # first sight: host rounds
+    got, dev_tr = fb.build()
+    assert np.array_equal(got, want)
     assert dev_tr["rounds"] == host["rounds"] and dev_tr["active"] == host["active"]
     assert dev_tr["graph_rounds"] == dev_tr["rounds"]
+    got, again = fb.build()                                            # the cached graph
+    assert np.array_equal(got, want) and again["graph_rounds"] == again["rounds"]
 
 
 def test_sa_graph_recaptured_for_new_sizes(ctx):
-    """The cached graph is captured again when the text size changes, and reused
-    (same buffers) when it does not: every call still equals the oracle."""
-    texts = [graph_text("repeat"), graph_text("multi"), graph_text("repeat"), graph_text("tandem")]
-    for t in texts + texts[:1]:
-        sa = gpu_sa(ctx, t)[0]
-        assert np.array_equal(sa.cpu().numpy().astype(np.int64), oracle.suffix_array(t))
-        assert ctx.trace()["graph_rounds"] >= 1
+    """Graphs are kept per configuration (buffers and sizes) and reused: builds of
+    several texts interleaved, each repeated, all equal the oracle; from the second
+    build of a configuration on, its rounds run in the graph."""
+    bufs = [FixedBuffers(ctx, graph_text(k)) for k in ("repeat", "multi", "tandem")]
+    wants = [oracle.suffix_array(fb.t) for fb in bufs]
+    for it in range(3):
+        for fb, want in zip(bufs, wants):
+            got, tr = fb.build()
+            assert np.array_equal(got, want)
+            if it > 0 and tr["rounds"] > 0:
+                assert tr["graph_rounds"] == tr["rounds"]
 
 
 @pytest.mark.parametrize("seg_max", [8, 256])
@@ -249,13 +271,16 @@ def test_sa_graph_hands_large_groups_to_host(ctx, seg_max):
 
 
 def test_sa_graph_max_rounds(ctx):
-    """max_rounds bounds the device loop as it bounds the host loop."""
+    """max_rounds bounds the device loop as it bounds the host loop (the first
+    build of the configuration runs from the host, the second in the graph)."""
     t = graph_text("repeat")
-    with pytest.raises(B().DnasaError) as e:
-        gpu_sa(ctx, t, opts=B().make_opts(max_rounds=2))
-    assert e.value.status == B().INVALID_ARG
-    sa = gpu_sa(ctx, t)[0]   # the context is still usable
-    assert np.array_equal(sa.cpu().numpy().astype(np.int64), oracle.suffix_array(t))
+    fb = FixedBuffers(ctx, t)
+    for _ in range(2):
+        with pytest.raises(B().DnasaError) as e:
+            fb.build(B().make_opts(max_rounds=2))
+        assert e.value.status == B().INVALID_ARG
+    got, _ = fb.build()   # the context is still usable
+    assert np.array_equal(got, oracle.suffix_array(t))
 
 
 def lcp_texts():
@@ -305,17 +330,26 @@ def test_sa_lcp_build_graph_cache_follows_buffers(ctx):
     lcp_b = torch.full_like(lcp_a, -7)
     want1 = oracle.suffix_array(t1)
     want2 = oracle.suffix_array(t2)
-    B().sa_lcp_build(ctx, packed1, toff1, nr1, t1.size, sa, lcp_a)
-    assert np.array_equal(lcp_a.cpu().numpy(), oracle.lcp_kasai(t1, want1))
+    for _ in range(2):   # the second build of each configuration runs in its captured graph
+        B().sa_lcp_build(ctx, packed1, toff1, nr1, t1.size, sa, lcp_a)
+        assert np.array_equal(lcp_a.cpu().numpy(), oracle.lcp_kasai(t1, want1))
+    assert ctx.trace()["graph_rounds"] >= 1
     a_copy = lcp_a.clone()
-    B().sa_lcp_build(ctx, packed1, toff1, nr1, t1.size, sa, lcp_b)       # another LCP buffer
-    assert np.array_equal(lcp_b.cpu().numpy(), oracle.lcp_kasai(t1, want1))
+    for _ in range(2):
+        lcp_b.fill_(-7)
+        B().sa_lcp_build(ctx, packed1, toff1, nr1, t1.size, sa, lcp_b)   # another LCP buffer
+        assert np.array_equal(lcp_b.cpu().numpy(), oracle.lcp_kasai(t1, want1))
+        assert torch.equal(lcp_a, a_copy)
     lcp_a.fill_(-9)
-    B().sa_build(ctx, packed2, toff2, nr2, t2.size, sa)                   # no LCP, other text
-    assert np.array_equal(sa.cpu().numpy().astype(np.int64), want2)
-    assert bool((lcp_a == -9).all()) and torch.equal(lcp_b.cpu(), a_copy.cpu())
-    B().sa_lcp_build(ctx, packed2, toff2, nr2, t2.size, sa, lcp_a)       # other text, first buffer
-    assert np.array_equal(lcp_a.cpu().numpy(), oracle.lcp_kasai(t2, want2))
+    for _ in range(2):
+        B().sa_build(ctx, packed2, toff2, nr2, t2.size, sa)               # no LCP, other text
+        assert np.array_equal(sa.cpu().numpy().astype(np.int64), want2)
+        assert bool((lcp_a == -9).all()) and torch.equal(lcp_b.cpu(), a_copy.cpu())
+    for _ in range(2):
+        B().sa_lcp_build(ctx, packed2, toff2, nr2, t2.size, sa, lcp_a)   # other text, first buffer
+        assert np.array_equal(lcp_a.cpu().numpy(), oracle.lcp_kasai(t2, want2))
+    B().sa_lcp_build(ctx, packed1, toff1, nr1, t1.size, sa, lcp_b)       # back to a cached graph
+    assert np.array_equal(lcp_b.cpu().numpy(), oracle.lcp_kasai(t1, want1))
     assert ctx.trace()["graph_rounds"] >= 1
 
 
