@@ -4,7 +4,9 @@ progression, checked by brute force against the oracle's suffix array (CPU only)
 For every h and every group of suffixes sharing their first h symbols (no '$'
 inside), if the members sit at i, i+p, ..., i+(n-1)p with n >= 3 and p <= h, then
 their true order is position order or its reverse, and the h-ranks of the suffixes
-h past the last two members differ and say which.  The h-rank used here is the one
+h past the last two members differ and say which; the LCP of two adjacent members
+(Kasai's, from the oracle) is e minus the larger position, where e = last + h + the
+common prefix of the suffixes h past the last two members.  The h-rank used here is the one
 the doubling rounds hold: the smallest SA slot among the suffixes sharing the first
 h symbols (a unique slot for a suffix whose '$' falls inside them)."""
 import numpy as np
@@ -31,6 +33,15 @@ def h_ranks(t, isa, nxt, h):
     return groups, rank
 
 
+def text_lcp(t, nxt, a, b, lim):
+    """Common prefix of the suffixes at a and b in bases (a '$' never matches), at most lim."""
+    m = min(lim, nxt[a] - a, nxt[b] - b)
+    k = 0
+    while k < m and t[a + k] == t[b + k]:
+        k += 1
+    return k
+
+
 def progression_groups(t):
     """Checks the rule on every progression group of text t; returns how many."""
     n = t.size
@@ -43,6 +54,7 @@ def progression_groups(t):
         if t[i] == ord("$"):
             j = i
         nxt[i] = j
+    lcp = oracle.lcp_kasai(t, sa)
     checked = 0
     h = 1
     while h < n:
@@ -62,6 +74,11 @@ def progression_groups(t):
             assert before != after
             want = g if before < after else g[::-1]
             assert sorted(g, key=lambda x: isa[x]) == want, (h, p, g[:4])
+            # the LCP of adjacent members in closed form: e - the larger position, e the
+            # position where the period breaks, found past the last two members
+            e = last + h + text_lcp(t, nxt, last - p + h, last + h, h)
+            for a, b in zip(want, want[1:]):
+                assert lcp[isa[b]] == e - max(a, b), (h, p, a, b)
             checked += 1
         h *= 2
     return checked
