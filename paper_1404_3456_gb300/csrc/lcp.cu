@@ -108,7 +108,8 @@ __global__ void __launch_bounds__(256) k_lcp(TextDesc t, const uint32_t *__restr
 // predecessor is at least that of p minus one, so along a run of consecutive
 // positions each comparison starts where the previous one ended instead of at
 // base 64.  One thread walks kChain consecutive entries, four words (128 bases)
-// per round trip.  The walk is a chain of dependent loads, so short chains (many
+// per round trip (one word first: past the bound most pairs differ within it).
+// The walk is a chain of dependent loads, so short chains (many
 // threads in flight) beat the comparisons the bound saves inside a long one: a
 // 16 Mbp genome queued ~1.3 M pairs, which at 128 entries per thread left the GPU
 // 6 % occupied.
@@ -128,7 +129,16 @@ __global__ void __launch_bounds__(256) k_lcp_chain(TextDesc t, const uint32_t *_
             PairInfo pi = pair_info(t, sa, j);
             int64_t h = (p == prev_p + 1 && prev_h - 1 > kShortBases) ? prev_h - 1 : kShortBases;
             int64_t res = pi.m;
-            for (; h < pi.m; h += 4 * 32) {
+            bool found = false;
+            if (h < pi.m) {   // one word first: past Kasai's bound most pairs differ within it
+                const uint64_t d0 = bases32(t.packed, pi.bp + h) ^ bases32(t.packed, pi.bq + h);
+                if (d0) {
+                    res = min(h + (int64_t)(__clzll((long long)d0) >> 1), pi.m);
+                    found = true;
+                }
+                h += 32;
+            }
+            for (; !found && h < pi.m; h += 4 * 32) {
                 uint64_t d[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
@@ -246,7 +256,16 @@ __global__ void __launch_bounds__(128) k_lcp_walk(TextDesc t, const uint32_t *__
             const uint64_t bp = (uint64_t)(p - rp), bq = (uint64_t)(q - rq);
             int64_t h = (p == prev_p + 1 && prev_h - 1 > skip) ? prev_h - 1 : skip;
             int64_t res = mlen;
-            for (; h < mlen; h += 4 * 32) {
+            bool found = false;
+            if (h < mlen) {   // one word first: past Kasai's bound most pairs differ within it
+                const uint64_t d0 = bases32(t.packed, bp + h) ^ bases32(t.packed, bq + h);
+                if (d0) {
+                    res = min(h + (int64_t)(__clzll((long long)d0) >> 1), mlen);
+                    found = true;
+                }
+                h += 32;
+            }
+            for (; !found && h < mlen; h += 4 * 32) {
                 uint64_t d[4];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
