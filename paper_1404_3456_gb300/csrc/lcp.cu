@@ -224,8 +224,24 @@ __global__ void k_lcp_gather(const uint32_t *__restrict__ sa, const uint32_t *__
 __global__ void __launch_bounds__(256) k_lcp_mark(const uint32_t *__restrict__ sa,
                                                   const int32_t *__restrict__ lcp, int64_t N,
                                                   uint32_t *__restrict__ bits) {
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < N;
-         j += (int64_t)gridDim.x * blockDim.x) {
+    // four entries per 16-byte load when lcp is 16-byte aligned (else all scalar);
+    // the SA is read only where an entry is left (-1)
+    const int64_t quads = ((uintptr_t)lcp & 15u) == 0 ? (N >> 2) : 0;
+    const int4 *lcp4 = reinterpret_cast<const int4 *>(lcp);
+    for (int64_t qd = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; qd < quads;
+         qd += (int64_t)gridDim.x * blockDim.x) {
+        const int4 v = lcp4[qd];
+        const int64_t j = qd << 2;
+        const int32_t e[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (e[u] < 0) {
+                const uint32_t p = sa[j + u];
+                atomicOr(bits + (p >> 5), 1u << (p & 31u));
+            }
+    }
+    for (int64_t j = (quads << 2) + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < N;
+         j += (int64_t)gridDim.x * blockDim.x) {   // the last N mod 4 entries
         if (lcp[j] < 0) {
             const uint32_t p = sa[j];
             atomicOr(bits + (p >> 5), 1u << (p & 31u));

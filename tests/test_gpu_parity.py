@@ -353,6 +353,22 @@ def test_sa_lcp_build_graph_cache_follows_buffers(ctx):
     assert ctx.trace()["graph_rounds"] >= 1
 
 
+def test_sa_lcp_build_unaligned_lcp(ctx):
+    """An LCP buffer that starts 4 bytes into an allocation (not 16-byte aligned)
+    is filled entirely and correctly."""
+    t = graph_text("repeat")
+    want = oracle.suffix_array(t)
+    packed, toff, nr = B().pack_text(ctx, dev(t))
+    sa = torch.empty(t.size, dtype=torch.int32, device="cuda")
+    big = torch.full((t.size + 1,), -7, dtype=torch.int32, device="cuda")
+    lcp = big[1:]
+    assert lcp.data_ptr() % 16 != 0
+    B().sa_lcp_build(ctx, packed, toff, nr, t.size, sa, lcp)
+    assert np.array_equal(sa.cpu().numpy().astype(np.int64), want)
+    assert np.array_equal(lcp.cpu().numpy(), oracle.lcp_kasai(t, want))
+    assert int(big[0]) == -7
+
+
 def test_sa_lcp_build_64m_sampled(ctx):
     """The fused call on the 64 Mbp benchmark genome equals the separate calls."""
     g = synth.sa64m_genome(1)
